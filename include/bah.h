@@ -1,0 +1,214 @@
+/*
+ * bah.h -- C ABI of the GB300 block-acoustic Helmholtz solver.
+ *
+ * Solves the mixed displacement-pressure form of the frequency-domain elastic
+ * Helmholtz equation (Yovel & Treister, "A block-acoustic preconditioner for
+ * the elastic Helmholtz equation", arXiv 2411.15897):
+ *
+ *     H [u; p] = [A  B^T; B  -C] [u; p] = b                          (Eq. 2.6)
+ *
+ * on a MAC-staggered grid (u_k on the x_k-faces; p, lambda, mu, rho, gamma at
+ * cell centres), with flexible GMRES (FGMRES) preconditioned by the
+ * block-triangular block-acoustic preconditioner P = [A B^T; 0 H_p]
+ * (Eq. 3.5) applied as P^{-1} D with the distributor D = [I 0; B -A_p]
+ * (Eq. 3.1-3.3), each acoustic diagonal block approximately inverted by one
+ * shifted-Laplacian geometric-multigrid cycle (Sec. 2.2, Eq. 2.8, Sec. 4.4.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid:     n[0] x n[1] (x n[2]) cells, x_1 fastest, spacings h[0..dim-1].
+ * Medium:   cell-centred FP64 host arrays of n[0]*n[1](*n[2]) values, x_1
+ *           fastest: lambda, mu (Lame), rho (density), gamma (attenuation,
+ *           absorbing layer included); angular frequency omega.  The system
+ *           uses rho~ = rho (1 - i gamma/omega) in its mass terms (Eq. 2.6).
+ * Vectors:  complex FP64 (interleaved re, im: 16 bytes per entry), padded
+ *           layout of (dim+1) components of n[0]*n[1](*n[2]) entries each:
+ *           component k < dim is u_{k+1}, stored at the cell whose lower
+ *           x_k-face carries it; the entries with index 0 along x_k are the
+ *           boundary-normal displacements, which are not unknowns (the
+ *           normal displacement vanishes on the boundary): they are read as
+ *           zero and written as zero.  Component dim is p.  nrhs vectors are
+ *           stored one after another.
+ * Pointers: vector arguments are DEVICE pointers on the current CUDA device
+ *           unless an entry point says otherwise.  The caller owns every
+ *           buffer it passes; the library owns its context and workspace,
+ *           allocated in bah_create and released in bah_destroy.  Calls that
+ *           take a stream enqueue their work on it (NULL = legacy default
+ *           stream) and, unless stated, do not synchronise it.
+ * Errors:   every int-returning call returns BAH_OK (0) or a negative
+ *           status; bah_status_string names it and bah_last_error() gives
+ *           the detail of the most recent failure on the calling thread.
+ *           Nothing aborts or throws across this boundary.
+ */
+#ifndef BAH_H
+#define BAH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BAH_OK                 0
+#define BAH_ERR_ARG           -1   /* invalid argument (pointer, size, option) */
+#define BAH_ERR_OOM           -2   /* device or host allocation failed */
+#define BAH_ERR_CUDA          -3   /* a CUDA runtime call failed */
+#define BAH_ERR_NOT_CONVERGED -4   /* maxit reached; x holds the last iterate */
+#define BAH_ERR_NONFINITE     -5   /* NaN/Inf met in a reduction; x holds the last finite iterate */
+#define BAH_ERR_UNSUPPORTED   -6   /* a valid request this build does not implement */
+
+/* precision of the preconditioner (the outer FGMRES, the operator apply and
+ * the coarsest-level solve are FP64 in both modes) */
+#define BAH_FP64   0   /* multigrid in complex FP64 with FP64 coefficients */
+#define BAH_MIXED  1   /* multigrid in complex FP32, coefficients stored in bfloat16 */
+
+#define BAH_CYCLE_V 0
+#define BAH_CYCLE_W 1
+
+#define BAH_INTERGRID_BILINEAR 0   /* Eq. 4.1, 4.2: 1/4[1 2 1], 1/8[1 3 * 3 1] */
+#define BAH_INTERGRID_MIXED    1   /* Eq. 4.4: 1/2[1 * 1] along cell-centred axes */
+
+typedef struct bah_ctx bah_ctx;    /* opaque, owned by the library */
+
+typedef struct {
+    int    dim;      /* 2 or 3 */
+    int    n[3];     /* cells along x_1, x_2, x_3 (n[2] ignored in 2D) */
+    double h[3];     /* cell size along each axis */
+} bah_grid;
+
+typedef struct {
+    const double* lambda;   /* host, cell-centred, x_1 fastest */
+    const double* mu;
+    const double* rho;
+    const double* gamma;    /* attenuation incl. the absorbing layer */
+    double        omega;    /* angular frequency, > 0 */
+} bah_medium;
+
+typedef struct {
+    int    precision;        /* BAH_FP64 or BAH_MIXED */
+    int    levels;           /* multigrid levels incl. the fine level; 0 = automatic */
+    int    max_coarse_cells; /* automatic levels: coarsen until a level has at most this many cells */
+    int    cycle;            /* BAH_CYCLE_V or BAH_CYCLE_W */
+    int    nu_pre, nu_post;  /* damped-Jacobi sweeps before / after the coarse correction */
+    double jacobi_w[8];      /* damping per level (the last value repeats on deeper levels) */
+    int    n_jacobi_w;
+    double shift_alpha;      /* complex shift alpha of Eq. 2.8; < 0 = by level count */
+    int    intergrid;        /* BAH_INTERGRID_* */
+    int    restart;          /* FGMRES restart length m (1..64) */
+    int    maxit;            /* maximum FGMRES iterations per right-hand side */
+} bah_opts;
+
+typedef struct {
+    int    iters;            /* FGMRES iterations (preconditioner applications) */
+    int    restarts;         /* restart cycles run */
+    double relres_true;      /* ||b - H x|| / ||b|| in FP64 at exit */
+    double relres_est;       /* Arnoldi estimate at exit */
+    int    status;           /* BAH_OK, BAH_ERR_NOT_CONVERGED or BAH_ERR_NONFINITE */
+} bah_stats;
+
+/* Fill *opts with the defaults: BAH_MIXED, automatic levels with at most 256
+ * coarsest cells, V(1,2), Jacobi weights 0.8, 0.8, 0.3 (Sec. 4.4.1), shift by
+ * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels, 0.5 deeper; Sec. 4.4.3,
+ * Table 4), bilinear intergrid, FGMRES(20), maxit 5000. */
+void bah_default_opts(bah_opts* opts);
+
+/* Build a solver for one grid, medium and frequency.  Copies the host medium
+ * to the device, forms the operator coefficients (Eq. 2.6), the distributor
+ * (Eq. 3.2), the shifted acoustic blocks A_k,s and H_p,s (Eq. 2.8, 3.4), their
+ * Galerkin hierarchies R A P (Eq. 4.3) and the FP64 inverse of every coarsest
+ * block, and allocates all solve workspace.  Synchronous.  *out receives the
+ * context; on failure *out is NULL and nothing is leaked.
+ * Errors: BAH_ERR_ARG (dim not 2, odd or too small sizes for the requested
+ * levels, non-positive h or omega, NULL arrays), BAH_ERR_UNSUPPORTED (dim 3),
+ * BAH_ERR_OOM, BAH_ERR_CUDA. */
+int bah_create(const bah_grid* grid, const bah_medium* medium, const bah_opts* opts, bah_ctx** out);
+
+/* Release the context and all device memory it owns.  NULL is ignored.  The
+ * caller must make sure no work enqueued on the context is still running. */
+void bah_destroy(bah_ctx* ctx);
+
+/* Entries of one padded vector ((dim+1) * cells) and the number of multigrid
+ * levels in use.  Either output pointer may be NULL. */
+int bah_sizes(const bah_ctx* ctx, long long* vector_len, int* levels);
+
+/* y = H x (conj_transpose = 0) or y = H^H x (conj_transpose = 1) in FP64 for
+ * nrhs vectors (Eq. 2.6; H is complex symmetric, so H^H = conj(H)).  x and y
+ * are device vectors and must not overlap. */
+int bah_apply_operator(bah_ctx* ctx, const void* x, void* y, int nrhs, int conj_transpose, void* stream);
+
+/* z = P^{-1} D r: one block-acoustic preconditioning step (Eq. 3.1-3.5):
+ *   t_p = B r_u - A_p r_p;  e_p ~ H_p,s^{-1} t_p;  e_u ~ A_s^{-1}(r_u - B^T e_p)
+ * with one multigrid cycle per block, in the context's precision.  r, z
+ * device vectors (FP64), must not overlap. */
+int bah_apply_preconditioner(bah_ctx* ctx, const void* r, void* z, int nrhs, void* stream);
+
+/* Solve H x = b to ||b - H x||_2 <= rtol ||b||_2 by FGMRES(m) with the
+ * block-acoustic preconditioner, x_0 = 0, for nrhs right-hand sides.  b and x
+ * may both be device pointers, or both host pointers (then the copies to and
+ * from the device are part of the call).  Synchronises the stream before
+ * returning.  stats (may be NULL) receives nrhs records.  Returns BAH_OK when
+ * every right-hand side converged, else the first failing status
+ * (BAH_ERR_NOT_CONVERGED / BAH_ERR_NONFINITE) after solving all of them. */
+int bah_solve(bah_ctx* ctx, const void* b, void* x, int nrhs, double rtol, bah_stats* stats, void* stream);
+
+/* Test hook: one multigrid cycle (the context's cycle type) on acoustic block
+ * `block` (0..dim-1 = A_{block+1},s; dim = H_p,s) with zero initial guess.
+ * b and x are device arrays of cells complex FP64 values in the padded
+ * per-component layout of that block. */
+int bah_block_cycle(bah_ctx* ctx, int block, const void* b, void* x, void* stream);
+
+/* Test hook: copy the FP64 operator of block `block` on level `level` to the
+ * host.  Level 0 gives the fine shifted block as a 3x3 stencil, coarser
+ * levels the Galerkin stencil (Eq. 4.3) of radius (rx, rz) written to *rx,
+ * *rz.  out receives (2rz+1)(2rx+1) slots x points complex values
+ * (slot-major, slot index (dz+rz)(2rx+1) + (dx+rx)); out may be NULL to query
+ * the radii.  Synchronous. */
+int bah_level_stencil(const bah_ctx* ctx, int block, int level, double* out, int* rx, int* rz, int* n1, int* n2);
+
+/* ---------------------------------------------------------------------------
+ * Profiling.  Every context counts the kernels it launches and, per kernel
+ * class, the algorithmic bytes those launches must move (the minimum traffic:
+ * each input and output array touched once, coefficients once per launch).
+ * For the classes set in timing_mask (bit 1 << BAH_K_*), each launch is also
+ * bracketed by CUDA events recorded on the launching stream, and the summed
+ * device time is reported.  Timing adds two event records per timed launch.
+ * ------------------------------------------------------------------------- */
+#define BAH_K_OPERATOR  0   /* y = H x or b - H x, FP64 (Eq. 2.6) */
+#define BAH_K_DISTRIB   1   /* t_p = B r_u - A_p r_p (Eq. 3.1-3.3) */
+#define BAH_K_URHS      2   /* s_u = r_u - B^T e_p (Eq. 3.5) */
+#define BAH_K_JACOBI    3   /* damped Jacobi sweep, all levels */
+#define BAH_K_RESIDUAL  4   /* multigrid residual, all levels */
+#define BAH_K_RESTRICT  5   /* restriction (Eq. 4.1, 4.2, 4.4) */
+#define BAH_K_PROLONG   6   /* prolongation + correction */
+#define BAH_K_COARSE    7   /* coarsest-level FP64 inverse apply */
+#define BAH_K_DOT       8   /* Gram-Schmidt block dot products (2 kernels) */
+#define BAH_K_AXPY      9   /* Gram-Schmidt update w -= V h */
+#define BAH_K_NORM     10   /* 2-norms (2 kernels) */
+#define BAH_K_UPDATE   11   /* x += Z y */
+#define BAH_K_SMALL    12   /* Givens update, triangular solve, scaling, copies, conversions */
+#define BAH_NKCLASS    13
+
+typedef struct {
+    long long launches;             /* kernels launched since the last reset */
+    long long class_launches[16];   /* kernels per class */
+    long long class_calls[16];      /* launcher calls per class (a call may launch 2 kernels) */
+    double    class_ms[16];         /* summed device time per timed class (ms) */
+    double    class_bytes[16];      /* summed algorithmic bytes per class */
+} bah_profile;
+
+/* Select the timed classes (bit mask of 1 << BAH_K_*) and optionally zero the
+ * counters (reset != 0).  Pending timings are folded in first.  Synchronous. */
+int bah_profile_control(bah_ctx* ctx, unsigned timing_mask, int reset);
+
+/* Read the counters (waits for pending timing events).  Synchronous. */
+int bah_profile_read(bah_ctx* ctx, bah_profile* out);
+
+/* Name of a status code (static string). */
+const char* bah_status_string(int status);
+
+/* Detail of the most recent failure on the calling thread ("" if none). */
+const char* bah_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAH_H */

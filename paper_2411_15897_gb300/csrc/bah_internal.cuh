@@ -1,0 +1,188 @@
+// Internal declarations shared by the CUDA translation units of libbah.
+//
+// Grid conventions (2-D): n1 x n2 cells, x_1 fastest, point (i, j) at index
+// j*n1 + i.  Every acoustic block lives on the same padded n1 x n2 index
+// space at each level; its unknowns are
+//   type 0 (u1, nodal along x_1): i >= 1
+//   type 1 (u2, nodal along x_2): j >= 1
+//   type 2 (p,  cell-centred):    all points
+// and the remaining (boundary-normal) points hold structural zeros.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/bah.h"
+
+namespace bah {
+
+// ---------------------------------------------------------------------------
+// precision traits: V = complex vector element, R = real arithmetic type,
+// C / CC = stored real / complex coefficient types
+// ---------------------------------------------------------------------------
+template <int MODE> struct Prec;
+template <> struct Prec<BAH_FP64> {
+    using V = double2; using R = double; using C = double; using CC = double2;
+};
+template <> struct Prec<BAH_MIXED> {
+    using V = float2; using R = float; using C = __nv_bfloat16; using CC = __nv_bfloat162;
+};
+
+__host__ __device__ __forceinline__ double ldr(double x) { return x; }
+__device__ __forceinline__ float ldr(__nv_bfloat16 x) { return __bfloat162float(x); }
+__host__ __device__ __forceinline__ double2 ldc(double2 x) { return x; }
+__device__ __forceinline__ float2 ldc(__nv_bfloat162 x) { return __bfloat1622float2(x); }
+
+template <class V> struct VecTraits;
+template <> struct VecTraits<double2> { using R = double; };
+template <> struct VecTraits<float2> { using R = float; };
+
+// complex helpers (x = re, y = im)
+template <class V> __host__ __device__ __forceinline__ V cmk(typename VecTraits<V>::R a, typename VecTraits<V>::R b) { V v; v.x = a; v.y = b; return v; }
+template <class V> __host__ __device__ __forceinline__ V czero() { return cmk<V>(0, 0); }
+template <class V> __host__ __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <class V> __host__ __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <class V> __host__ __device__ __forceinline__ V cmul(V a, V b) { return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <class V> __host__ __device__ __forceinline__ V cscale(V a, typename VecTraits<V>::R s) { return cmk<V>(a.x * s, a.y * s); }
+template <class V> __host__ __device__ __forceinline__ V cconj(V a) { return cmk<V>(a.x, -a.y); }
+// a * conj-free reciprocal: b / a
+template <class V> __host__ __device__ __forceinline__ V cdiv(V b, V a) {
+    typename VecTraits<V>::R d = a.x * a.x + a.y * a.y;
+    return cmk<V>((b.x * a.x + b.y * a.y) / d, (b.y * a.x - b.x * a.y) / d);
+}
+template <class To, class From> __host__ __device__ __forceinline__ To cconv(From a) {
+    return cmk<To>((typename VecTraits<To>::R)a.x, (typename VecTraits<To>::R)a.y);
+}
+
+__host__ __device__ __forceinline__ bool valid_pt(int type, int i, int j) {
+    return (type == 0) ? (i >= 1) : (type == 1) ? (j >= 1) : true;
+}
+
+// ---------------------------------------------------------------------------
+// operator coefficients of H (FP64, Eq. 2.6), all pre-scaled by 1/h^2 or 1/h
+// ---------------------------------------------------------------------------
+struct OpCoef {
+    int n1, n2;
+    const double* cx;    // mu_c / h1^2 at cells     (u1 own-direction, x-neighbours)
+    const double* cz;    // mu_c / h2^2 at cells     (u2 own-direction)
+    const double* nx;    // mu_node / h1^2 at nodes (i,j), zero on boundary nodes
+    const double* nz;    // mu_node / h2^2
+    const double2* d1;   // diagonal of A_1 incl. -omega^2 rho~ (unshifted)
+    const double2* d2;   // diagonal of A_2
+    const double* cinv;  // 1 / (lambda + mu)
+    double ihx, ihz;     // 1/h1, 1/h2
+};
+
+// ---------------------------------------------------------------------------
+// multigrid level-0 (fine) operators: 5-point stencils from per-point arrays
+// (Eq. 2.6 blocks with the shift of Eq. 2.8; H_p,s of Eq. 3.4; A_p of Eq. 3.2)
+// ---------------------------------------------------------------------------
+template <class C, class CC> struct Fine5 {
+    int n1, n2;
+    const C *cx, *cz, *nx, *nz;   // as OpCoef
+    const C *wx, *wz;             // w / h^2, w = (lambda+2mu)/(lambda+mu)  (H_p off-diagonals)
+    const CC *dg0, *dg1, *dg2;    // shifted diagonals of A_1,s, A_2,s, H_p,s
+    const CC *dAp;                // diagonal of A_p (unshifted)
+};
+
+// one block's data on one level, for batched launches over blocks
+template <class V, class CC> struct LvlBlk {
+    int type;
+    const CC* S;       // stencil [(2rz+1)(2rx+1)][n1*n2] (levels >= 1)
+    int rx, rz;
+    const V* b;        // right-hand side
+    const V* xin;      // current iterate
+    V* xout;           // output iterate / residual
+};
+template <class V, class CC> struct LvlSet {
+    int nb;            // blocks in the set (1..3)
+    int n1, n2;        // level grid
+    LvlBlk<V, CC> blk[3];
+};
+
+// FP64 stencil of one block on one level (setup and test hook)
+struct StencilF64 {
+    double2* S = nullptr;   // [(2rz+1)(2rx+1)][n1*n2]
+    int rx = 1, rz = 1;
+    int n1 = 0, n2 = 0;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (host functions, all asynchronous on `st`)
+// ---------------------------------------------------------------------------
+// setup (k_setup.cu)
+void launch_medium_prep(int n1, int n2, double h1, double h2, double omega, double alpha,
+                        const double* lam, const double* mu, const double* rho, const double* gam,
+                        double* cx, double* cz, double* nx, double* nz, double* wx, double* wz,
+                        double2* d1, double2* d2, double* cinv,
+                        double2* dg0, double2* dg1, double2* dg2, double2* dAp, cudaStream_t st);
+void launch_fine_stencil(int type, int n1, int n2, const double* cx, const double* cz, const double* nx,
+                         const double* nz, const double* wx, const double* wz, const double2* dg,
+                         double2* S, cudaStream_t st);
+void launch_galerkin(int type, int intergrid, const StencilF64& fine, StencilF64& coarse, cudaStream_t st);
+void launch_round_real(const double* src, void* dst, size_t n, int mode, cudaStream_t st);
+void launch_round_cplx(const double2* src, void* dst, size_t n, int mode, cudaStream_t st);
+int  coarse_invert(int type, const StencilF64& S, double2* inv, double2* work, int* piv_work, cudaStream_t st);
+
+// operator (k_ops.cu)
+template <class Vin>
+void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st);
+
+// multigrid (k_mg.cu)
+template <int MODE>
+void launch_jacobi(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                   const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w, int zero_init,
+                   cudaStream_t st);
+template <int MODE>
+void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, cudaStream_t st);
+template <int MODE>
+void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
+                     typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st);
+template <int MODE>
+void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
+                        const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st);
+template <int MODE>
+void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
+                         typename Prec<MODE>::V* const* x, cudaStream_t st);
+template <int MODE>
+void launch_distributor(int n1, int n2, double ihx, double ihz,
+                        const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5,
+                        const double2* r, typename Prec<MODE>::V* tp, cudaStream_t st);
+template <int MODE>
+void launch_u_rhs(int n1, int n2, double ihx, double ihz, const double2* r, const typename Prec<MODE>::V* ep,
+                  typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st);
+void launch_sanitize(double2* v, int n1, int n2, int nvec, cudaStream_t st);
+template <class Vin, class Vout>
+void launch_convert(const Vin* x, Vout* y, size_t n, cudaStream_t st);
+
+// Krylov (k_krylov.cu)
+constexpr int RED_CTAS = 296;   // partial sums per reduction (2 per SM on 148+ SMs)
+void launch_multi_dot(const double2* V, size_t ldv, int k, const double2* w, size_t n,
+                      double2* partial, double2* out, cudaStream_t st);
+void launch_norm2(const double2* w, size_t n, double* partial, double* out, cudaStream_t st);
+void launch_multi_axpy_sub(const double2* V, size_t ldv, int k, const double2* coef, double2* w, size_t n,
+                           cudaStream_t st);
+template <class Vz>
+void launch_update_x(const Vz* Z, size_t ldz, int k, const double2* y, double2* x, size_t n, cudaStream_t st);
+void launch_scale_copy(const double2* w, const double* nrm, double2* v, size_t n, int inverse, cudaStream_t st);
+void launch_arnoldi_givens(double2* Hcol, const double2* h1, const double2* h2, const double* wnorm, int j,
+                           double2* cs, double2* sn, double2* g, double* status, cudaStream_t st);
+void launch_triangular_solve(const double2* Hm, int ldh, const double2* g, int k, double2* y, cudaStream_t st);
+void launch_init_arnoldi(const double* beta, double2* g, int m, double* status, cudaStream_t st);
+
+// error handling
+void set_error(const std::string& msg);
+}  // namespace bah
+
+#define BAH_CUDA_TRY(expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            bah::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));           \
+            return BAH_ERR_CUDA;                                                            \
+        }                                                                                   \
+    } while (0)

@@ -1,0 +1,213 @@
+// Matrix-free kernels of the outer system and the preconditioner's two
+// coupling steps:
+//   * y = H x (or y = b - H x) in FP64, Eq. 2.6;
+//   * t_p = B r_u - A_p r_p, the distributed right-hand side (Eq. 3.1-3.3);
+//   * s_u = r_u - B^T e_p, the back-substitution of the block-triangular
+//     solve with P = [A B^T; 0 H_p] (Eq. 3.5).
+#include "bah_internal.cuh"
+
+namespace bah {
+
+template <class V>
+__device__ __forceinline__ double2 ld64(const V* p, int idx) {
+    V v = p[idx];
+    return make_double2((double)v.x, (double)v.y);
+}
+
+// ---------------------------------------------------------------------------
+// y = H x  (b == nullptr)  or  y = b - H x,  one cell per thread.
+// conj != 0 applies H^H = conj(H) (H is complex symmetric).
+// ---------------------------------------------------------------------------
+template <class Vin>
+__global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __restrict__ x, double2* __restrict__ y,
+                                                       const double2* __restrict__ b, int conj) {
+    const int n1 = c.n1, n2 = c.n2, np = n1 * n2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np) return;
+    const int i = t % n1, j = t / n1;
+    const Vin* x1 = x;
+    const Vin* x2 = x + np;
+    const Vin* xp = x + 2 * np;
+    const double2 z = make_double2(0.0, 0.0);
+    auto U1 = [&](int ii, int jj) { return (ii >= 1 && ii < n1 && jj >= 0 && jj < n2) ? ld64(x1, jj * n1 + ii) : z; };
+    auto U2 = [&](int ii, int jj) { return (ii >= 0 && ii < n1 && jj >= 1 && jj < n2) ? ld64(x2, jj * n1 + ii) : z; };
+    const double2 p = ld64(xp, t);
+    const double sg = conj ? -1.0 : 1.0;
+
+    // u1 row: grad_h^T A_e(mu) grad_h - omega^2 M on x_1-faces, plus (grad_h p)_1
+    double2 y1 = z, y2 = z;
+    if (i >= 1) {
+        const double2 u = U1(i, j);
+        double2 d = c.d1[t];
+        d.y *= sg;
+        double2 a = cmul(d, u);
+        const double2 uw = U1(i - 1, j), ue = U1(i + 1, j), us = U1(i, j - 1), un = U1(i, j + 1);
+        const double kw = c.cx[t - 1], ke = c.cx[t];
+        const double ks = c.nz[t], kn = (j + 1 < n2) ? c.nz[t + n1] : 0.0;
+        a.x -= kw * uw.x + ke * ue.x + ks * us.x + kn * un.x;
+        a.y -= kw * uw.y + ke * ue.y + ks * us.y + kn * un.y;
+        const double2 pw = ld64(xp, t - 1);
+        a.x += c.ihx * (p.x - pw.x);
+        a.y += c.ihx * (p.y - pw.y);
+        y1 = a;
+    }
+    if (j >= 1) {
+        const double2 u = U2(i, j);
+        double2 d = c.d2[t];
+        d.y *= sg;
+        double2 a = cmul(d, u);
+        const double2 us = U2(i, j - 1), un = U2(i, j + 1), uw = U2(i - 1, j), ue = U2(i + 1, j);
+        const double ks = c.cz[t - n1], kn = c.cz[t];
+        const double kw = c.nx[t], ke = (i + 1 < n1) ? c.nx[t + 1] : 0.0;
+        a.x -= ks * us.x + kn * un.x + kw * uw.x + ke * ue.x;
+        a.y -= ks * us.y + kn * un.y + kw * uw.y + ke * ue.y;
+        const double2 ps = ld64(xp, t - n1);
+        a.x += c.ihz * (p.x - ps.x);
+        a.y += c.ihz * (p.y - ps.y);
+        y2 = a;
+    }
+    // p row: B u - C p,  B = grad_h^T (minus divergence)
+    const double2 u1c = U1(i, j), u1e = U1(i + 1, j), u2c = U2(i, j), u2n = U2(i, j + 1);
+    const double ci = c.cinv[t];
+    double2 yp;
+    yp.x = c.ihx * (u1c.x - u1e.x) + c.ihz * (u2c.x - u2n.x) - ci * p.x;
+    yp.y = c.ihx * (u1c.y - u1e.y) + c.ihz * (u2c.y - u2n.y) - ci * p.y;
+    if (b) {
+        if (i >= 1) y1 = csub(b[t], y1);
+        if (j >= 1) y2 = csub(b[np + t], y2);
+        yp = csub(b[2 * np + t], yp);
+    }
+    y[t] = y1;
+    y[np + t] = y2;
+    y[2 * np + t] = yp;
+}
+
+template <class Vin>
+void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st) {
+    int np = c.n1 * c.n2;
+    k_elastic_apply<Vin><<<(np + 255) / 256, 256, 0, st>>>(c, x, y, b, conj);
+}
+template void launch_elastic_apply<double2>(const OpCoef&, const double2*, double2*, const double2*, int, cudaStream_t);
+template void launch_elastic_apply<float2>(const OpCoef&, const float2*, double2*, const double2*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// t_p = B r_u - A_p r_p   (r in FP64, t_p in the preconditioner's precision)
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) k_distributor(int n1, int n2, typename Prec<MODE>::R ihx,
+                                                     typename Prec<MODE>::R ihz,
+                                                     Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> f,
+                                                     const double2* __restrict__ r, typename Prec<MODE>::V* __restrict__ tp) {
+    using V = typename Prec<MODE>::V;
+    using R = typename Prec<MODE>::R;
+    const int np = n1 * n2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np) return;
+    const int i = t % n1, j = t / n1;
+    auto L = [&](int idx) { double2 v = r[idx]; return cmk<V>((R)v.x, (R)v.y); };
+    const V z = czero<V>();
+    const V u1c = (i >= 1) ? L(t) : z;
+    const V u1e = (i + 1 < n1) ? L(t + 1) : z;
+    const V u2c = (j >= 1) ? L(np + t) : z;
+    const V u2n = (j + 1 < n2) ? L(np + t + n1) : z;
+    // B r_u
+    V acc = cmk<V>(ihx * (u1c.x - u1e.x) + ihz * (u2c.x - u2n.x), ihx * (u1c.y - u1e.y) + ihz * (u2c.y - u2n.y));
+    // - A_p r_p,  A_p = B B^T diag(mu) - omega^2 diag(rho~): off-diagonal (c, n) = -mu_n / h^2
+    const V pc = L(2 * np + t);
+    V ap = cmul(ldc(f.dAp[t]), pc);
+    if (i >= 1) { R k = ldr(f.cx[t - 1]); V q = L(2 * np + t - 1); ap.x -= k * q.x; ap.y -= k * q.y; }
+    if (i + 1 < n1) { R k = ldr(f.cx[t + 1]); V q = L(2 * np + t + 1); ap.x -= k * q.x; ap.y -= k * q.y; }
+    if (j >= 1) { R k = ldr(f.cz[t - n1]); V q = L(2 * np + t - n1); ap.x -= k * q.x; ap.y -= k * q.y; }
+    if (j + 1 < n2) { R k = ldr(f.cz[t + n1]); V q = L(2 * np + t + n1); ap.x -= k * q.x; ap.y -= k * q.y; }
+    tp[t] = csub(acc, ap);
+}
+
+template <int MODE>
+void launch_distributor(int n1, int n2, double ihx, double ihz,
+                        const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5, const double2* r,
+                        typename Prec<MODE>::V* tp, cudaStream_t st) {
+    int np = n1 * n2;
+    k_distributor<MODE><<<(np + 255) / 256, 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
+                                                           (typename Prec<MODE>::R)ihz, f5, r, tp);
+}
+template void launch_distributor<BAH_FP64>(int, int, double, double, const Fine5<double, double2>&, const double2*,
+                                           double2*, cudaStream_t);
+template void launch_distributor<BAH_MIXED>(int, int, double, double, const Fine5<__nv_bfloat16, __nv_bfloat162>&,
+                                            const double2*, float2*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// s_u = r_u - B^T e_p  (B^T = grad_h onto the interior faces)
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) k_u_rhs(int n1, int n2, typename Prec<MODE>::R ihx, typename Prec<MODE>::R ihz,
+                                               const double2* __restrict__ r, const typename Prec<MODE>::V* __restrict__ ep,
+                                               typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2) {
+    using V = typename Prec<MODE>::V;
+    using R = typename Prec<MODE>::R;
+    const int np = n1 * n2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np) return;
+    const int i = t % n1, j = t / n1;
+    const V e = ep[t];
+    V s1 = czero<V>(), s2 = czero<V>();
+    if (i >= 1) {
+        double2 rv = r[t];
+        V ew = ep[t - 1];
+        s1 = cmk<V>((R)rv.x - ihx * (e.x - ew.x), (R)rv.y - ihx * (e.y - ew.y));
+    }
+    if (j >= 1) {
+        double2 rv = r[np + t];
+        V es = ep[t - n1];
+        s2 = cmk<V>((R)rv.x - ihz * (e.x - es.x), (R)rv.y - ihz * (e.y - es.y));
+    }
+    su1[t] = s1;
+    su2[t] = s2;
+}
+
+template <int MODE>
+void launch_u_rhs(int n1, int n2, double ihx, double ihz, const double2* r, const typename Prec<MODE>::V* ep,
+                  typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st) {
+    int np = n1 * n2;
+    k_u_rhs<MODE><<<(np + 255) / 256, 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx, (typename Prec<MODE>::R)ihz,
+                                                     r, ep, su1, su2);
+}
+template void launch_u_rhs<BAH_FP64>(int, int, double, double, const double2*, const double2*, double2*, double2*,
+                                     cudaStream_t);
+template void launch_u_rhs<BAH_MIXED>(int, int, double, double, const double2*, const float2*, float2*, float2*,
+                                      cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// element-wise precision conversion
+// ---------------------------------------------------------------------------
+template <class Vin, class Vout>
+__global__ void k_convert(const Vin* __restrict__ x, Vout* __restrict__ y, size_t n) {
+    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t < n) y[t] = cconv<Vout>(x[t]);
+}
+template <class Vin, class Vout>
+void launch_convert(const Vin* x, Vout* y, size_t n, cudaStream_t st) {
+    k_convert<Vin, Vout><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n);
+}
+template void launch_convert<double2, float2>(const double2*, float2*, size_t, cudaStream_t);
+template void launch_convert<float2, double2>(const float2*, double2*, size_t, cudaStream_t);
+template void launch_convert<double2, double2>(const double2*, double2*, size_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// zero the boundary-normal (non-unknown) entries of padded vectors
+// ---------------------------------------------------------------------------
+__global__ void k_sanitize(double2* v, int n1, int n2, int nvec) {
+    const int np = n1 * n2;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= (size_t)np * nvec) return;
+    const int k = (int)(t / np), pt = (int)(t % np);
+    const int i = pt % n1, j = pt / n1;
+    double2* u = v + (size_t)k * 3 * np;
+    if (i == 0) u[pt] = make_double2(0.0, 0.0);
+    if (j == 0) u[np + pt] = make_double2(0.0, 0.0);
+}
+void launch_sanitize(double2* v, int n1, int n2, int nvec, cudaStream_t st) {
+    size_t n = (size_t)n1 * n2 * nvec;
+    k_sanitize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, n1, n2, nvec);
+}
+
+}  // namespace bah

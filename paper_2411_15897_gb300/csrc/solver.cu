@@ -1,0 +1,808 @@
+// Host side of libbah: context construction, the multigrid cycle schedule,
+// the block-acoustic preconditioner, flexible GMRES, and the C ABI of bah.h.
+//
+// The preconditioning step (Sec. 3, Eq. 3.1-3.5) is
+//     t_p = B v_u - A_p v_p;   e_p = cycle(H_p,s, t_p);
+//     s_u = v_u - B^T e_p;     e_u = cycle(A_s, s_u)   (the d blocks in one batch)
+// and FGMRES (right preconditioned, two-pass classical Gram-Schmidt, Givens
+// rotations on the device) wraps it with the FP64 operator H of Eq. 2.6.
+#include "bah_internal.cuh"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <utility>
+
+namespace bah {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+
+#define TRY(expr)                                  \
+    do {                                           \
+        int _s = (expr);                           \
+        if (_s != BAH_OK) return _s;               \
+    } while (0)
+
+static const double kAlphaByLevels[5] = {0.0, 0.0, 0.1, 0.2, 0.4};
+
+struct Ctx {
+    int dim = 2, n1 = 0, n2 = 0, np = 0;
+    double h1 = 0, h2 = 0, omega = 0, alpha = 0;
+    bah_opts o{};
+    int L = 1;
+    int mode = BAH_MIXED;
+    size_t vsz = 8;                      // bytes of one complex entry in the preconditioner's precision
+    std::vector<void*> allocs;
+
+    // FP64 coefficient arrays (cells)
+    double *cx = nullptr, *cz = nullptr, *nx = nullptr, *nz = nullptr, *wx = nullptr, *wz = nullptr, *cinv = nullptr;
+    double2 *d1 = nullptr, *d2 = nullptr, *dg[3] = {nullptr, nullptr, nullptr}, *dAp = nullptr;
+    OpCoef op{};
+    // level-0 arrays in storage precision
+    void *s_cx = nullptr, *s_cz = nullptr, *s_nx = nullptr, *s_nz = nullptr, *s_wx = nullptr, *s_wz = nullptr;
+    void *s_dg[3] = {nullptr, nullptr, nullptr}, *s_dAp = nullptr;
+    // hierarchy
+    std::vector<int> ln1, ln2;
+    std::vector<std::array<StencilF64, 3>> s64;   // FP64 stencils per level (level 0: 3x3 fine operator)
+    std::vector<std::array<void*, 3>> sst;        // storage-precision stencils, levels >= 1
+    double2* inv[3] = {nullptr, nullptr, nullptr};
+    std::vector<std::array<void*, 3>> vX, vB, vT; // multigrid vectors per level and block
+    // Krylov workspace
+    int m = 20;
+    double2 *V = nullptr, *W = nullptr, *R = nullptr, *Bs = nullptr, *X = nullptr;
+    double2 *Hm = nullptr, *h1v = nullptr, *h2v = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double2* partial = nullptr;
+    double *nrm = nullptr, *dpart = nullptr, *status = nullptr;
+    void* Z = nullptr;
+    double* hstatus = nullptr;           // pinned host mirror of status
+    void* ztmp = nullptr;                // preconditioner output in storage precision (apply hook)
+
+    // profiling: launch counts, algorithmic bytes, event timing per kernel class
+    unsigned tmask = 0;
+    long long launches = 0;
+    long long cls_launch[16] = {}, cls_calls[16] = {};
+    double cls_ms[16] = {}, cls_bytes[16] = {};
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+    std::vector<std::pair<int, size_t>> pending;
+
+    ~Ctx() {
+        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+        for (void* p : allocs) cudaFree(p);
+        if (hstatus) cudaFreeHost(hstatus);
+    }
+    int alloc(void** p, size_t bytes) {
+        *p = nullptr;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+            return BAH_ERR_OOM;
+        }
+        allocs.push_back(*p);
+        return BAH_OK;
+    }
+    template <class T> int alloc_t(T** p, size_t count) {
+        void* q;
+        int s = alloc(&q, count * sizeof(T));
+        *p = (T*)q;
+        return s;
+    }
+    size_t vec_len() const { return (size_t)3 * np; }
+};
+
+// ---------------------------------------------------------------------------
+// profiling scope: counts the kernels of one launcher call and its algorithmic
+// bytes; for timed classes brackets the launch with events on its stream
+// ---------------------------------------------------------------------------
+static void prof_flush(Ctx& c) {
+    if (c.pending.empty()) return;
+    cudaEventSynchronize(c.evpool[c.pending.back().second + 1]);
+    for (auto& pr : c.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c.evpool[pr.second], c.evpool[pr.second + 1]) == cudaSuccess)
+            c.cls_ms[pr.first] += ms;
+    }
+    cudaGetLastError();
+    c.pending.clear();
+    c.evused = 0;
+}
+
+struct Prof {
+    Ctx& c;
+    int cls;
+    cudaStream_t st;
+    double bytes;
+    int nk;
+    size_t idx = (size_t)-1;
+    Prof(Ctx& c_, int cls_, cudaStream_t st_, double bytes_, int nk_ = 1)
+        : c(c_), cls(cls_), st(st_), bytes(bytes_), nk(nk_) {
+        if (c.tmask & (1u << cls)) {
+            if (c.evused + 2 > c.evpool.size()) {
+                if (c.evpool.size() < 16384) {
+                    for (int k = 0; k < 2; ++k) {
+                        cudaEvent_t e;
+                        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+                        c.evpool.push_back(e);
+                    }
+                } else {
+                    prof_flush(c);
+                }
+            }
+            idx = c.evused;
+            c.evused += 2;
+            cudaEventRecord(c.evpool[idx], st);
+        }
+    }
+    ~Prof() {
+        if (idx != (size_t)-1) {
+            cudaEventRecord(c.evpool[idx + 1], st);
+            c.pending.emplace_back(cls, idx);
+        }
+        c.launches += nk;
+        c.cls_launch[cls] += nk;
+        c.cls_calls[cls] += 1;
+        c.cls_bytes[cls] += bytes;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// multigrid cycle over a set of blocks (Algorithm 1 applied recursively)
+// ---------------------------------------------------------------------------
+template <int MODE>
+struct MG {
+    using V = typename Prec<MODE>::V;
+    using C = typename Prec<MODE>::C;
+    using CC = typename Prec<MODE>::CC;
+
+    static Fine5<C, CC> fine5(const Ctx& c) {
+        Fine5<C, CC> f;
+        f.n1 = c.n1; f.n2 = c.n2;
+        f.cx = (const C*)c.s_cx; f.cz = (const C*)c.s_cz; f.nx = (const C*)c.s_nx; f.nz = (const C*)c.s_nz;
+        f.wx = (const C*)c.s_wx; f.wz = (const C*)c.s_wz;
+        f.dg0 = (const CC*)c.s_dg[0]; f.dg1 = (const CC*)c.s_dg[1]; f.dg2 = (const CC*)c.s_dg[2];
+        f.dAp = (const CC*)c.s_dAp;
+        return f;
+    }
+
+    static double weight(const Ctx& c, int l) {
+        int k = std::min(l, c.o.n_jacobi_w - 1);
+        return c.o.jacobi_w[k];
+    }
+
+    static LvlSet<V, CC> set(const Ctx& c, int l, int b0, int nb, V* const* xin, V* const* xout) {
+        LvlSet<V, CC> s;
+        s.nb = nb; s.n1 = c.ln1[l]; s.n2 = c.ln2[l];
+        for (int z = 0; z < nb; ++z) {
+            const int b = b0 + z;
+            auto& B = s.blk[z];
+            B.type = b;
+            B.S = l > 0 ? (const CC*)c.sst[l][b] : nullptr;
+            B.rx = c.s64[l][b].rx; B.rz = c.s64[l][b].rz;
+            B.b = (const V*)c.vB[l][b];
+            B.xin = xin ? xin[z] : nullptr;
+            B.xout = xout[z];
+        }
+        return s;
+    }
+
+    // algorithmic bytes of one sweep-type launch on level l for blocks [b0, b0+nb)
+    static double coef_bytes(const Ctx& c, int l, int b0, int nb) {
+        const double cs = sizeof(C), ccs = sizeof(CC);
+        const double npl = (double)c.ln1[l] * c.ln2[l];
+        double t = 0;
+        for (int b = b0; b < b0 + nb; ++b) {
+            if (l == 0) t += npl * (((b == 2 && c.h1 == c.h2) ? 1.0 : 2.0) * cs + ccs);
+            else t += npl * ccs * (2 * c.s64[l][b].rx + 1) * (2 * c.s64[l][b].rz + 1);
+        }
+        return t;
+    }
+
+    // Result of one cycle with zero initial guess on level l for blocks
+    // [b0, b0+nb): right-hand side in vB[l][b], result written to out[z].
+    static void cycle(Ctx& c, int l, int b0, int nb, V* const* out, cudaStream_t st) {
+        const size_t npl = (size_t)c.ln1[l] * c.ln2[l];
+        const double vs = sizeof(V), ccs = sizeof(CC);
+        if (l == c.L - 1) {
+            const double2* inv[3];
+            const V* bb[3];
+            V* xx[3];
+            for (int z = 0; z < nb; ++z) { inv[z] = c.inv[b0 + z]; bb[z] = (const V*)c.vB[l][b0 + z]; xx[z] = out[z]; }
+            Prof pr(c, BAH_K_COARSE, st, nb * ((double)npl * npl * 16.0 + 2.0 * npl * vs));
+            launch_coarse_apply<MODE>(nb, (int)npl, inv, bb, xx, st);
+            return;
+        }
+        Fine5<C, CC> f5 = fine5(c);
+        const Fine5<C, CC>* pf5 = l == 0 ? &f5 : nullptr;
+        const double w = weight(c, l);
+        const double cb_ = coef_bytes(c, l, b0, nb);
+        const double sweep = cb_ + 3.0 * vs * npl * nb;
+        V* cur[3];
+        V* oth[3];
+        for (int z = 0; z < nb; ++z) { cur[z] = out[z]; oth[z] = (V*)c.vT[l][b0 + z]; }
+        auto swap_cur = [&]() { for (int z = 0; z < nb; ++z) std::swap(cur[z], oth[z]); };
+        // pre-relaxation
+        if (c.o.nu_pre >= 1) {
+            {
+                Prof pr(c, BAH_K_JACOBI, st, nb * npl * (2.0 * vs + ccs));
+                launch_jacobi<MODE>(set(c, l, b0, nb, nullptr, cur), pf5, w, 1, st);
+            }
+            for (int s = 1; s < c.o.nu_pre; ++s) {
+                Prof pr(c, BAH_K_JACOBI, st, sweep);
+                launch_jacobi<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, 0, st);
+                swap_cur();
+            }
+        } else {
+            Prof pr(c, BAH_K_SMALL, st, nb * npl * vs, 0);
+            for (int z = 0; z < nb; ++z) cudaMemsetAsync(cur[z], 0, npl * sizeof(V), st);
+        }
+        // residual and restriction
+        auto rs = set(c, l, b0, nb, cur, oth);
+        {
+            Prof pr(c, BAH_K_RESIDUAL, st, sweep);
+            launch_residual<MODE>(rs, pf5, st);
+        }
+        V* cb[3];
+        V* cx[3];
+        for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
+        {
+            Prof pr(c, BAH_K_RESTRICT, st, nb * npl * vs * 1.25);
+            launch_restrict<MODE>(rs, cb, c.o.intergrid, st);
+        }
+        // coarse-grid correction
+        cycle(c, l + 1, b0, nb, cx, st);
+        {
+            Prof pr(c, BAH_K_PROLONG, st, nb * npl * vs * 2.25);
+            launch_prolong_add<MODE>(set(c, l, b0, nb, nullptr, cur), cx, st);
+        }
+        // post-relaxation
+        for (int s = 0; s < c.o.nu_post; ++s) {
+            Prof pr(c, BAH_K_JACOBI, st, sweep);
+            launch_jacobi<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, 0, st);
+            swap_cur();
+        }
+        for (int z = 0; z < nb; ++z)
+            if (cur[z] != out[z]) {
+                Prof pr(c, BAH_K_SMALL, st, 2.0 * npl * vs, 0);
+                cudaMemcpyAsync(out[z], cur[z], npl * sizeof(V), cudaMemcpyDeviceToDevice, st);
+            }
+    }
+
+    // z = P^{-1} D r  (r FP64 padded vector, z storage precision padded vector)
+    static void precond(Ctx& c, const double2* r, V* z, cudaStream_t st) {
+        const int np = c.np;
+        const double vs = sizeof(V);
+        Fine5<C, CC> f5 = fine5(c);
+        {
+            Prof pr(c, BAH_K_DISTRIB, st, (double)np * (48.0 + sizeof(C) + sizeof(CC) + vs));
+            launch_distributor<MODE>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, f5, r, (V*)c.vB[0][2], st);
+        }
+        V* outp[1] = {z + 2 * (size_t)np};
+        cycle(c, 0, 2, 1, outp, st);
+        {
+            Prof pr(c, BAH_K_URHS, st, (double)np * (32.0 + 3.0 * vs));
+            launch_u_rhs<MODE>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, r, z + 2 * (size_t)np, (V*)c.vB[0][0],
+                               (V*)c.vB[0][1], st);
+        }
+        V* outu[2] = {z, z + (size_t)np};
+        cycle(c, 0, 0, 2, outu, st);
+    }
+};
+
+static void precond_any(Ctx& c, const double2* r, void* z, cudaStream_t st) {
+    if (c.mode == BAH_MIXED) MG<BAH_MIXED>::precond(c, r, (float2*)z, st);
+    else MG<BAH_FP64>::precond(c, r, (double2*)z, st);
+}
+// algorithmic bytes of one operator apply: input (3 components), FP64
+// output, coefficients cx, nx (z-aliases when h1 == h2), d1, d2, 1/(lambda+mu)
+static double op_bytes(const Ctx& c, double in_bytes, bool residual) {
+    const double coef = (c.h1 == c.h2 ? 16.0 : 32.0) + 32.0 + 8.0;
+    return (double)c.np * (3.0 * in_bytes + 48.0 + coef + (residual ? 48.0 : 0.0));
+}
+static void op_apply_z(Ctx& c, const void* z, double2* y, cudaStream_t st) {
+    Prof pr(c, BAH_K_OPERATOR, st, op_bytes(c, (double)c.vsz, false));
+    if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, y, nullptr, 0, st);
+    else launch_elastic_apply<double2>(c.op, (const double2*)z, y, nullptr, 0, st);
+}
+
+// ---------------------------------------------------------------------------
+// context construction
+// ---------------------------------------------------------------------------
+static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
+    const int np = c.np;
+    const size_t cs = c.mode == BAH_MIXED ? 2 : 8, ccs = c.mode == BAH_MIXED ? 4 : 16;
+    // medium upload
+    double *lam, *mu, *rho, *gam;
+    TRY(c.alloc_t(&lam, np)); TRY(c.alloc_t(&mu, np)); TRY(c.alloc_t(&rho, np)); TRY(c.alloc_t(&gam, np));
+    BAH_CUDA_TRY(cudaMemcpyAsync(lam, med->lambda, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(mu, med->mu, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(rho, med->rho, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(gam, med->gamma, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    TRY(c.alloc_t(&c.cx, np)); TRY(c.alloc_t(&c.cz, np)); TRY(c.alloc_t(&c.nx, np)); TRY(c.alloc_t(&c.nz, np));
+    TRY(c.alloc_t(&c.wx, np)); TRY(c.alloc_t(&c.wz, np)); TRY(c.alloc_t(&c.cinv, np));
+    TRY(c.alloc_t(&c.d1, np)); TRY(c.alloc_t(&c.d2, np)); TRY(c.alloc_t(&c.dAp, np));
+    for (int b = 0; b < 3; ++b) TRY(c.alloc_t(&c.dg[b], np));
+    launch_medium_prep(c.n1, c.n2, c.h1, c.h2, c.omega, c.alpha, lam, mu, rho, gam, c.cx, c.cz, c.nx, c.nz, c.wx,
+                       c.wz, c.d1, c.d2, c.cinv, c.dg[0], c.dg[1], c.dg[2], c.dAp, st);
+    BAH_CUDA_TRY(cudaGetLastError());
+    c.op = OpCoef{c.n1, c.n2, c.cx, c.cz, c.nx, c.nz, c.d1, c.d2, c.cinv, 1.0 / c.h1, 1.0 / c.h2};
+
+    // level-0 coefficients in storage precision
+    const bool iso = c.h1 == c.h2;
+    TRY(c.alloc(&c.s_cx, np * cs)); TRY(c.alloc(&c.s_nx, np * cs)); TRY(c.alloc(&c.s_wx, np * cs));
+    launch_round_real(c.cx, c.s_cx, np, c.mode, st);
+    launch_round_real(c.nx, c.s_nx, np, c.mode, st);
+    launch_round_real(c.wx, c.s_wx, np, c.mode, st);
+    if (iso) {
+        c.s_cz = c.s_cx; c.s_nz = c.s_nx; c.s_wz = c.s_wx;
+    } else {
+        TRY(c.alloc(&c.s_cz, np * cs)); TRY(c.alloc(&c.s_nz, np * cs)); TRY(c.alloc(&c.s_wz, np * cs));
+        launch_round_real(c.cz, c.s_cz, np, c.mode, st);
+        launch_round_real(c.nz, c.s_nz, np, c.mode, st);
+        launch_round_real(c.wz, c.s_wz, np, c.mode, st);
+    }
+    for (int b = 0; b < 3; ++b) {
+        TRY(c.alloc(&c.s_dg[b], np * ccs));
+        launch_round_cplx(c.dg[b], c.s_dg[b], np, c.mode, st);
+    }
+    TRY(c.alloc(&c.s_dAp, np * ccs));
+    launch_round_cplx(c.dAp, c.s_dAp, np, c.mode, st);
+
+    // hierarchy: level grids, FP64 stencils, Galerkin products, storage copies
+    c.ln1.assign(c.L, 0); c.ln2.assign(c.L, 0);
+    c.s64.assign(c.L, {}); c.sst.assign(c.L, {nullptr, nullptr, nullptr});
+    for (int l = 0; l < c.L; ++l) { c.ln1[l] = c.n1 >> l; c.ln2[l] = c.n2 >> l; }
+    for (int b = 0; b < 3; ++b) {
+        StencilF64& s0 = c.s64[0][b];
+        s0.rx = 1; s0.rz = 1; s0.n1 = c.n1; s0.n2 = c.n2;
+        TRY(c.alloc_t(&s0.S, (size_t)9 * np));
+        launch_fine_stencil(b, c.n1, c.n2, c.cx, c.cz, c.nx, c.nz, c.wx, c.wz, c.dg[b], s0.S, st);
+        for (int l = 1; l < c.L; ++l) {
+            StencilF64& s = c.s64[l][b];
+            const bool bil = c.o.intergrid == BAH_INTERGRID_BILINEAR;
+            s.rx = (b == 0) ? 1 : (bil ? 2 : 1);
+            s.rz = (b == 1) ? 1 : (bil ? 2 : 1);
+            s.n1 = c.ln1[l]; s.n2 = c.ln2[l];
+            const size_t ns = (size_t)(2 * s.rx + 1) * (2 * s.rz + 1) * s.n1 * s.n2;
+            TRY(c.alloc_t(&s.S, ns));
+            launch_galerkin(b, c.o.intergrid, c.s64[l - 1][b], s, st);
+            if (l < c.L - 1) {
+                TRY(c.alloc(&c.sst[l][b], ns * ccs));
+                launch_round_cplx(s.S, c.sst[l][b], ns, c.mode, st);
+            }
+        }
+    }
+    BAH_CUDA_TRY(cudaGetLastError());
+    // coarsest-level inverses
+    {
+        const int nc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
+        void* work;
+        int* flag;
+        TRY(c.alloc(&work, ((size_t)nc * nc + nc) * sizeof(double2)));
+        TRY(c.alloc_t(&flag, 1));
+        for (int b = 0; b < 3; ++b) {
+            TRY(c.alloc_t(&c.inv[b], (size_t)nc * nc));
+            TRY(coarse_invert(b, c.s64[c.L - 1][b], c.inv[b], (double2*)work, flag, st));
+        }
+    }
+    // multigrid vectors
+    c.vX.assign(c.L, {nullptr, nullptr, nullptr});
+    c.vB = c.vX; c.vT = c.vX;
+    for (int l = 0; l < c.L; ++l)
+        for (int b = 0; b < 3; ++b) {
+            const size_t npl = (size_t)c.ln1[l] * c.ln2[l];
+            TRY(c.alloc(&c.vX[l][b], npl * c.vsz));
+            TRY(c.alloc(&c.vB[l][b], npl * c.vsz));
+            TRY(c.alloc(&c.vT[l][b], npl * c.vsz));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.vX[l][b], 0, npl * c.vsz, st));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.vB[l][b], 0, npl * c.vsz, st));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.vT[l][b], 0, npl * c.vsz, st));
+        }
+    // Krylov workspace
+    const size_t n = c.vec_len();
+    const int m = c.m;
+    TRY(c.alloc_t(&c.V, n * (m + 1)));
+    TRY(c.alloc(&c.Z, n * m * c.vsz));
+    TRY(c.alloc_t(&c.W, n)); TRY(c.alloc_t(&c.R, n)); TRY(c.alloc_t(&c.Bs, n)); TRY(c.alloc_t(&c.X, n));
+    TRY(c.alloc(&c.ztmp, n * c.vsz));
+    TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m));
+    TRY(c.alloc_t(&c.h1v, m + 1)); TRY(c.alloc_t(&c.h2v, m + 1));
+    TRY(c.alloc_t(&c.cs, m + 1)); TRY(c.alloc_t(&c.sn, m + 1)); TRY(c.alloc_t(&c.g, m + 2)); TRY(c.alloc_t(&c.y, m + 1));
+    TRY(c.alloc_t(&c.partial, (size_t)(m + 1) * RED_CTAS));
+    TRY(c.alloc_t(&c.dpart, RED_CTAS));
+    TRY(c.alloc_t(&c.nrm, 4));
+    TRY(c.alloc_t(&c.status, 4));
+    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hstatus, 8 * sizeof(double)));
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    // the raw medium is no longer needed
+    return BAH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES for one right-hand side (device vectors b, x; b is sanitised)
+// ---------------------------------------------------------------------------
+static int read_status(Ctx& c, cudaStream_t st) {
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.hstatus, c.status, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    return BAH_OK;
+}
+static int read_scalar(Ctx& c, const double* d, double* h, cudaStream_t st) {
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.hstatus + 4, d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    *h = c.hstatus[4];
+    return BAH_OK;
+}
+
+static int fgmres_one(Ctx& c, const double2* b, double2* x, double rtol, bah_stats* out, cudaStream_t st) {
+    const size_t n = c.vec_len();
+    const int m = c.m;
+    bah_stats s{};
+    s.status = BAH_OK;
+    {
+        Prof pr(c, BAH_K_NORM, st, n * 16.0, 2);
+        launch_norm2(b, n, c.dpart, c.nrm + 1, st);
+    }
+    double nb;
+    TRY(read_scalar(c, c.nrm + 1, &nb, st));
+    BAH_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
+    if (!(nb > 0.0)) {
+        s.relres_true = 0.0;
+        if (out) *out = s;
+        return std::isfinite(nb) ? BAH_OK : BAH_ERR_NONFINITE;
+    }
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.R, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    double beta = nb;
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.nrm, c.nrm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int total = 0;
+    double est = 1.0;
+    while (beta > rtol * nb && total < c.o.maxit) {
+        // v_0 = r / beta, g = beta e_1
+        {
+            Prof pr(c, BAH_K_SMALL, st, n * 32.0, 2);
+            launch_scale_copy(c.R, c.nrm, c.V, n, 1, st);
+            launch_init_arnoldi(c.nrm, c.g, m, c.status, st);
+        }
+        int jdone = 0;
+        bool stop = false;
+        for (int j = 0; j < m && total < c.o.maxit; ++j) {
+            double2* vj = c.V + (size_t)j * n;
+            void* zj = (char*)c.Z + (size_t)j * n * c.vsz;
+            precond_any(c, vj, zj, st);
+            op_apply_z(c, zj, c.W, st);
+            // two-pass classical Gram-Schmidt
+            const double k1 = j + 1;
+            {
+                Prof pr(c, BAH_K_DOT, st, (k1 + 1) * n * 16.0, 2);
+                launch_multi_dot(c.V, n, j + 1, c.W, n, c.partial, c.h1v, st);
+            }
+            {
+                Prof pr(c, BAH_K_AXPY, st, (k1 + 2) * n * 16.0);
+                launch_multi_axpy_sub(c.V, n, j + 1, c.h1v, c.W, n, st);
+            }
+            {
+                Prof pr(c, BAH_K_DOT, st, (k1 + 1) * n * 16.0, 2);
+                launch_multi_dot(c.V, n, j + 1, c.W, n, c.partial, c.h2v, st);
+            }
+            {
+                Prof pr(c, BAH_K_AXPY, st, (k1 + 2) * n * 16.0);
+                launch_multi_axpy_sub(c.V, n, j + 1, c.h2v, c.W, n, st);
+            }
+            {
+                Prof pr(c, BAH_K_NORM, st, n * 16.0, 2);
+                launch_norm2(c.W, n, c.dpart, c.nrm + 2, st);
+            }
+            {
+                Prof pr(c, BAH_K_SMALL, st, n * 32.0, 2);
+                launch_arnoldi_givens(c.Hm + (size_t)j * (m + 1), c.h1v, c.h2v, c.nrm + 2, j, c.cs, c.sn, c.g,
+                                      c.status, st);
+                launch_scale_copy(c.W, c.nrm + 2, c.V + (size_t)(j + 1) * n, n, 1, st);
+            }
+            BAH_CUDA_TRY(cudaGetLastError());
+            ++total;
+            jdone = j + 1;
+            TRY(read_status(c, st));
+            est = c.hstatus[0] / nb;
+            if (c.hstatus[2] != 0.0 || !std::isfinite(est)) { s.status = BAH_ERR_NONFINITE; stop = true; break; }
+            if (est <= rtol) break;
+            if (c.hstatus[1] <= 1e-14 * nb) break;     // (lucky) breakdown: the Krylov space is invariant
+        }
+        if (s.status == BAH_ERR_NONFINITE) {
+            // keep the last finite iterate in x
+            break;
+        }
+        {
+            Prof pr(c, BAH_K_SMALL, st, 0.0);
+            launch_triangular_solve(c.Hm, m + 1, c.g, jdone, c.y, st);
+        }
+        {
+            Prof pr(c, BAH_K_UPDATE, st, (double)jdone * n * c.vsz + 32.0 * n);
+            if (c.mode == BAH_MIXED) launch_update_x<float2>((const float2*)c.Z, n, jdone, c.y, x, n, st);
+            else launch_update_x<double2>((const double2*)c.Z, n, jdone, c.y, x, n, st);
+        }
+        // true residual in FP64
+        {
+            Prof pr(c, BAH_K_OPERATOR, st, op_bytes(c, 16.0, true));
+            launch_elastic_apply<double2>(c.op, x, c.R, b, 0, st);
+        }
+        {
+            Prof pr(c, BAH_K_NORM, st, n * 16.0, 2);
+            launch_norm2(c.R, n, c.dpart, c.nrm, st);
+        }
+        TRY(read_scalar(c, c.nrm, &beta, st));
+        s.restarts++;
+        if (!std::isfinite(beta)) { s.status = BAH_ERR_NONFINITE; break; }
+        if (stop) break;
+    }
+    s.iters = total;
+    s.relres_true = beta / nb;
+    s.relres_est = est;
+    if (s.status == BAH_OK && !(s.relres_true <= rtol)) s.status = BAH_ERR_NOT_CONVERGED;
+    if (out) *out = s;
+    return s.status;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace bah
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace bah;
+
+struct bah_ctx {
+    Ctx c;
+};
+
+extern "C" {
+
+void bah_default_opts(bah_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = BAH_MIXED;
+    o->levels = 0;
+    o->max_coarse_cells = 256;
+    o->cycle = BAH_CYCLE_V;
+    o->nu_pre = 1;
+    o->nu_post = 2;
+    o->jacobi_w[0] = 0.8; o->jacobi_w[1] = 0.8; o->jacobi_w[2] = 0.3;
+    o->n_jacobi_w = 3;
+    o->shift_alpha = -1.0;
+    o->intergrid = BAH_INTERGRID_BILINEAR;
+    o->restart = 20;
+    o->maxit = 5000;
+}
+
+const char* bah_status_string(int s) {
+    switch (s) {
+        case BAH_OK: return "BAH_OK";
+        case BAH_ERR_ARG: return "BAH_ERR_ARG";
+        case BAH_ERR_OOM: return "BAH_ERR_OOM";
+        case BAH_ERR_CUDA: return "BAH_ERR_CUDA";
+        case BAH_ERR_NOT_CONVERGED: return "BAH_ERR_NOT_CONVERGED";
+        case BAH_ERR_NONFINITE: return "BAH_ERR_NONFINITE";
+        case BAH_ERR_UNSUPPORTED: return "BAH_ERR_UNSUPPORTED";
+        default: return "BAH_ERR_UNKNOWN";
+    }
+}
+
+const char* bah_last_error(void) { return g_err.c_str(); }
+
+int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts, bah_ctx** out) {
+    if (!out) { set_error("out is NULL"); return BAH_ERR_ARG; }
+    *out = nullptr;
+    g_err.clear();
+    if (!grid || !med) { set_error("grid or medium is NULL"); return BAH_ERR_ARG; }
+    if (grid->dim == 3) { set_error("3-D grids are not implemented in this build"); return BAH_ERR_UNSUPPORTED; }
+    if (grid->dim != 2) { set_error("dim must be 2"); return BAH_ERR_ARG; }
+    if (!med->lambda || !med->mu || !med->rho || !med->gamma) { set_error("medium array is NULL"); return BAH_ERR_ARG; }
+    if (!(med->omega > 0.0)) { set_error("omega must be > 0"); return BAH_ERR_ARG; }
+    if (grid->n[0] < 4 || grid->n[1] < 4 || !(grid->h[0] > 0.0) || !(grid->h[1] > 0.0)) {
+        set_error("need n >= 4 cells per axis and h > 0");
+        return BAH_ERR_ARG;
+    }
+    bah_opts o;
+    if (opts) o = *opts; else bah_default_opts(&o);
+    if (o.precision != BAH_FP64 && o.precision != BAH_MIXED) { set_error("bad precision"); return BAH_ERR_ARG; }
+    if (o.restart < 1 || o.restart > 64) { set_error("restart must be in 1..64"); return BAH_ERR_ARG; }
+    if (o.maxit < 1) { set_error("maxit must be >= 1"); return BAH_ERR_ARG; }
+    if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre > 8 || o.nu_post > 8) { set_error("bad nu"); return BAH_ERR_ARG; }
+    if (o.n_jacobi_w < 1 || o.n_jacobi_w > 8) { set_error("n_jacobi_w must be in 1..8"); return BAH_ERR_ARG; }
+    if (o.intergrid != BAH_INTERGRID_BILINEAR && o.intergrid != BAH_INTERGRID_MIXED) {
+        set_error("bad intergrid");
+        return BAH_ERR_ARG;
+    }
+    if (o.cycle == BAH_CYCLE_W) { set_error("W-cycles are not implemented in this build"); return BAH_ERR_UNSUPPORTED; }
+    if (o.cycle != BAH_CYCLE_V) { set_error("bad cycle"); return BAH_ERR_ARG; }
+
+    bah_ctx* h = new (std::nothrow) bah_ctx();
+    if (!h) { set_error("host allocation failed"); return BAH_ERR_OOM; }
+    Ctx& c = h->c;
+    c.dim = 2; c.n1 = grid->n[0]; c.n2 = grid->n[1]; c.np = c.n1 * c.n2;
+    c.h1 = grid->h[0]; c.h2 = grid->h[1]; c.omega = med->omega;
+    c.o = o;
+    c.mode = o.precision;
+    c.vsz = c.mode == BAH_MIXED ? sizeof(float2) : sizeof(double2);
+    c.m = o.restart;
+    // levels
+    int L = 1;
+    {
+        int a = c.n1, b = c.n2;
+        if (o.levels > 0) {
+            for (int l = 1; l < o.levels; ++l) {
+                if (a % 2 || b % 2 || a / 2 < 2 || b / 2 < 2) {
+                    delete h;
+                    set_error("grid cannot be coarsened to the requested number of levels");
+                    return BAH_ERR_ARG;
+                }
+                a /= 2; b /= 2; ++L;
+            }
+        } else {
+            const int maxc = o.max_coarse_cells > 0 ? o.max_coarse_cells : 256;
+            while ((long long)a * b > maxc && a % 2 == 0 && b % 2 == 0 && a / 2 >= 2 && b / 2 >= 2) {
+                a /= 2; b /= 2; ++L;
+            }
+        }
+        if ((long long)a * b > 4096) {
+            delete h;
+            set_error("coarsest level larger than 4096 cells; use more levels");
+            return BAH_ERR_ARG;
+        }
+    }
+    c.L = L;
+    c.alpha = o.shift_alpha >= 0.0 ? o.shift_alpha : (L < 5 ? kAlphaByLevels[L] : 0.5);
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        set_error("cudaStreamCreate failed");
+        return BAH_ERR_CUDA;
+    }
+    int s = build(c, med, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (s != BAH_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return BAH_OK;
+}
+
+void bah_destroy(bah_ctx* h) { delete h; }
+
+int bah_sizes(const bah_ctx* h, long long* vector_len, int* levels) {
+    if (!h) { set_error("ctx is NULL"); return BAH_ERR_ARG; }
+    if (vector_len) *vector_len = (long long)h->c.vec_len();
+    if (levels) *levels = h->c.L;
+    return BAH_OK;
+}
+
+int bah_apply_operator(bah_ctx* h, const void* x, void* y, int nrhs, int conj, void* stream) {
+    if (!h || !x || !y || nrhs < 0) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = c.vec_len();
+    for (int k = 0; k < nrhs; ++k)
+        launch_elastic_apply<double2>(c.op, (const double2*)x + k * n, (double2*)y + k * n, nullptr, conj ? 1 : 0, st);
+    BAH_CUDA_TRY(cudaGetLastError());
+    return BAH_OK;
+}
+
+int bah_apply_preconditioner(bah_ctx* h, const void* r, void* z, int nrhs, void* stream) {
+    if (!h || !r || !z || nrhs < 0) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = c.vec_len();
+    for (int k = 0; k < nrhs; ++k) {
+        const double2* rk = (const double2*)r + k * n;
+        double2* zk = (double2*)z + k * n;
+        if (c.mode == BAH_MIXED) {
+            precond_any(c, rk, c.ztmp, st);
+            launch_convert<float2, double2>((const float2*)c.ztmp, zk, n, st);
+        } else {
+            precond_any(c, rk, zk, st);
+        }
+    }
+    BAH_CUDA_TRY(cudaGetLastError());
+    return BAH_OK;
+}
+
+int bah_block_cycle(bah_ctx* h, int block, const void* b, void* x, void* stream) {
+    if (!h || !b || !x || block < 0 || block > h->c.dim) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t np = c.np;
+    if (c.mode == BAH_MIXED) {
+        launch_convert<double2, float2>((const double2*)b, (float2*)c.vB[0][block], np, st);
+        float2* o[1] = {(float2*)c.ztmp};
+        MG<BAH_MIXED>::cycle(c, 0, block, 1, o, st);
+        launch_convert<float2, double2>((const float2*)c.ztmp, (double2*)x, np, st);
+    } else {
+        BAH_CUDA_TRY(cudaMemcpyAsync(c.vB[0][block], b, np * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        double2* o[1] = {(double2*)x};
+        MG<BAH_FP64>::cycle(c, 0, block, 1, o, st);
+    }
+    BAH_CUDA_TRY(cudaGetLastError());
+    return BAH_OK;
+}
+
+int bah_level_stencil(const bah_ctx* h, int block, int level, double* out, int* rx, int* rz, int* n1, int* n2) {
+    if (!h || block < 0 || block > h->c.dim || level < 0 || level >= h->c.L) { set_error("bad argument"); return BAH_ERR_ARG; }
+    const StencilF64& s = h->c.s64[level][block];
+    if (rx) *rx = s.rx;
+    if (rz) *rz = s.rz;
+    if (n1) *n1 = s.n1;
+    if (n2) *n2 = s.n2;
+    if (out) {
+        const size_t cnt = (size_t)(2 * s.rx + 1) * (2 * s.rz + 1) * s.n1 * s.n2;
+        BAH_CUDA_TRY(cudaMemcpy(out, s.S, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+    }
+    return BAH_OK;
+}
+
+int bah_profile_control(bah_ctx* h, unsigned mask, int reset) {
+    if (!h) { set_error("ctx is NULL"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    prof_flush(c);
+    c.tmask = mask;
+    if (reset) {
+        c.launches = 0;
+        for (int k = 0; k < 16; ++k) { c.cls_launch[k] = 0; c.cls_calls[k] = 0; c.cls_ms[k] = 0; c.cls_bytes[k] = 0; }
+    }
+    return BAH_OK;
+}
+
+int bah_profile_read(bah_ctx* h, bah_profile* out) {
+    if (!h || !out) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    prof_flush(c);
+    out->launches = c.launches;
+    for (int k = 0; k < 16; ++k) {
+        out->class_launches[k] = c.cls_launch[k];
+        out->class_calls[k] = c.cls_calls[k];
+        out->class_ms[k] = c.cls_ms[k];
+        out->class_bytes[k] = c.cls_bytes[k];
+    }
+    return BAH_OK;
+}
+
+int bah_solve(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_stats* stats, void* stream) {
+    if (!h || !b || !x || nrhs < 0 || !(rtol > 0.0)) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = c.vec_len();
+    const bool dev_b = is_device_ptr(b), dev_x = is_device_ptr(x);
+    if (dev_b != dev_x) { set_error("b and x must both be device or both be host pointers"); return BAH_ERR_ARG; }
+    int first_fail = BAH_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        const double2* bk = (const double2*)b + k * n;
+        double2* xk = (double2*)x + k * n;
+        BAH_CUDA_TRY(cudaMemcpyAsync(c.Bs, bk, n * sizeof(double2),
+                                     dev_b ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        {
+            Prof pr(c, BAH_K_SMALL, st, (double)c.np * 32.0);
+            launch_sanitize(c.Bs, c.n1, c.n2, 1, st);
+        }
+        double2* xd = dev_x ? xk : c.X;
+        int s = fgmres_one(c, c.Bs, xd, rtol, stats ? stats + k : nullptr, st);
+        if (s == BAH_ERR_CUDA || s == BAH_ERR_OOM || s == BAH_ERR_ARG) return s;
+        if (!dev_x) BAH_CUDA_TRY(cudaMemcpyAsync(xk, c.X, n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        if (s != BAH_OK && first_fail == BAH_OK) first_fail = s;
+    }
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    return first_fail;
+}
+
+}  // extern "C"
