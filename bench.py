@@ -1,0 +1,387 @@
+"""Benchmark: elastic Helmholtz solves per second to relative residual 1e-6.
+
+One step = one complete FGMRES solve (block-acoustic multigrid
+preconditioner) of the 512x512 layered workload (6 layers, Vp in [1.5, 4.5],
+nu in [0.25, 0.45], rho = 0.31 Vp^0.25, 10 points per shear wavelength,
+20-cell absorbing layer, one point source at the top centre), inputs resident
+in HBM, setup excluded.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bah|reference]
+
+The main arm (bah) times the mixed-precision solve (bfloat16 coefficients,
+FP32 multigrid, FP64 FGMRES / operator / coarsest solve) and, beside it, the
+plain FP64 solve on the same GPU; the end-to-end figure is the same solve
+through the C ABI with host buffers (copies inside the timed region).  The
+reference arm (--impl reference) times the CPU oracle on the host cores.
+Under torchrun every rank solves its own copy of the workload (independent
+right-hand sides, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import math  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "elastic solves/s to rel-res 1e-6 (mixed vs FP64); stencil+V-cycle HBM GB/s"
+UNIT = "solves/s"
+WORKLOAD = ("2D 512x512 layered medium (6 layers, Vp U[1.5,4.5], nu U[0.25,0.45], rho=0.31 Vp^0.25), "
+            "10 points per shear wavelength, 20-cell absorbing layer, one top-centre point source, "
+            "FGMRES(20) to rel-res 1e-6")
+L2_FLUSH_BYTES = 512 << 20
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA/clk/SM at the 2070 MHz maximum clock (1.26 TFLOP/s)
+KERNEL_NAMES = {0: "k_elastic_apply", 1: "k_distributor", 2: "k_u_rhs", 3: "k_jacobi", 4: "k_residual",
+                5: "k_restrict", 6: "k_prolong_add", 7: "k_coarse_apply", 8: "k_multi_dot_partial",
+                9: "k_multi_axpy_sub", 10: "k_norm2_partial", 11: "k_update_x", 12: "small kernels"}
+# FP64 flops per algorithmic byte of the FP64 classes (2 flops per real FMA):
+#   dot/axpy: 8 flops per complex MAC on 16 streamed bytes; operator: ~84 flops per cell on ~200 bytes
+FP64_FLOP_PER_BYTE = {"dot": 0.5, "axpy": 0.5, "update": 8.0 / 8.0, "operator": 84.0 / 200.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bah", choices=["bah", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle FGMRES iterations per baseline sample")
+    ap.add_argument("--profile-json", default="", help="write the per-kernel-class profile here")
+    ap.add_argument("--levels", type=int, default=0)
+    ap.add_argument("--max-coarse", type=int, default=1024)
+    ap.add_argument("--restart", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_counts():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
+    if os.path.exists(path):
+        return json.load(open(path))
+    return {}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+def oracle_sample(prob, levels, alpha, restart, iters, reps=1):
+    """Oracle setup once, then ``reps`` samples of ``iters`` FGMRES iterations;
+    returns (seconds per iteration list, setup seconds)."""
+    from oracle import elastic, fgmres, precond
+    t0 = time.perf_counter()
+    S = elastic.from_problem(prob)
+    H = S.H
+    pc = precond.multigrid(S, levels, alpha, precision="mixed")
+    setup = time.perf_counter() - t0
+    b = W.padded_to_compact(W.point_source(prob), prob.n)
+    per = []
+    for _ in range(reps):
+        t1 = time.perf_counter()
+        fgmres.fgmres(lambda v: H @ v, b, pc.apply, restart=restart, rtol=1e-30, maxit=iters)
+        per.append((time.perf_counter() - t1) / iters)
+    return per, setup
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    prob = W.config(args.config)
+    counts = oracle_counts().get(args.config)
+    levels = counts["levels"] if counts else 6
+    alpha = counts["alpha"] if counts else 0.5
+    its = counts["iters"] if counts else None
+    per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=args.warmup + args.steps)
+    per = per[args.warmup:]
+    t_iter = statistics.mean(per)
+    if its is None:
+        value = None
+        note = "no stored oracle iteration count"
+    else:
+        value = 1.0 / (its * t_iter)
+        note = f"extrapolated: {its} oracle iterations per solve (tests/golden/oracle_counts.json) x measured s/iteration"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * args.cpu_iters * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "levels": levels, "alpha": alpha},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.cpu_iters} FGMRES iterations per step after setup ({setup:.1f} s); {note}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# clocks sampler
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for ln in open(self.f.name):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_bah(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    if rank == 0:
+        from paper_2411_15897_gb300 import _build
+        _build.build()
+    barrier()
+    import paper_2411_15897_gb300 as bah
+
+    prob = W.config(args.config)
+    opts = dict(precision=bah.BAH_MIXED, levels=args.levels, max_coarse_cells=args.max_coarse, restart=args.restart)
+    solver = bah.Solver.from_problem(prob, **opts)
+    levels = solver.levels
+    b_host = W.point_source(prob)
+    b = torch.from_numpy(b_host).cuda()
+    x = torch.zeros_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve_once(s, bb, xx):
+        st, stats = bah.bah_solve(s.ctx, bb, xx, 1, 1e-6)
+        return st, stats[0]
+
+    # warm-up, with every kernel class timed once to find the dominant one
+    bah.bah_profile_control(solver.ctx, (1 << 13) - 1, True)
+    st0, stats0 = solve_once(solver, b, x)
+    prof_all = bah.bah_profile_read(solver.ctx)
+    for _ in range(max(0, args.warmup - 1)):
+        solve_once(solver, b, x)
+    classes = prof_all["classes"]
+    dom = max((k for k in classes if k != "small"), key=lambda k: classes[k]["ms"])
+    dom_id = bah.BAH_K_NAMES.index(dom)
+
+    # timed region: K solves, no instrumentation; events per step on the launching
+    # stream; L2 flushed between steps (outside the events)
+    bah.bah_profile_control(solver.ctx, 0, True)
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    step_ms, iters = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, stats = solve_once(solver, b, x)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(stats["iters"])
+        assert st == bah.BAH_OK, stats
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof_timed = bah.bah_profile_read(solver.ctx)
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # the dominant kernel class, timed launch by launch with CUDA events recorded
+    # on the launching stream, over the same number of solves right after the
+    # timed region (events inside the step graphs would slow the timed solves)
+    bah.bah_profile_control(solver.ctx, 1 << dom_id, True)
+    for _ in range(args.steps):
+        flush.zero_()
+        solve_once(solver, b, x)
+    prof = bah.bah_profile_read(solver.ctx)
+    bah.bah_profile_control(solver.ctx, 0, True)
+    dc = prof["classes"][dom]
+    calls = max(dc["calls"], 1)
+    dom_ms = dc["ms"] / calls
+    dom_bytes = dc["bytes"] / calls
+
+    # relative residual of the last solve, by the library's FP64 residual
+    relres = stats["relres_true"]
+
+    # FP64 mode on the same GPU
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = bah.Solver.from_problem(prob, **dict(opts, precision=bah.BAH_FP64))
+        x64 = torch.zeros_like(b)
+        solve_once(s64, b, x64)
+        ms64, it64 = [], []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st64, stt = solve_once(s64, b, x64)
+            e1.record(stream)
+            e1.synchronize()
+            ms64.append(e0.elapsed_time(e1))
+            it64.append(stt["iters"])
+        fp64 = {"value": world * args.fp64_steps / (sum(ms64) / 1e3), "unit": UNIT, "iters": it64[-1],
+                "ms_per_step": statistics.mean(ms64), "relres_true": stt["relres_true"]}
+        s64.close()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    bp = torch.from_numpy(b_host.copy()).pin_memory()
+    xp = torch.zeros_like(bp).pin_memory()
+    bnp, xnp = bp.numpy(), xp.numpy()
+    solve_once(solver, bnp, xnp)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solve_once(solver, bnp, xnp)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(b_host.nbytes),
+           "d2h_bytes_per_step": int(b_host.nbytes)}
+
+    # roofline of the dominant kernel class
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
+    roof = {"kernel": KERNEL_NAMES.get(dom_id, dom), "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
+            "unit": "GB/s", "frac": (achieved_gbs / hbm_peak) if achieved_gbs else None, "traffic": None,
+            "peak_source": peak_src, "avg_launch_us": dom_ms * 1e3, "algorithmic_bytes_per_launch": dom_bytes,
+            "launches_timed": dc["calls"],
+            "timing": f"CUDA events on the launching stream around every launch of the class, {args.steps} solves "
+                      "right after the timed region"}
+    if dom in FP64_FLOP_PER_BYTE and achieved_gbs:
+        tfl = achieved_gbs * FP64_FLOP_PER_BYTE[dom] / 1e3
+        if tfl / FP64_PEAK_TFLOPS > roof["frac"]:
+            roof.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tfl / FP64_PEAK_TFLOPS, "peak_source": "derived: FP64 2 FMA/clk/SM x 152 SMs x 2070 MHz",
+                         "hbm_gbs": achieved_gbs})
+    wc = prof_all["classes"]
+    tot_ms = sum(v["ms"] for v in wc.values()) or 1.0
+    shares = {k: round(v["ms"] / tot_ms, 4) for k, v in sorted(wc.items(), key=lambda kv: -kv[1]["ms"])[:6]}
+    prof_path = args.profile_json
+    if rank == 0 and prof_path:
+        json.dump({"warmup_all_classes": prof_all, "dominant_instrumented": prof, "timed": prof_timed,
+                   "dominant": dom}, open(prof_path, "w"), indent=1)
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = oracle_counts().get(args.config)
+        alpha = 0.5 if levels >= 5 else {1: 0.0, 2: 0.1, 3: 0.2, 4: 0.4}[levels]
+        per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=1)
+        its = counts["iters"] if counts and counts.get("levels") == levels else statistics.median(iters)
+        src = "oracle's own count" if counts and counts.get("levels") == levels else "the GPU run's count"
+        cpu = {"value": 1.0 / (its * per[0]), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_iters} oracle FGMRES iterations of the same workload after a {setup:.1f} s setup, "
+                         f"extrapolated to {its} iterations per solve ({src})"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: bf16 coef / f32 multigrid / f64 FGMRES+operator+coarsest", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(prob.n), "unknowns": int(sum(W.compact_sizes(prob.n))),
+                   "levels": levels, "cycle": "V(1,2)", "restart": args.restart, "iters": iters[-1],
+                   "relres_true": relres, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"independent solves per GPU x{world}"},
+        "fp64": fp64,
+        "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "e2e": e2e,
+        "gpu_launches": prof_timed["launches"],
+        "kernel_shares": shares,
+        "roofline": roof,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_bah(args)
+
+
+if __name__ == "__main__":
+    main()

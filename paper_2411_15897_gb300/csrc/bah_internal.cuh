@@ -146,6 +146,14 @@ template <int MODE>
 void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                         const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st);
 template <int MODE>
+void launch_smooth_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                            const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                            typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st);
+template <int MODE>
+void launch_prolong_smooth(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                           const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                           const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st);
+template <int MODE>
 void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
                          typename Prec<MODE>::V* const* x, cudaStream_t st);
 template <int MODE>
@@ -164,6 +172,12 @@ constexpr int RED_CTAS = 296;   // partial sums per reduction (2 per SM on 148+ 
 void launch_multi_dot(const double2* V, size_t ldv, int k, const double2* w, size_t n,
                       double2* partial, double2* out, cudaStream_t st);
 void launch_norm2(const double2* w, size_t n, double* partial, double* out, cudaStream_t st);
+void launch_dot_norm(const double2* V, size_t ldv, int k, const double2* w, size_t n, double2* partial, double2* out,
+                     const int* flag, cudaStream_t st);
+void launch_axpy_norm(const double2* V, size_t ldv, int k, const double2* coef, double2* w, size_t n, double* npart,
+                      const int* flag, cudaStream_t st);
+void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* wn, cudaStream_t st);
+void launch_pass2_norm(const double* npart, const int* flag, double* wn, cudaStream_t st);
 void launch_multi_axpy_sub(const double2* V, size_t ldv, int k, const double2* coef, double2* w, size_t n,
                            cudaStream_t st);
 template <class Vz>

@@ -62,6 +62,114 @@ __global__ void __launch_bounds__(256) k_reduce_partials2(const double2* __restr
     if (threadIdx.x == 0) out[blockIdx.y] = acc;
 }
 
+// ---------------------------------------------------------------------------
+// Gram-Schmidt with selective reorthogonalisation (Daniel-Gragg-Kaufman-Stewart
+// criterion): pass 1 forms h1 = V^H w together with ||w||^2 and then
+// w' = w - V h1 together with ||w'||^2; a second pass runs only if
+// ||w'|| < ||w|| / sqrt(2).  The pass-2 kernels read the device flag and
+// return at once when it is clear.
+// ---------------------------------------------------------------------------
+// rows 0..k-1: conj(V_y) w; row k: |w|^2 (imaginary part 0)
+__global__ void __launch_bounds__(256) k_dot_norm_partial(const double2* __restrict__ V, size_t ldv, int k,
+                                                          const double2* __restrict__ w, size_t n,
+                                                          double2* __restrict__ partial, const int* flag) {
+    if (flag && *flag == 0) return;
+    const int y = blockIdx.y;
+    double2 acc = make_double2(0.0, 0.0);
+    if (y < k) {
+        const double2* v = V + (size_t)y * ldv;
+        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+            const double2 a = v[e], b = w[e];
+            acc.x += a.x * b.x + a.y * b.y;
+            acc.y += a.x * b.y - a.y * b.x;
+        }
+    } else {
+        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+            const double2 b = w[e];
+            acc.x += b.x * b.x + b.y * b.y;
+        }
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0) partial[(size_t)y * gridDim.x + blockIdx.x] = acc;
+}
+__global__ void __launch_bounds__(256) k_reduce_rows(const double2* __restrict__ partial, int np, double2* out,
+                                                     const int* flag) {
+    if (flag && *flag == 0) {
+        if (threadIdx.x == 0) out[blockIdx.y] = make_double2(0.0, 0.0);
+        return;
+    }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+        const double2 a = partial[(size_t)blockIdx.y * np + e];
+        acc.x += a.x;
+        acc.y += a.y;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0) out[blockIdx.y] = acc;
+}
+void launch_dot_norm(const double2* V, size_t ldv, int k, const double2* w, size_t n, double2* partial, double2* out,
+                     const int* flag, cudaStream_t st) {
+    k_dot_norm_partial<<<dim3(RED_CTAS, k + 1), 256, 0, st>>>(V, ldv, k, w, n, partial, flag);
+    k_reduce_rows<<<dim3(1, k + 1), 256, 0, st>>>(partial, RED_CTAS, out, flag);
+}
+
+// w -= sum_i coef[i] V_i, and per-CTA partial sums of |w_new|^2
+__global__ void __launch_bounds__(256) k_axpy_norm(const double2* __restrict__ V, size_t ldv, int k,
+                                                   const double2* __restrict__ coef, double2* __restrict__ w, size_t n,
+                                                   double* __restrict__ npart, const int* flag) {
+    if (flag && *flag == 0) return;
+    __shared__ double2 c[64];
+    if (threadIdx.x < k) c[threadIdx.x] = coef[threadIdx.x];
+    __syncthreads();
+    double nn = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        double2 acc = w[e];
+        for (int i = 0; i < k; ++i) {
+            const double2 v = V[(size_t)i * ldv + e];
+            acc.x -= c[i].x * v.x - c[i].y * v.y;
+            acc.y -= c[i].x * v.y + c[i].y * v.x;
+        }
+        w[e] = acc;
+        nn += acc.x * acc.x + acc.y * acc.y;
+    }
+    double2 r = block_sum2(make_double2(nn, 0.0));
+    if (threadIdx.x == 0) npart[blockIdx.x] = r.x;
+}
+void launch_axpy_norm(const double2* V, size_t ldv, int k, const double2* coef, double2* w, size_t n, double* npart,
+                      const int* flag, cudaStream_t st) {
+    k_axpy_norm<<<RED_CTAS, 256, 0, st>>>(V, ldv, k, coef, w, n, npart, flag);
+}
+
+// reduce the pass-1 norm, decide on the second pass, set ||w|| for the Givens step
+// wn[0] = ||w_final||; flag = 1 when ||w'||^2 < ||w||^2 / 2
+__global__ void __launch_bounds__(256) k_dgks_decide(const double* npart, int np, const double2* h1norm, int k,
+                                                     int* flag, double* wn) {
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) acc += npart[e];
+    double2 r = block_sum2(make_double2(acc, 0.0));
+    if (threadIdx.x == 0) {
+        const double w0 = h1norm[k].x;          // ||w||^2 before pass 1
+        const int f = (r.x < 0.5 * w0) ? 1 : 0;
+        *flag = f;
+        wn[0] = sqrt(r.x);
+        wn[1] += (double)f;                      // count of second passes (diagnostic)
+    }
+}
+void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* wn, cudaStream_t st) {
+    k_dgks_decide<<<1, 256, 0, st>>>(npart, RED_CTAS, h1norm, k, flag, wn);
+}
+// after pass 2: ||w''|| replaces ||w'||
+__global__ void __launch_bounds__(256) k_pass2_norm(const double* npart, int np, const int* flag, double* wn) {
+    if (*flag == 0) return;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) acc += npart[e];
+    double2 r = block_sum2(make_double2(acc, 0.0));
+    if (threadIdx.x == 0) wn[0] = sqrt(r.x);
+}
+void launch_pass2_norm(const double* npart, const int* flag, double* wn, cudaStream_t st) {
+    k_pass2_norm<<<1, 256, 0, st>>>(npart, RED_CTAS, flag, wn);
+}
+
 void launch_multi_dot(const double2* V, size_t ldv, int k, const double2* w, size_t n, double2* partial, double2* out,
                       cudaStream_t st) {
     k_multi_dot_partial<<<dim3(RED_CTAS, k), 256, 0, st>>>(V, ldv, w, n, partial);
@@ -156,31 +264,39 @@ void launch_scale_copy(const double2* w, const double* nrm, double2* v, size_t n
 // ---------------------------------------------------------------------------
 __global__ void k_arnoldi_givens(double2* Hcol, const double2* h1, const double2* h2, const double* wnorm, int j,
                                  double2* cs, double2* sn, double2* g, double* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double2 h[65];
-    for (int i = 0; i <= j; ++i) h[i] = h2 ? cadd(h1[i], h2[i]) : h1[i];
-    h[j + 1] = make_double2(*wnorm, 0.0);
-    bool bad = !isfinite(h[j + 1].x);
+    __shared__ double2 h[66];
+    __shared__ double2 ssn[65];
+    __shared__ double scs[65];
+    // the warp stages the column and the previous rotations
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        h[i] = h2 ? cadd(h1[i], h2[i]) : h1[i];
+        if (i < j) { scs[i] = cs[i].x; ssn[i] = sn[i]; }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double wn = *wnorm;
+    h[j + 1] = make_double2(wn, 0.0);
+    bool bad = !isfinite(wn);
     for (int i = 0; i <= j; ++i) bad |= !isfinite(h[i].x) || !isfinite(h[i].y);
     for (int i = 0; i < j; ++i) {
-        const double c = cs[i].x;
-        const double2 s = sn[i];
+        const double c = scs[i];
+        const double2 s = ssn[i];
         const double2 a = h[i], b = h[i + 1];
         h[i] = cadd(cscale(a, c), cmul(s, b));
         h[i + 1] = csub(cscale(b, c), cmul(cconj(s), a));
     }
     const double2 a = h[j], b = h[j + 1];
-    const double na = sqrt(a.x * a.x + a.y * a.y), nb = sqrt(b.x * b.x + b.y * b.y);
+    const double na2 = a.x * a.x + a.y * a.y, nb2 = b.x * b.x + b.y * b.y;
     double c;
     double2 s;
-    if (nb == 0.0) {
+    if (nb2 == 0.0) {
         c = 1.0; s = make_double2(0.0, 0.0);
-    } else if (na == 0.0) {
-        c = 0.0; s = cscale(cconj(b), 1.0 / nb);
+    } else if (na2 == 0.0) {
+        c = 0.0; s = cscale(cconj(b), 1.0 / sqrt(nb2));
     } else {
-        const double r = hypot(na, nb);
+        const double na = sqrt(na2), r = sqrt(na2 + nb2);
         c = na / r;
-        s = cscale(cmul(cscale(a, 1.0 / na), cconj(b)), 1.0 / r);
+        s = cscale(cmul(a, cconj(b)), 1.0 / (na * r));
     }
     cs[j] = make_double2(c, 0.0);
     sn[j] = s;
@@ -189,9 +305,10 @@ __global__ void k_arnoldi_givens(double2* Hcol, const double2* h1, const double2
     for (int i = 0; i <= j + 1; ++i) Hcol[i] = h[i];
     const double2 gj = g[j];
     g[j] = cscale(gj, c);
-    g[j + 1] = cscale(cmul(cconj(s), gj), -1.0);
-    status[0] = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
-    status[1] = *wnorm;
+    const double2 gn = cscale(cmul(cconj(s), gj), -1.0);
+    g[j + 1] = gn;
+    status[0] = sqrt(gn.x * gn.x + gn.y * gn.y);
+    status[1] = wn;
     status[2] = bad ? 1.0 : 0.0;
 }
 void launch_arnoldi_givens(double2* Hcol, const double2* h1, const double2* h2, const double* wnorm, int j,

@@ -9,6 +9,8 @@
 #include "bah_internal.cuh"
 #include "intergrid.cuh"
 
+#include <algorithm>
+
 namespace bah {
 
 template <int MODE>
@@ -18,6 +20,13 @@ struct MGT {
     using C = typename Prec<MODE>::C;
     using CC = typename Prec<MODE>::CC;
 };
+
+template <class LS>
+static inline int max_radius(const LS& s) {
+    int r = 0;
+    for (int z = 0; z < s.nb; ++z) r = std::max(r, std::max(s.blk[z].rx, s.blk[z].rz));
+    return r;
+}
 
 // A x and diag(A) at point t of a level-0 block
 template <int MODE>
@@ -50,29 +59,60 @@ __device__ __forceinline__ void apply_fine5(const Fine5<typename MGT<MODE>::C, t
     ax = acc;
 }
 
-// A x and diag(A) at point t from an explicit stencil
-template <int MODE>
-__device__ __forceinline__ void apply_stencil(const typename MGT<MODE>::CC* __restrict__ S, int rx, int rz, int n1,
-                                              int n2, int i, int j, int t, const typename MGT<MODE>::V* __restrict__ x,
-                                              typename MGT<MODE>::V& ax, typename MGT<MODE>::V& dg) {
+
+// A x at point (i, j) of a level-0 block where x is given by an accessor X(index)
+template <int MODE, class XF>
+__device__ __forceinline__ typename MGT<MODE>::V apply_fine5_fn(const Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC>& f,
+                                                               int type, int i, int j, int t, XF X) {
+    using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
+    const int n1 = f.n1, n2 = f.n2;
+    const auto* dgp = type == 0 ? f.dg0 : (type == 1 ? f.dg1 : f.dg2);
+    V acc = cmul(ldc(dgp[t]), X(t));
+    auto sub = [&](R k, V v) { acc.x -= k * v.x; acc.y -= k * v.y; };
+    if (type == 0) {
+        if (i - 1 >= 1) sub(ldr(f.cx[t - 1]), X(t - 1));
+        if (i + 1 <= n1 - 1) sub(ldr(f.cx[t]), X(t + 1));
+        if (j >= 1) sub(ldr(f.nz[t]), X(t - n1));
+        if (j + 1 <= n2 - 1) sub(ldr(f.nz[t + n1]), X(t + n1));
+    } else if (type == 1) {
+        if (j - 1 >= 1) sub(ldr(f.cz[t - n1]), X(t - n1));
+        if (j + 1 <= n2 - 1) sub(ldr(f.cz[t]), X(t + n1));
+        if (i >= 1) sub(ldr(f.nx[t]), X(t - 1));
+        if (i + 1 <= n1 - 1) sub(ldr(f.nx[t + 1]), X(t + 1));
+    } else {
+        if (i >= 1) sub(ldr(f.wx[t - 1]), X(t - 1));
+        if (i + 1 < n1) sub(ldr(f.wx[t + 1]), X(t + 1));
+        if (j >= 1) sub(ldr(f.wz[t - n1]), X(t - n1));
+        if (j + 1 < n2) sub(ldr(f.wz[t + n1]), X(t + n1));
+    }
+    return acc;
+}
+
+// RM is the compile-time maximum radius (1 or 2); rx, rz <= RM are the block's
+// radii, so the loops unroll fully and the loads issue back to back.
+template <int MODE, int RM, class XF>
+__device__ __forceinline__ typename MGT<MODE>::V apply_stencil_fn(const typename MGT<MODE>::CC* __restrict__ S, int rx,
+                                                                 int rz, int n1, int n2, int i, int j, int t, XF X) {
     using V = typename MGT<MODE>::V;
     const size_t np = (size_t)n1 * n2;
     const int wx = 2 * rx + 1;
     V acc = czero<V>();
-    for (int dz = -rz; dz <= rz; ++dz) {
+#pragma unroll
+    for (int dz = -RM; dz <= RM; ++dz) {
         const int jj = j + dz;
-        if (jj < 0 || jj >= n2) continue;
-        for (int dx = -rx; dx <= rx; ++dx) {
+        if (dz < -rz || dz > rz || jj < 0 || jj >= n2) continue;
+#pragma unroll
+        for (int dx = -RM; dx <= RM; ++dx) {
             const int ii = i + dx;
-            if (ii < 0 || ii >= n1) continue;
-            const V s = ldc(S[(size_t)((dz + rz) * wx + (dx + rx)) * np + t]);
-            const V v = x[jj * n1 + ii];
-            acc.x += s.x * v.x - s.y * v.y;
-            acc.y += s.x * v.y + s.y * v.x;
+            if (dx < -rx || dx > rx || ii < 0 || ii >= n1) continue;
+            const V sv = ldc(S[(size_t)((dz + rz) * wx + (dx + rx)) * np + t]);
+            const V v = X(jj * n1 + ii);
+            acc.x += sv.x * v.x - sv.y * v.y;
+            acc.y += sv.x * v.y + sv.y * v.x;
         }
     }
-    ax = acc;
-    dg = ldc(S[(size_t)(rz * wx + rx) * np + t]);
+    return acc;
 }
 
 template <int MODE>
@@ -89,7 +129,7 @@ __device__ __forceinline__ typename MGT<MODE>::V diag_only(const Fine5<typename 
 // ---------------------------------------------------------------------------
 // damped Jacobi:  x_out = x_in + w D^{-1} (b - A x_in)   (zero_init: w D^{-1} b)
 // ---------------------------------------------------------------------------
-template <int MODE, bool L0>
+template <int MODE, bool L0, int RM>
 __global__ void __launch_bounds__(256) k_jacobi(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
                                                 Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC> f5,
                                                 typename MGT<MODE>::R w, int zero_init) {
@@ -106,9 +146,12 @@ __global__ void __launch_bounds__(256) k_jacobi(LvlSet<typename MGT<MODE>::V, ty
         B.xout[t] = cscale(cdiv(b, dg), w);
         return;
     }
-    V ax, dg;
-    if (L0) apply_fine5<MODE>(f5, B.type, i, j, t, B.xin, ax, dg);
-    else apply_stencil<MODE>(B.S, B.rx, B.rz, n1, n2, i, j, t, B.xin, ax, dg);
+    const V* __restrict__ xin = B.xin;
+    auto X = [&](int g) { return xin[g]; };
+    V ax;
+    if (L0) ax = apply_fine5_fn<MODE>(f5, B.type, i, j, t, X);
+    else ax = apply_stencil_fn<MODE, RM>(B.S, B.rx, B.rz, n1, n2, i, j, t, X);
+    const V dg = diag_only<MODE>(L0 ? &f5 : nullptr, B, np, t);
     const V corr = cdiv(csub(b, ax), dg);
     const V x = B.xin[t];
     B.xout[t] = cmk<V>(x.x + w * corr.x, x.y + w * corr.y);
@@ -117,7 +160,7 @@ __global__ void __launch_bounds__(256) k_jacobi(LvlSet<typename MGT<MODE>::V, ty
 // ---------------------------------------------------------------------------
 // residual:  r = b - A x
 // ---------------------------------------------------------------------------
-template <int MODE, bool L0>
+template <int MODE, bool L0, int RM>
 __global__ void __launch_bounds__(256) k_residual(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
                                                   Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC> f5) {
     using V = typename MGT<MODE>::V;
@@ -127,10 +170,146 @@ __global__ void __launch_bounds__(256) k_residual(LvlSet<typename MGT<MODE>::V, 
     if (t >= np) return;
     const int i = t % n1, j = t / n1;
     if (!valid_pt(B.type, i, j)) { B.xout[t] = czero<V>(); return; }
-    V ax, dg;
-    if (L0) apply_fine5<MODE>(f5, B.type, i, j, t, B.xin, ax, dg);
-    else apply_stencil<MODE>(B.S, B.rx, B.rz, n1, n2, i, j, t, B.xin, ax, dg);
+    const V* __restrict__ xin = B.xin;
+    auto X = [&](int g) { return xin[g]; };
+    V ax;
+    if (L0) ax = apply_fine5_fn<MODE>(f5, B.type, i, j, t, X);
+    else ax = apply_stencil_fn<MODE, RM>(B.S, B.rx, B.rz, n1, n2, i, j, t, X);
     B.xout[t] = csub(B.b[t], ax);
+}
+
+// ---------------------------------------------------------------------------
+// fused pre-smoothing + residual + restriction (one thread per coarse point):
+//   x = w D^{-1} b  (one damped Jacobi sweep from the zero guess),
+//   b_c = R (b - A x),
+// with x recomputed on the fly at every fine point the restriction touches;
+// the thread also writes x on the 2x2 fine points it owns.
+// ---------------------------------------------------------------------------
+template <class V> struct PtrSetF { V* p[3]; };
+
+template <int MODE, bool L0, int RM>
+__global__ void __launch_bounds__(256) k_smooth_restrict(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
+                                                         Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC> f5,
+                                                         typename MGT<MODE>::R w, PtrSetF<typename MGT<MODE>::V> cb,
+                                                         int intergrid) {
+    using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
+    const auto& B = s.blk[blockIdx.y];
+    const int n1 = s.n1, n2 = s.n2, n1c = n1 / 2, n2c = n2 / 2;
+    const int np = n1 * n2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n1c * n2c) return;
+    const int I = t % n1c, J = t / n1c;
+    const int type = B.type;
+    // zero-guess Jacobi iterate at fine index g
+    auto X = [&](int g) -> V {
+        const int gi = g % n1, gj = g / n1;
+        if (!valid_pt(type, gi, gj)) return czero<V>();
+        const V dg = diag_only<MODE>(L0 ? &f5 : nullptr, B, np, g);
+        return cscale(cdiv(B.b[g], dg), w);
+    };
+    // the owned 2x2 fine points
+    for (int q = 0; q < 4; ++q) {
+        const int fi = 2 * I + (q & 1), fj = 2 * J + (q >> 1);
+        B.xout[fj * n1 + fi] = X(fj * n1 + fi);
+    }
+    V acc = czero<V>();
+    if (valid_pt(type, I, J)) {
+        const bool nodx = type == 0, nodz = type == 1;
+        for (int fj = 2 * J - 2; fj <= 2 * J + 3; ++fj) {
+            const R wz = rw_axis_t<R>(nodz, intergrid, n2, J, fj);
+            if (wz == R(0)) continue;
+            for (int fi = 2 * I - 2; fi <= 2 * I + 3; ++fi) {
+                const R wxw = rw_axis_t<R>(nodx, intergrid, n1, I, fi);
+                if (wxw == R(0)) continue;
+                const int f = fj * n1 + fi;
+                V ax;
+                if (L0) ax = apply_fine5_fn<MODE>(f5, type, fi, fj, f, X);
+                else ax = apply_stencil_fn<MODE, RM>(B.S, B.rx, B.rz, n1, n2, fi, fj, f, X);
+                const V r = csub(B.b[f], ax);
+                const R wgt = wz * wxw;
+                acc.x += wgt * r.x;
+                acc.y += wgt * r.y;
+            }
+        }
+    }
+    cb.p[blockIdx.y][t] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// fused prolongation + correction + one damped Jacobi sweep (one thread per
+// fine point): y = x + P e_c evaluated on the fly at the point and its
+// stencil neighbours, then x_out = y + w D^{-1} (b - A y).
+// ---------------------------------------------------------------------------
+template <int MODE, bool L0, int RM>
+__global__ void __launch_bounds__(256) k_prolong_smooth(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
+                                                        Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC> f5,
+                                                        typename MGT<MODE>::R w, PtrSetF<const typename MGT<MODE>::V> ce) {
+    using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
+    const auto& B = s.blk[blockIdx.y];
+    const int n1 = s.n1, n2 = s.n2, n1c = n1 / 2;
+    const int np = n1 * n2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np) return;
+    const int i = t % n1, j = t / n1;
+    const int type = B.type;
+    if (!valid_pt(type, i, j)) { B.xout[t] = czero<V>(); return; }
+    const bool nodx = type == 0, nodz = type == 1;
+    const V* e = ce.p[blockIdx.y];
+    auto Y = [&](int g) -> V {
+        const int gi = g % n1, gj = g / n1;
+        if (!valid_pt(type, gi, gj)) return czero<V>();
+        V acc = B.xin[g];
+        for (int cj = (gj >> 1) - 1; cj <= (gj >> 1) + 1; ++cj) {
+            const R pz = pw_axis_t<R>(nodz, n2, gj, cj);
+            if (pz == R(0)) continue;
+            for (int ci = (gi >> 1) - 1; ci <= (gi >> 1) + 1; ++ci) {
+                const R px = pw_axis_t<R>(nodx, n1, gi, ci);
+                if (px == R(0)) continue;
+                const V v = e[cj * n1c + ci];
+                acc.x += px * pz * v.x;
+                acc.y += px * pz * v.y;
+            }
+        }
+        return acc;
+    };
+    V ay;
+    if (L0) ay = apply_fine5_fn<MODE>(f5, type, i, j, t, Y);
+    else ay = apply_stencil_fn<MODE, RM>(B.S, B.rx, B.rz, n1, n2, i, j, t, Y);
+    const V dg = diag_only<MODE>(L0 ? &f5 : nullptr, B, np, t);
+    const V corr = cdiv(csub(B.b[t], ay), dg);
+    const V y = Y(t);
+    B.xout[t] = cmk<V>(y.x + w * corr.x, y.y + w * corr.y);
+}
+
+template <int MODE>
+void launch_smooth_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                            const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                            typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st) {
+    PtrSetF<typename Prec<MODE>::V> cb;
+    for (int z = 0; z < 3; ++z) cb.p[z] = z < s.nb ? coarse_b[z] : nullptr;
+    const int npc = (s.n1 / 2) * (s.n2 / 2);
+    dim3 g((npc + 255) / 256, s.nb);
+    using R = typename Prec<MODE>::R;
+    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
+    if (f5) k_smooth_restrict<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5, (R)w, cb, intergrid);
+    else if (max_radius(s) <= 1) k_smooth_restrict<MODE, false, 1><<<g, 256, 0, st>>>(s, nof, (R)w, cb, intergrid);
+    else k_smooth_restrict<MODE, false, 2><<<g, 256, 0, st>>>(s, nof, (R)w, cb, intergrid);
+}
+template <int MODE>
+void launch_prolong_smooth(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                           const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                           const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st) {
+    PtrSetF<const typename Prec<MODE>::V> ce;
+    for (int z = 0; z < 3; ++z) ce.p[z] = z < s.nb ? coarse_x[z] : nullptr;
+    const int np = s.n1 * s.n2;
+    dim3 g((np + 255) / 256, s.nb);
+    using R = typename Prec<MODE>::R;
+    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
+    if (f5) k_prolong_smooth<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5, (R)w, ce);
+    else if (max_radius(s) <= 1) k_prolong_smooth<MODE, false, 1><<<g, 256, 0, st>>>(s, nof, (R)w, ce);
+    else k_prolong_smooth<MODE, false, 2><<<g, 256, 0, st>>>(s, nof, (R)w, ce);
 }
 
 template <int MODE>
@@ -140,17 +319,20 @@ void launch_jacobi(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>
     const int np = s.n1 * s.n2;
     dim3 g((np + 255) / 256, s.nb);
     using R = typename Prec<MODE>::R;
-    if (f5) k_jacobi<MODE, true><<<g, 256, 0, st>>>(s, *f5, (R)w, zero_init);
-    else k_jacobi<MODE, false><<<g, 256, 0, st>>>(s, Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>{}, (R)w,
-                                                  zero_init);
+    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
+    if (f5) k_jacobi<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5, (R)w, zero_init);
+    else if (max_radius(s) <= 1) k_jacobi<MODE, false, 1><<<g, 256, 0, st>>>(s, nof, (R)w, zero_init);
+    else k_jacobi<MODE, false, 2><<<g, 256, 0, st>>>(s, nof, (R)w, zero_init);
 }
 template <int MODE>
 void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
                      const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, cudaStream_t st) {
     const int np = s.n1 * s.n2;
     dim3 g((np + 255) / 256, s.nb);
-    if (f5) k_residual<MODE, true><<<g, 256, 0, st>>>(s, *f5);
-    else k_residual<MODE, false><<<g, 256, 0, st>>>(s, Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>{});
+    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
+    if (f5) k_residual<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5);
+    else if (max_radius(s) <= 1) k_residual<MODE, false, 1><<<g, 256, 0, st>>>(s, nof);
+    else k_residual<MODE, false, 2><<<g, 256, 0, st>>>(s, nof);
 }
 
 // ---------------------------------------------------------------------------
@@ -173,12 +355,12 @@ __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, 
         const bool nodx = B.type == 0, nodz = B.type == 1;
         const V* r = B.xout;
         for (int fj = 2 * J - 2; fj <= 2 * J + 3; ++fj) {
-            const double wz = rw_axis(nodz, intergrid, n2, J, fj);
-            if (wz == 0.0) continue;
+            const R wz = rw_axis_t<R>(nodz, intergrid, n2, J, fj);
+            if (wz == R(0)) continue;
             for (int fi = 2 * I - 2; fi <= 2 * I + 3; ++fi) {
-                const double wxw = rw_axis(nodx, intergrid, n1, I, fi);
-                if (wxw == 0.0) continue;
-                const R wgt = (R)(wz * wxw);
+                const R wxw = rw_axis_t<R>(nodx, intergrid, n1, I, fi);
+                if (wxw == R(0)) continue;
+                const R wgt = wz * wxw;
                 const V v = r[fj * n1 + fi];
                 acc.x += wgt * v.x;
                 acc.y += wgt * v.y;
@@ -216,12 +398,12 @@ __global__ void __launch_bounds__(256) k_prolong_add(LvlSet<typename MGT<MODE>::
     const V* e = ce.p[blockIdx.y];
     V acc = czero<V>();
     for (int cj = (j >> 1) - 1; cj <= (j >> 1) + 1; ++cj) {
-        const double pz = pw_axis(nodz, n2, j, cj);
-        if (pz == 0.0) continue;
+        const R pz = pw_axis_t<R>(nodz, n2, j, cj);
+        if (pz == R(0)) continue;
         for (int ci = (i >> 1) - 1; ci <= (i >> 1) + 1; ++ci) {
-            const double px = pw_axis(nodx, n1, i, ci);
-            if (px == 0.0) continue;
-            const R wgt = (R)(px * pz);
+            const R px = pw_axis_t<R>(nodx, n1, i, ci);
+            if (px == R(0)) continue;
+            const R wgt = px * pz;
             const V v = e[cj * n1c + ci];
             acc.x += wgt * v.x;
             acc.y += wgt * v.y;
@@ -244,6 +426,8 @@ void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>
 // ---------------------------------------------------------------------------
 // coarsest level: x = A_c^{-1} b with the stored FP64 inverse (one warp per row)
 // ---------------------------------------------------------------------------
+constexpr int kCoarseSmem = 3072;   // points staged in shared memory (48 KB of FP64 complex)
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const double2> inv,
                                                       PtrSet<const typename MGT<MODE>::V> b,
@@ -252,16 +436,24 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const dou
     const int z = blockIdx.y;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    extern __shared__ double2 bsh[];
+    const V* bb = b.p[z];
+    const bool staged = npts <= kCoarseSmem;
+    if (staged) {
+        // the right-hand side in FP64, converted once per CTA
+        for (int c = threadIdx.x; c < npts; c += blockDim.x) bsh[c] = make_double2((double)bb[c].x, (double)bb[c].y);
+        __syncthreads();
+    }
     if (warp >= npts) return;
     const double2* row = inv.p[z] + (size_t)warp * npts;
-    const V* bb = b.p[z];
     double re = 0.0, im = 0.0;
     for (int c = lane; c < npts; c += 32) {
         const double2 a = row[c];
-        const V v = bb[c];
-        const double vx = (double)v.x, vy = (double)v.y;
-        re += a.x * vx - a.y * vy;
-        im += a.x * vy + a.y * vx;
+        double2 v;
+        if (staged) v = bsh[c];
+        else v = make_double2((double)bb[c].x, (double)bb[c].y);
+        re += a.x * v.x - a.y * v.y;
+        im += a.x * v.y + a.y * v.x;
     }
     for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -282,7 +474,8 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
         px.p[z] = z < nb ? x[z] : nullptr;
     }
     dim3 g((npts * 32 + 255) / 256, nb);
-    k_coarse_apply<MODE><<<g, 256, 0, st>>>(npts, pi, pb, px);
+    const size_t smem = npts <= kCoarseSmem ? (size_t)npts * sizeof(double2) : 0;
+    k_coarse_apply<MODE><<<g, 256, smem, st>>>(npts, pi, pb, px);
 }
 
 #define INST(MODE)                                                                                                 \
@@ -295,7 +488,13 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
     template void launch_prolong_add<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                           \
                                            const Prec<MODE>::V* const*, cudaStream_t);                             \
     template void launch_coarse_apply<MODE>(int, int, const double2* const*, const Prec<MODE>::V* const*,         \
-                                            Prec<MODE>::V* const*, cudaStream_t);
+                                            Prec<MODE>::V* const*, cudaStream_t);                                  \
+    template void launch_smooth_restrict<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                       \
+                                               const Fine5<Prec<MODE>::C, Prec<MODE>::CC>*, double,                \
+                                               Prec<MODE>::V* const*, int, cudaStream_t);                          \
+    template void launch_prolong_smooth<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                        \
+                                              const Fine5<Prec<MODE>::C, Prec<MODE>::CC>*, double,                 \
+                                              const Prec<MODE>::V* const*, cudaStream_t);
 INST(BAH_FP64)
 INST(BAH_MIXED)
 

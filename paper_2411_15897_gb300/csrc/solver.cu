@@ -12,6 +12,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <utility>
@@ -70,7 +71,32 @@ struct Ctx {
     size_t evused = 0;
     std::vector<std::pair<int, size_t>> pending;
 
+    // Gram-Schmidt flag and per-step graphs
+    int* gsflag = nullptr;
+    struct IterGraph {
+        cudaGraphExec_t exec = nullptr;
+        unsigned mask = ~0u;
+        long long launches = 0, cls_launch[16] = {}, cls_calls[16] = {};
+        double cls_bytes[16] = {};
+        std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    };
+    std::vector<IterGraph> ig;
+    IterGraph* capturing = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<cudaEvent_t> itev;
+    bool use_graphs = true;
+    bool fused = false;                  // fused multigrid kernels (BAH_FUSED=1) when nu_pre == 1 and nu_post >= 1
+
+    static void clear_graph(IterGraph& G) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        for (auto& e : G.ev) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
+        G = IterGraph();
+    }
+
     ~Ctx() {
+        for (auto& G : ig) clear_graph(G);
+        for (cudaEvent_t e : itev) cudaEventDestroy(e);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         for (void* p : allocs) cudaFree(p);
         if (hstatus) cudaFreeHost(hstatus);
@@ -120,8 +146,21 @@ struct Prof {
     double bytes;
     int nk;
     size_t idx = (size_t)-1;
+    cudaEvent_t ce0 = nullptr, ce1 = nullptr;
     Prof(Ctx& c_, int cls_, cudaStream_t st_, double bytes_, int nk_ = 1)
         : c(c_), cls(cls_), st(st_), bytes(bytes_), nk(nk_) {
+        if (c.capturing) {
+            if (c.tmask & (1u << cls)) {
+                if (cudaEventCreate(&ce0) == cudaSuccess && cudaEventCreate(&ce1) == cudaSuccess) {
+                    // an external record becomes an event-record node of the graph, replayed per launch
+                    cudaEventRecordWithFlags(ce0, st, cudaEventRecordExternal);
+                } else {
+                    cudaGetLastError();
+                    ce0 = ce1 = nullptr;
+                }
+            }
+            return;
+        }
         if (c.tmask & (1u << cls)) {
             if (c.evused + 2 > c.evpool.size()) {
                 if (c.evpool.size() < 16384) {
@@ -140,6 +179,18 @@ struct Prof {
         }
     }
     ~Prof() {
+        if (c.capturing) {
+            auto* G = c.capturing;
+            if (ce0) {
+                cudaEventRecordWithFlags(ce1, st, cudaEventRecordExternal);
+                G->ev.push_back({cls, {ce0, ce1}});
+            }
+            G->launches += nk;
+            G->cls_launch[cls] += nk;
+            G->cls_calls[cls] += 1;
+            G->cls_bytes[cls] += bytes;
+            return;
+        }
         if (idx != (size_t)-1) {
             cudaEventRecord(c.evpool[idx + 1], st);
             c.pending.emplace_back(cls, idx);
@@ -226,6 +277,28 @@ struct MG {
         V* oth[3];
         for (int z = 0; z < nb; ++z) { cur[z] = out[z]; oth[z] = (V*)c.vT[l][b0 + z]; }
         auto swap_cur = [&]() { for (int z = 0; z < nb; ++z) std::swap(cur[z], oth[z]); };
+        V* cb[3];
+        V* cx[3];
+        for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
+        if (c.fused && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
+            // pre-smoothing + residual + restriction in one launch
+            {
+                Prof pr(c, BAH_K_RESTRICT, st, cb_ + nb * npl * vs * 2.25);
+                launch_smooth_restrict<MODE>(set(c, l, b0, nb, nullptr, cur), pf5, w, cb, c.o.intergrid, st);
+            }
+            cycle(c, l + 1, b0, nb, cx, st);
+            // prolongation + correction + first post-smoothing sweep
+            {
+                Prof pr(c, BAH_K_PROLONG, st, sweep + nb * npl * vs * 0.25);
+                launch_prolong_smooth<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, cx, st);
+                swap_cur();
+            }
+            for (int s = 1; s < c.o.nu_post; ++s) {
+                Prof pr(c, BAH_K_JACOBI, st, sweep);
+                launch_jacobi<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, 0, st);
+                swap_cur();
+            }
+        } else {
         // pre-relaxation
         if (c.o.nu_pre >= 1) {
             {
@@ -247,9 +320,6 @@ struct MG {
             Prof pr(c, BAH_K_RESIDUAL, st, sweep);
             launch_residual<MODE>(rs, pf5, st);
         }
-        V* cb[3];
-        V* cx[3];
-        for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
         {
             Prof pr(c, BAH_K_RESTRICT, st, nb * npl * vs * 1.25);
             launch_restrict<MODE>(rs, cb, c.o.intergrid, st);
@@ -265,6 +335,7 @@ struct MG {
             Prof pr(c, BAH_K_JACOBI, st, sweep);
             launch_jacobi<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, 0, st);
             swap_cur();
+        }
         }
         for (int z = 0; z < nb; ++z)
             if (cur[z] != out[z]) {
@@ -411,13 +482,20 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     TRY(c.alloc_t(&c.W, n)); TRY(c.alloc_t(&c.R, n)); TRY(c.alloc_t(&c.Bs, n)); TRY(c.alloc_t(&c.X, n));
     TRY(c.alloc(&c.ztmp, n * c.vsz));
     TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m));
-    TRY(c.alloc_t(&c.h1v, m + 1)); TRY(c.alloc_t(&c.h2v, m + 1));
+    TRY(c.alloc_t(&c.h1v, m + 2)); TRY(c.alloc_t(&c.h2v, m + 2));
+    TRY(c.alloc_t(&c.gsflag, 1));
     TRY(c.alloc_t(&c.cs, m + 1)); TRY(c.alloc_t(&c.sn, m + 1)); TRY(c.alloc_t(&c.g, m + 2)); TRY(c.alloc_t(&c.y, m + 1));
     TRY(c.alloc_t(&c.partial, (size_t)(m + 1) * RED_CTAS));
     TRY(c.alloc_t(&c.dpart, RED_CTAS));
     TRY(c.alloc_t(&c.nrm, 4));
     TRY(c.alloc_t(&c.status, 4));
-    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hstatus, 8 * sizeof(double)));
+    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hstatus, 8 * (size_t)(m + 2) * sizeof(double)));
+    BAH_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    c.ig.assign(m, Ctx::IterGraph());
+    c.itev.assign(m, nullptr);
+    for (int j = 0; j < m; ++j) BAH_CUDA_TRY(cudaEventCreateWithFlags(&c.itev[j], cudaEventDisableTiming));
+    if (const char* e = getenv("BAH_NO_GRAPHS")) c.use_graphs = (e[0] == '0');
+    if (const char* e = getenv("BAH_FUSED")) c.fused = (e[0] == '1');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
     return BAH_OK;
@@ -426,15 +504,112 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // FGMRES for one right-hand side (device vectors b, x; b is sanitised)
 // ---------------------------------------------------------------------------
-static int read_status(Ctx& c, cudaStream_t st) {
-    BAH_CUDA_TRY(cudaMemcpyAsync(c.hstatus, c.status, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+static int read_scalar(Ctx& c, const double* d, double* h, cudaStream_t st) {
+    double* slot = c.hstatus + 8 * (size_t)(c.m + 1);
+    BAH_CUDA_TRY(cudaMemcpyAsync(slot, d, sizeof(double), cudaMemcpyDeviceToHost, st));
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    *h = *slot;
     return BAH_OK;
 }
-static int read_scalar(Ctx& c, const double* d, double* h, cudaStream_t st) {
-    BAH_CUDA_TRY(cudaMemcpyAsync(c.hstatus + 4, d, sizeof(double), cudaMemcpyDeviceToHost, st));
-    BAH_CUDA_TRY(cudaStreamSynchronize(st));
-    *h = c.hstatus[4];
+
+// One FGMRES step j (everything between two status reads): z_j = P^{-1} D v_j,
+// w = H z_j, Gram-Schmidt with selective reorthogonalisation, Givens update,
+// v_{j+1} = w / ||w||, and the copy of the step's status to pinned slot j.
+static void iter_body(Ctx& c, int j, cudaStream_t st) {
+    const size_t n = c.vec_len();
+    const int m = c.m;
+    double2* vj = c.V + (size_t)j * n;
+    void* zj = (char*)c.Z + (size_t)j * n * c.vsz;
+    precond_any(c, vj, zj, st);
+    op_apply_z(c, zj, c.W, st);
+    const double k1 = j + 1;
+    {
+        Prof pr(c, BAH_K_DOT, st, (k1 + 1) * n * 16.0, 2);
+        launch_dot_norm(c.V, n, j + 1, c.W, n, c.partial, c.h1v, nullptr, st);
+    }
+    {
+        Prof pr(c, BAH_K_AXPY, st, (k1 + 2) * n * 16.0);
+        launch_axpy_norm(c.V, n, j + 1, c.h1v, c.W, n, c.dpart, nullptr, st);
+    }
+    {
+        Prof pr(c, BAH_K_NORM, st, 0.0);
+        launch_dgks_decide(c.dpart, c.h1v, j + 1, c.gsflag, c.nrm + 2, st);
+    }
+    {
+        Prof pr(c, BAH_K_DOT, st, 0.0, 2);      // runs only when the flag is set (bytes counted as zero)
+        launch_dot_norm(c.V, n, j + 1, c.W, n, c.partial, c.h2v, c.gsflag, st);
+    }
+    {
+        Prof pr(c, BAH_K_AXPY, st, 0.0);
+        launch_axpy_norm(c.V, n, j + 1, c.h2v, c.W, n, c.dpart, c.gsflag, st);
+    }
+    {
+        Prof pr(c, BAH_K_SMALL, st, n * 32.0, 3);
+        launch_pass2_norm(c.dpart, c.gsflag, c.nrm + 2, st);
+        launch_arnoldi_givens(c.Hm + (size_t)j * (m + 1), c.h1v, c.h2v, c.nrm + 2, j, c.cs, c.sn, c.g, c.status, st);
+        launch_scale_copy(c.W, c.nrm + 2, c.V + (size_t)(j + 1) * n, n, 1, st);
+    }
+    cudaMemcpyAsync(c.hstatus + 8 * (size_t)j, c.status, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+}
+
+static int ensure_graph(Ctx& c, int j) {
+    Ctx::IterGraph& G = c.ig[j];
+    if (G.exec && G.mask == c.tmask) return BAH_OK;
+    Ctx::clear_graph(G);
+    G.mask = c.tmask;
+    BAH_CUDA_TRY(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    c.capturing = &G;
+    iter_body(c, j, c.cap_stream);
+    c.capturing = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c.cap_stream, &g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        Ctx::clear_graph(G);
+        set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
+        return BAH_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&G.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        Ctx::clear_graph(G);
+        set_error(std::string("graph instantiate failed: ") + cudaGetErrorString(e));
+        return BAH_ERR_CUDA;
+    }
+    return BAH_OK;
+}
+
+static int launch_iter(Ctx& c, int j, cudaStream_t st) {
+    if (c.use_graphs) {
+        int s = ensure_graph(c, j);
+        if (s != BAH_OK) {
+            c.use_graphs = false;     // fall back to direct launches from now on
+        } else {
+            Ctx::IterGraph& G = c.ig[j];
+            BAH_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+            c.launches += G.launches;
+            for (int k = 0; k < 16; ++k) {
+                c.cls_launch[k] += G.cls_launch[k];
+                c.cls_calls[k] += G.cls_calls[k];
+                c.cls_bytes[k] += G.cls_bytes[k];
+            }
+        }
+    }
+    if (!c.use_graphs) iter_body(c, j, st);
+    BAH_CUDA_TRY(cudaEventRecord(c.itev[j], st));
+    return BAH_OK;
+}
+
+static int finish_iter(Ctx& c, int j) {
+    BAH_CUDA_TRY(cudaEventSynchronize(c.itev[j]));
+    if (c.use_graphs && c.ig[j].exec) {
+        for (auto& e : c.ig[j].ev) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) == cudaSuccess) c.cls_ms[e.first] += ms;
+            else cudaGetLastError();
+        }
+    }
     return BAH_OK;
 }
 
@@ -456,8 +631,9 @@ static int fgmres_one(Ctx& c, const double2* b, double2* x, double rtol, bah_sta
         return std::isfinite(nb) ? BAH_OK : BAH_ERR_NONFINITE;
     }
     BAH_CUDA_TRY(cudaMemcpyAsync(c.R, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    double beta = nb;
     BAH_CUDA_TRY(cudaMemcpyAsync(c.nrm, c.nrm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    BAH_CUDA_TRY(cudaMemsetAsync(c.nrm + 3, 0, sizeof(double), st));
+    double beta = nb;
     int total = 0;
     double est = 1.0;
     while (beta > rtol * nb && total < c.o.maxit) {
@@ -467,54 +643,22 @@ static int fgmres_one(Ctx& c, const double2* b, double2* x, double rtol, bah_sta
             launch_scale_copy(c.R, c.nrm, c.V, n, 1, st);
             launch_init_arnoldi(c.nrm, c.g, m, c.status, st);
         }
+        const int mm = std::min(m, c.o.maxit - total);
         int jdone = 0;
         bool stop = false;
-        for (int j = 0; j < m && total < c.o.maxit; ++j) {
-            double2* vj = c.V + (size_t)j * n;
-            void* zj = (char*)c.Z + (size_t)j * n * c.vsz;
-            precond_any(c, vj, zj, st);
-            op_apply_z(c, zj, c.W, st);
-            // two-pass classical Gram-Schmidt
-            const double k1 = j + 1;
-            {
-                Prof pr(c, BAH_K_DOT, st, (k1 + 1) * n * 16.0, 2);
-                launch_multi_dot(c.V, n, j + 1, c.W, n, c.partial, c.h1v, st);
-            }
-            {
-                Prof pr(c, BAH_K_AXPY, st, (k1 + 2) * n * 16.0);
-                launch_multi_axpy_sub(c.V, n, j + 1, c.h1v, c.W, n, st);
-            }
-            {
-                Prof pr(c, BAH_K_DOT, st, (k1 + 1) * n * 16.0, 2);
-                launch_multi_dot(c.V, n, j + 1, c.W, n, c.partial, c.h2v, st);
-            }
-            {
-                Prof pr(c, BAH_K_AXPY, st, (k1 + 2) * n * 16.0);
-                launch_multi_axpy_sub(c.V, n, j + 1, c.h2v, c.W, n, st);
-            }
-            {
-                Prof pr(c, BAH_K_NORM, st, n * 16.0, 2);
-                launch_norm2(c.W, n, c.dpart, c.nrm + 2, st);
-            }
-            {
-                Prof pr(c, BAH_K_SMALL, st, n * 32.0, 2);
-                launch_arnoldi_givens(c.Hm + (size_t)j * (m + 1), c.h1v, c.h2v, c.nrm + 2, j, c.cs, c.sn, c.g,
-                                      c.status, st);
-                launch_scale_copy(c.W, c.nrm + 2, c.V + (size_t)(j + 1) * n, n, 1, st);
-            }
-            BAH_CUDA_TRY(cudaGetLastError());
+        TRY(launch_iter(c, 0, st));
+        for (int j = 0; j < mm; ++j) {
+            if (j + 1 < mm) TRY(launch_iter(c, j + 1, st));    // queued behind step j
+            TRY(finish_iter(c, j));
+            const double* hs = c.hstatus + 8 * (size_t)j;
             ++total;
             jdone = j + 1;
-            TRY(read_status(c, st));
-            est = c.hstatus[0] / nb;
-            if (c.hstatus[2] != 0.0 || !std::isfinite(est)) { s.status = BAH_ERR_NONFINITE; stop = true; break; }
+            est = hs[0] / nb;
+            if (hs[2] != 0.0 || !std::isfinite(est)) { s.status = BAH_ERR_NONFINITE; stop = true; break; }
             if (est <= rtol) break;
-            if (c.hstatus[1] <= 1e-14 * nb) break;     // (lucky) breakdown: the Krylov space is invariant
+            if (hs[1] <= 1e-14 * nb) break;     // (lucky) breakdown: the Krylov space is invariant
         }
-        if (s.status == BAH_ERR_NONFINITE) {
-            // keep the last finite iterate in x
-            break;
-        }
+        if (s.status == BAH_ERR_NONFINITE) break;   // x keeps the last finite iterate
         {
             Prof pr(c, BAH_K_SMALL, st, 0.0);
             launch_triangular_solve(c.Hm, m + 1, c.g, jdone, c.y, st);
@@ -533,6 +677,7 @@ static int fgmres_one(Ctx& c, const double2* b, double2* x, double rtol, bah_sta
             Prof pr(c, BAH_K_NORM, st, n * 16.0, 2);
             launch_norm2(c.R, n, c.dpart, c.nrm, st);
         }
+        BAH_CUDA_TRY(cudaGetLastError());
         TRY(read_scalar(c, c.nrm, &beta, st));
         s.restarts++;
         if (!std::isfinite(beta)) { s.status = BAH_ERR_NONFINITE; break; }
@@ -573,7 +718,7 @@ void bah_default_opts(bah_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->precision = BAH_MIXED;
     o->levels = 0;
-    o->max_coarse_cells = 256;
+    o->max_coarse_cells = 1024;
     o->cycle = BAH_CYCLE_V;
     o->nu_pre = 1;
     o->nu_post = 2;
@@ -650,7 +795,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
                 a /= 2; b /= 2; ++L;
             }
         } else {
-            const int maxc = o.max_coarse_cells > 0 ? o.max_coarse_cells : 256;
+            const int maxc = o.max_coarse_cells > 0 ? o.max_coarse_cells : 1024;
             while ((long long)a * b > maxc && a % 2 == 0 && b % 2 == 0 && a / 2 >= 2 && b / 2 >= 2) {
                 a /= 2; b /= 2; ++L;
             }

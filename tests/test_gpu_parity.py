@@ -316,3 +316,48 @@ def test_multiple_rhs_sequential(systems):
         xc = W.padded_to_compact(xh[k], p.n)
         assert np.linalg.norm(bc - S.H @ xc) / np.linalg.norm(bc) <= 1e-8
     s.close()
+
+
+def test_graph_and_direct_launch_paths_agree(systems, monkeypatch):
+    """The per-step CUDA graphs replay exactly the kernels of the direct launch
+    path: identical iterates, bit for bit."""
+    p, S = get("random_48x40", systems)
+    b = to_dev(W.point_source(p))
+    s1 = bah.Solver.from_problem(p, maxit=30)
+    x1, _, st1 = s1.solve(b)
+    monkeypatch.setenv("BAH_NO_GRAPHS", "1")
+    s2 = bah.Solver.from_problem(p, maxit=30)
+    x2, _, st2 = s2.solve(b)
+    assert st1[0]["iters"] == st2[0]["iters"]
+    assert torch.equal(x1, x2)
+    s1.close()
+    s2.close()
+
+
+def test_profile_counters(systems):
+    """Launch and byte counters advance and timed classes report device time."""
+    p, S = get("c1", systems)
+    s = bah.Solver.from_problem(p, maxit=5)
+    bah.bah_profile_control(s.ctx, 1 << 3, True)
+    s.solve(to_dev(W.point_source(p)))
+    pr = bah.bah_profile_read(s.ctx)
+    assert pr["launches"] > 5 * 20
+    assert pr["classes"]["jacobi"]["ms"] > 0 and pr["classes"]["jacobi"]["bytes"] > 0
+    assert pr["classes"]["dot"]["ms"] == 0
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fused_schedule_matches_oracle(prec, systems, monkeypatch):
+    """The fused multigrid schedule (pre-smoothing + residual + restriction in
+    one kernel, prolongation + first post-sweep in another) gives the same
+    preconditioner as the oracle."""
+    monkeypatch.setenv("BAH_FUSED", "1")
+    p, S = get("layered_64x32", systems)
+    s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=3)
+    pc = precond.multigrid(S, 3, precond.default_alpha(3), precision=prec)
+    r = W.random_vector(p.n, 33)
+    z = to_host(s.apply_preconditioner(to_dev(r)))
+    ref = pc.apply(W.padded_to_compact(r, p.n))
+    assert rel(W.padded_to_compact(z, p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
+    s.close()
