@@ -202,6 +202,34 @@ int bah_profile_control(bah_ctx* ctx, unsigned timing_mask, int reset);
 /* Read the counters (waits for pending timing events).  Synchronous. */
 int bah_profile_read(bah_ctx* ctx, bah_profile* out);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free relative residual.  The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc at the point where they
+ * need the number -- code running inside CUDA stream capture (an allocation
+ * there breaks the capture), real-time loops that forbid allocator calls
+ * after start-up, and hosts whose device memory belongs to another
+ * allocator.
+ *
+ * relres[k] = ||b_k - H x_k||_2 / ||b_k||_2 (0 when b_k = 0) for k < nrhs,
+ * written to the DEVICE array relres (nrhs doubles) on the stream, without
+ * synchronising.  b, x: nrhs device vectors in the layout above
+ * (boundary-normal entries read as zero).
+ *
+ * Scratch: the per-block partial sums live in one file-scope device array of
+ * 2 * BAH_STATIC_MAX_RHS * 296 doubles (296 KiB), which every GPU that loads
+ * the library holds until the process exits.  The call launches two kernels
+ * and allocates nothing (no cudaMalloc, no allocating library routine).
+ * The first call on a device looks up that array's device address with the
+ * device current; make that first call before any stream capture.  Every
+ * call overwrites the slots it reads, so nothing needs clearing, but all
+ * calls share the array: calls that overlap on the GPU (other streams or
+ * threads) race and must be serialised by the caller.
+ * Errors: BAH_ERR_ARG (NULL pointer, nrhs < 0, nrhs > BAH_STATIC_MAX_RHS),
+ * BAH_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+#define BAH_STATIC_MAX_RHS 64
+int bah_residual_norm_static(bah_ctx* ctx, const void* b, const void* x, int nrhs, double* relres, void* stream);
+
 /* Name of a status code (static string). */
 const char* bah_status_string(int status);
 

@@ -36,7 +36,9 @@ BAH_INTERGRID_MIXED = 1
 # every symbol include/bah.h declares
 EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_apply_operator",
            "bah_apply_preconditioner", "bah_solve", "bah_block_cycle", "bah_level_stencil",
-           "bah_status_string", "bah_last_error", "bah_profile_control", "bah_profile_read")
+           "bah_status_string", "bah_last_error", "bah_profile_control", "bah_profile_read",
+           "bah_residual_norm_static")
+BAH_STATIC_MAX_RHS = 64
 
 
 class bah_grid(C.Structure):
@@ -103,6 +105,8 @@ def lib():
         L.bah_profile_control.restype = C.c_int
         L.bah_profile_read.argtypes = [vp, vp]
         L.bah_profile_read.restype = C.c_int
+        L.bah_residual_norm_static.argtypes = [vp, vp, vp, C.c_int, vp, vp]
+        L.bah_residual_norm_static.restype = C.c_int
         L.bah_status_string.argtypes = [C.c_int]
         L.bah_status_string.restype = C.c_char_p
         L.bah_last_error.argtypes = []
@@ -238,6 +242,13 @@ def bah_profile_read(ctx):
     p = bah_profile()
     _check(lib().bah_profile_read(ctx, C.byref(p)), "bah_profile_read")
     return p.as_dict()
+
+
+def bah_residual_norm_static(ctx, b, x, nrhs, relres, stream=None):
+    """relres (device, nrhs doubles) = ||b - H x|| / ||b|| per right-hand side,
+    computed without allocating (static device scratch); see include/bah.h."""
+    return _check(lib().bah_residual_norm_static(ctx, _ptr(b), _ptr(x), int(nrhs), _ptr(relres), _stream(stream)),
+                  "bah_residual_norm_static")
 
 
 # ---------------------------------------------------------------------------

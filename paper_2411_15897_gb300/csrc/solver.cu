@@ -711,6 +711,11 @@ struct bah_ctx {
     Ctx c;
 };
 
+namespace bah {
+const OpCoef* context_op(const bah_ctx* ctx) { return &ctx->c.op; }
+size_t context_vec_len(const bah_ctx* ctx) { return ctx->c.vec_len(); }
+}  // namespace bah
+
 extern "C" {
 
 void bah_default_opts(bah_opts* o) {
