@@ -185,7 +185,8 @@ int bah_level_stencil(const bah_ctx* ctx, int block, int level, double* out, int
 #define BAH_K_NORM     10   /* 2-norms (2 kernels) */
 #define BAH_K_UPDATE   11   /* x += Z y */
 #define BAH_K_SMALL    12   /* Givens update, triangular solve, scaling, copies, conversions */
-#define BAH_NKCLASS    13
+#define BAH_K_COOP     13   /* cooperative launch running all levels below the fine grid */
+#define BAH_NKCLASS    14
 
 typedef struct {
     long long launches;             /* kernels launched since the last reset */

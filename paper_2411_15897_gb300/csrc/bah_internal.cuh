@@ -103,6 +103,26 @@ template <class V, class CC> struct LvlSet {
     LvlBlk<V, CC> blk[3];
 };
 
+// device-resident descriptor of one multigrid level for the cooperative cycle
+struct CoopLevel {
+    int n1, n2;
+    double w;                 // Jacobi damping on this level
+    const void* S[3];         // stencils (storage precision), levels >= 1
+    int rx[3], rz[3];
+    void* b[3];               // right-hand side, iterate and temporary per block
+    void* x[3];
+    void* t[3];
+};
+struct CoopArgs {
+    const CoopLevel* lv;      // device array indexed by level
+    int l0, L, b0, nb, nu_pre, nu_post, intergrid;
+    const double2* inv[3];    // coarsest FP64 inverses
+    double2* bc64[3];         // coarsest right-hand side in FP64
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* err;
+};
+
 // FP64 stencil of one block on one level (setup and test hook)
 struct StencilF64 {
     double2* S = nullptr;   // [(2rz+1)(2rx+1)][n1*n2]
@@ -153,6 +173,8 @@ template <int MODE>
 void launch_prolong_smooth(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
                            const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
                            const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st);
+template <int MODE>
+int launch_coop_cycle(const CoopArgs& a, int max_radius, int nsm, cudaStream_t st);
 template <int MODE>
 void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
                          typename Prec<MODE>::V* const* x, cudaStream_t st);

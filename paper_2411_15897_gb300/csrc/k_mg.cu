@@ -10,6 +10,7 @@
 #include "intergrid.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace bah {
 
@@ -497,5 +498,262 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
                                               const Prec<MODE>::V* const*, cudaStream_t);
 INST(BAH_FP64)
 INST(BAH_MIXED)
+
+}  // namespace bah
+
+// ===========================================================================
+// Cooperative multigrid: all levels l0..L-1 of a block set in one launch.
+// A persistent grid (co-residency checked by the cooperative launch) walks
+// the cycle phase by phase -- zero-guess Jacobi, residual, restriction, ...,
+// coarsest FP64 solve, prolongation, post-smoothing -- with a grid barrier
+// between phases.  The barrier's spin is bounded: on time-out it raises the
+// error flag and the kernel carries on without waiting (the host reports
+// the flag as a failed solve).
+// ===========================================================================
+namespace bah {
+
+template <int MODE>
+__device__ __forceinline__ typename MGT<MODE>::V coop_x0(const typename MGT<MODE>::CC* S, int rx, int rz, int np,
+                                                         int type, int n1, int g, const typename MGT<MODE>::V* b,
+                                                         typename MGT<MODE>::R w) {
+    using V = typename MGT<MODE>::V;
+    const int gi = g % n1, gj = g / n1;
+    if (!valid_pt(type, gi, gj)) return czero<V>();
+    const V dg = ldc(S[(size_t)(rz * (2 * rx + 1) + rx) * np + g]);
+    return cscale(cdiv(b[g], dg), w);
+}
+
+__constant__ unsigned g_barrier_sleep_ns = 32;
+
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vg = gen;
+        const unsigned g = *vg;
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vg == g) {
+                if (++spins > (1ull << 24)) {      // well over a second with the back-off below
+                    atomicExch(err, 1);
+                    break;
+                }
+                if (g_barrier_sleep_ns) __nanosleep(g_barrier_sleep_ns);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <int MODE, int RM>
+__global__ void __launch_bounds__(256) k_coop_cycle(CoopArgs a) {
+    using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
+    using CC = typename MGT<MODE>::CC;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gsz = (long long)gridDim.x * blockDim.x;
+    const int nb = a.nb;
+    auto lvl = [&](int l) -> const CoopLevel& { return a.lv[l]; };
+    auto sync = [&]() { grid_barrier(a.bar_count, a.bar_gen, a.err); };
+    auto apply = [&](const CoopLevel& L, int z, int t, const V* x) -> V {
+        const int n1 = L.n1, n2 = L.n2;
+        auto X = [&](int g) { return x[g]; };
+        return apply_stencil_fn<MODE, RM>((const CC*)L.S[z], L.rx[z], L.rz[z], n1, n2, t % n1, t / n1, t, X);
+    };
+    auto diag = [&](const CoopLevel& L, int z, int t) -> V {
+        const int np = L.n1 * L.n2;
+        return ldc(((const CC*)L.S[z])[(size_t)(L.rz[z] * (2 * L.rx[z] + 1) + L.rx[z]) * np + t]);
+    };
+    // phase: x_out = x_in + w D^-1 (b - A x_in)  (zero: w D^-1 b)
+    auto jacobi = [&](int l, V* const* xin, V* const* xout, bool zero) {
+        const CoopLevel& L = lvl(l);
+        const int np = L.n1 * L.n2;
+        const R w = (R)L.w;
+        for (long long idx = gtid; idx < (long long)nb * np; idx += gsz) {
+            const int z = (int)(idx / np), t = (int)(idx % np);
+            const int type = a.b0 + z;
+            const V* b = (const V*)L.b[z];
+            if (!valid_pt(type, t % L.n1, t / L.n1)) { xout[z][t] = czero<V>(); continue; }
+            const V dg = diag(L, z, t);
+            if (zero) { xout[z][t] = cscale(cdiv(b[t], dg), w); continue; }
+            const V ax = apply(L, z, t, xin[z]);
+            const V corr = cdiv(csub(b[t], ax), dg);
+            const V xv = xin[z][t];
+            xout[z][t] = cmk<V>(xv.x + w * corr.x, xv.y + w * corr.y);
+        }
+    };
+    auto residual = [&](int l, V* const* x, V* const* r) {
+        const CoopLevel& L = lvl(l);
+        const int np = L.n1 * L.n2;
+        for (long long idx = gtid; idx < (long long)nb * np; idx += gsz) {
+            const int z = (int)(idx / np), t = (int)(idx % np);
+            const int type = a.b0 + z;
+            if (!valid_pt(type, t % L.n1, t / L.n1)) { r[z][t] = czero<V>(); continue; }
+            r[z][t] = csub(((const V*)L.b[z])[t], apply(L, z, t, x[z]));
+        }
+    };
+    auto restrict_ = [&](int l, V* const* r) {      // into level l+1's right-hand side
+        const CoopLevel& L = lvl(l);
+        const CoopLevel& Lc = lvl(l + 1);
+        const int n1 = L.n1, n2 = L.n2, n1c = Lc.n1, npc = Lc.n1 * Lc.n2;
+        const bool to_coarsest = (l + 1 == a.L - 1);
+        for (long long idx = gtid; idx < (long long)nb * npc; idx += gsz) {
+            const int z = (int)(idx / npc), t = (int)(idx % npc);
+            const int type = a.b0 + z;
+            const int I = t % n1c, J = t / n1c;
+            V acc = czero<V>();
+            if (valid_pt(type, I, J)) {
+                const bool nodx = type == 0, nodz = type == 1;
+                for (int fj = 2 * J - 2; fj <= 2 * J + 3; ++fj) {
+                    const R wz = rw_axis_t<R>(nodz, a.intergrid, n2, J, fj);
+                    if (wz == R(0)) continue;
+                    for (int fi = 2 * I - 2; fi <= 2 * I + 3; ++fi) {
+                        const R wxw = rw_axis_t<R>(nodx, a.intergrid, n1, I, fi);
+                        if (wxw == R(0)) continue;
+                        const V v = r[z][fj * n1 + fi];
+                        acc.x += wz * wxw * v.x;
+                        acc.y += wz * wxw * v.y;
+                    }
+                }
+            }
+            if (to_coarsest) a.bc64[z][t] = make_double2((double)acc.x, (double)acc.y);
+            else ((V*)Lc.b[z])[t] = acc;
+        }
+    };
+    auto prolong = [&](int l, V* const* x, const V* const* e) {
+        const CoopLevel& L = lvl(l);
+        const int n1 = L.n1, n2 = L.n2, n1c = n1 / 2, np = n1 * n2;
+        for (long long idx = gtid; idx < (long long)nb * np; idx += gsz) {
+            const int z = (int)(idx / np), t = (int)(idx % np);
+            const int type = a.b0 + z;
+            const int i = t % n1, j = t / n1;
+            if (!valid_pt(type, i, j)) continue;
+            const bool nodx = type == 0, nodz = type == 1;
+            V acc = czero<V>();
+            for (int cj = (j >> 1) - 1; cj <= (j >> 1) + 1; ++cj) {
+                const R pz = pw_axis_t<R>(nodz, n2, j, cj);
+                if (pz == R(0)) continue;
+                for (int ci = (i >> 1) - 1; ci <= (i >> 1) + 1; ++ci) {
+                    const R px = pw_axis_t<R>(nodx, n1, i, ci);
+                    if (px == R(0)) continue;
+                    const V v = e[z][cj * n1c + ci];
+                    acc.x += px * pz * v.x;
+                    acc.y += px * pz * v.y;
+                }
+            }
+            x[z][t] = cadd(x[z][t], acc);
+        }
+    };
+    auto coarse = [&]() {                            // x_{L-1} = A_c^{-1} b_{L-1} (FP64), one warp per row
+        const CoopLevel& L = lvl(a.L - 1);
+        const int npts = L.n1 * L.n2;
+        const long long warp = gtid >> 5, nwarps = gsz >> 5;
+        const int lane = threadIdx.x & 31;
+        for (long long row = warp; row < (long long)nb * npts; row += nwarps) {
+            const int z = (int)(row / npts), rr = (int)(row % npts);
+            const double2* arow = a.inv[z] + (size_t)rr * npts;
+            const double2* bb = a.bc64[z];
+            double re = 0.0, im = 0.0;
+            for (int c = lane; c < npts; c += 32) {
+                const double2 m = arow[c], v = bb[c];
+                re += m.x * v.x - m.y * v.y;
+                im += m.x * v.y + m.y * v.x;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (lane == 0) ((V*)L.x[z])[rr] = cmk<V>((R)re, (R)im);
+        }
+    };
+
+    V* X[3]; V* T[3];
+    // ---- down ----
+    for (int l = a.l0; l < a.L - 1; ++l) {
+        const CoopLevel& L = lvl(l);
+        for (int z = 0; z < nb; ++z) { X[z] = (V*)L.x[z]; T[z] = (V*)L.t[z]; }
+        jacobi(l, nullptr, X, true);
+        sync();
+        for (int s = 1; s < a.nu_pre; ++s) {
+            jacobi(l, X, T, false);
+            sync();
+            for (int z = 0; z < nb; ++z) { V* q = X[z]; X[z] = T[z]; T[z] = q; }
+        }
+        residual(l, X, T);
+        sync();
+        restrict_(l, T);
+        sync();
+    }
+    coarse();
+    sync();
+    // ---- up ----
+    for (int l = a.L - 2; l >= a.l0; --l) {
+        const CoopLevel& L = lvl(l);
+        const CoopLevel& Lc = lvl(l + 1);
+        // the pre-smoothing result sits in L.x (nu_pre - 1 swaps are undone by the pairing below)
+        for (int z = 0; z < nb; ++z) {
+            X[z] = (a.nu_pre % 2 == 1) ? (V*)L.x[z] : (V*)L.t[z];
+            T[z] = (a.nu_pre % 2 == 1) ? (V*)L.t[z] : (V*)L.x[z];
+        }
+        const V* E[3];
+        for (int z = 0; z < nb; ++z) E[z] = (const V*)Lc.x[z];
+        prolong(l, X, E);
+        sync();
+        for (int s = 0; s < a.nu_post; ++s) {
+            jacobi(l, X, T, false);
+            sync();
+            for (int z = 0; z < nb; ++z) { V* q = X[z]; X[z] = T[z]; T[z] = q; }
+        }
+        if (X[0] != (V*)L.x[0]) {                     // leave the result in L.x
+            const int np = L.n1 * L.n2;
+            for (long long idx = gtid; idx < (long long)nb * np; idx += gsz) {
+                const int z = (int)(idx / np), t = (int)(idx % np);
+                ((V*)L.x[z])[t] = X[z][t];
+            }
+            sync();
+        }
+    }
+}
+
+template <int MODE>
+int launch_coop_cycle(const CoopArgs& a, int max_radius, int nsm, cudaStream_t st) {
+    const void* fn = max_radius <= 1 ? (const void*)k_coop_cycle<MODE, 1> : (const void*)k_coop_cycle<MODE, 2>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return -1;
+    }
+    int cap = 1;
+    if (const char* e = getenv("BAH_COOP_CTAS_PER_SM")) cap = atoi(e) > 0 ? atoi(e) : 1;
+    per_sm = per_sm > cap ? cap : per_sm;
+    static bool sleep_set = false;
+    if (!sleep_set) {
+        unsigned ns = 32;
+        if (const char* e = getenv("BAH_COOP_SLEEP_NS")) ns = (unsigned)atoi(e);
+        cudaMemcpyToSymbol(g_barrier_sleep_ns, &ns, sizeof(ns));
+        sleep_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsm * per_sm);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = max_radius <= 1 ? cudaLaunchKernelEx(&cfg, k_coop_cycle<MODE, 1>, a)
+                                    : cudaLaunchKernelEx(&cfg, k_coop_cycle<MODE, 2>, a);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+template int launch_coop_cycle<BAH_FP64>(const CoopArgs&, int, int, cudaStream_t);
+template int launch_coop_cycle<BAH_MIXED>(const CoopArgs&, int, int, cudaStream_t);
 
 }  // namespace bah

@@ -86,6 +86,13 @@ struct Ctx {
     std::vector<cudaEvent_t> itev;
     bool use_graphs = true;
     bool fused = false;                  // fused multigrid kernels (BAH_FUSED=1) when nu_pre == 1 and nu_post >= 1
+    // cooperative cycle over levels 1..L-1 (one launch per block set)
+    bool coop = false;                   // opt-in (BAH_COOP=1): measured slower than separate launches
+    int nsm = 0;
+    CoopLevel* coop_lv[4] = {nullptr, nullptr, nullptr, nullptr};   // device descriptors per block set
+    double2* bc64[3] = {nullptr, nullptr, nullptr};
+    unsigned* bar = nullptr;                      // [0] count, [1] generation
+    int* coop_err = nullptr;
 
     static void clear_graph(IterGraph& G) {
         if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -254,6 +261,33 @@ struct MG {
         return t;
     }
 
+    // levels 1..L-1 of the cycle in one cooperative launch: right-hand side in
+    // vB[1], result in vX[1]
+    static void coop_levels(Ctx& c, int b0, int nb, cudaStream_t st) {
+        CoopArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.lv = c.coop_lv[b0 == 2 ? 0 : (b0 == 1 ? 3 : (nb == 2 ? 1 : 2))];
+        a.l0 = 1; a.L = c.L; a.b0 = b0; a.nb = nb;
+        a.nu_pre = c.o.nu_pre; a.nu_post = c.o.nu_post; a.intergrid = c.o.intergrid;
+        int rmax = 1;
+        for (int z = 0; z < nb; ++z) {
+            a.inv[z] = c.inv[b0 + z];
+            a.bc64[z] = c.bc64[b0 + z];
+            rmax = std::max(rmax, std::max(c.s64[1][b0 + z].rx, c.s64[1][b0 + z].rz));
+        }
+        a.bar_count = c.bar; a.bar_gen = c.bar + 1; a.err = c.coop_err;
+        double bytes = 0;
+        const double vs = sizeof(V), ccs = sizeof(CC);
+        for (int l = 1; l < c.L - 1; ++l) {
+            const double npl = (double)c.ln1[l] * c.ln2[l];
+            bytes += 14.5 * vs * npl * nb + 3.0 * coef_bytes(c, l, b0, nb) + ccs * npl * nb;
+        }
+        const double npc = (double)c.ln1[c.L - 1] * c.ln2[c.L - 1];
+        bytes += nb * (npc * npc * 16.0 + 32.0 * npc);
+        Prof pr(c, BAH_K_COOP, st, bytes);
+        launch_coop_cycle<MODE>(a, rmax, c.nsm, st);
+    }
+
     // Result of one cycle with zero initial guess on level l for blocks
     // [b0, b0+nb): right-hand side in vB[l][b], result written to out[z].
     static void cycle(Ctx& c, int l, int b0, int nb, V* const* out, cudaStream_t st) {
@@ -325,7 +359,8 @@ struct MG {
             launch_restrict<MODE>(rs, cb, c.o.intergrid, st);
         }
         // coarse-grid correction
-        cycle(c, l + 1, b0, nb, cx, st);
+        if (l == 0 && c.coop) coop_levels(c, b0, nb, st);
+        else cycle(c, l + 1, b0, nb, cx, st);
         {
             Prof pr(c, BAH_K_PROLONG, st, nb * npl * vs * 2.25);
             launch_prolong_add<MODE>(set(c, l, b0, nb, nullptr, cur), cx, st);
@@ -474,6 +509,41 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
             BAH_CUDA_TRY(cudaMemsetAsync(c.vB[l][b], 0, npl * c.vsz, st));
             BAH_CUDA_TRY(cudaMemsetAsync(c.vT[l][b], 0, npl * c.vsz, st));
         }
+    // cooperative cycle descriptors
+    {
+        int dev = 0;
+        BAH_CUDA_TRY(cudaGetDevice(&dev));
+        BAH_CUDA_TRY(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
+        int coopok = 0;
+        BAH_CUDA_TRY(cudaDeviceGetAttribute(&coopok, cudaDevAttrCooperativeLaunch, dev));
+        if (const char* e = getenv("BAH_COOP")) c.coop = (e[0] == '1');
+        if (!coopok || c.L < 3) c.coop = false;
+        const int npc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
+        for (int b = 0; b < 3; ++b) TRY(c.alloc_t(&c.bc64[b], npc));
+        TRY(c.alloc(( void**)&c.bar, 2 * sizeof(unsigned)));
+        TRY(c.alloc_t(&c.coop_err, 1));
+        BAH_CUDA_TRY(cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), st));
+        BAH_CUDA_TRY(cudaMemsetAsync(c.coop_err, 0, sizeof(int), st));
+        // block sets: {p}, {u1, u2}, {u1}, {u2}
+        for (int set = 0; set < 4; ++set) {
+            const int b0 = set == 0 ? 2 : (set == 3 ? 1 : 0), nb = set == 1 ? 2 : 1;
+            std::vector<CoopLevel> lv(c.L);
+            for (int l = 0; l < c.L; ++l) {
+                CoopLevel& q = lv[l];
+                std::memset(&q, 0, sizeof(q));
+                q.n1 = c.ln1[l]; q.n2 = c.ln2[l];
+                q.w = c.o.jacobi_w[std::min(l, c.o.n_jacobi_w - 1)];
+                for (int z = 0; z < nb; ++z) {
+                    const int b = b0 + z;
+                    q.S[z] = c.sst[l][b];
+                    q.rx[z] = c.s64[l][b].rx; q.rz[z] = c.s64[l][b].rz;
+                    q.b[z] = c.vB[l][b]; q.x[z] = c.vX[l][b]; q.t[z] = c.vT[l][b];
+                }
+            }
+            TRY(c.alloc_t(&c.coop_lv[set], c.L));
+            BAH_CUDA_TRY(cudaMemcpyAsync(c.coop_lv[set], lv.data(), c.L * sizeof(CoopLevel), cudaMemcpyHostToDevice, st));
+        }
+    }
     // Krylov workspace
     const size_t n = c.vec_len();
     const int m = c.m;
@@ -952,6 +1022,15 @@ int bah_solve(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_sta
         if (s != BAH_OK && first_fail == BAH_OK) first_fail = s;
     }
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    if (c.coop) {
+        int err = 0;
+        BAH_CUDA_TRY(cudaMemcpy(&err, c.coop_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) {
+            set_error("grid barrier of the cooperative multigrid cycle timed out");
+            cudaMemset(c.coop_err, 0, sizeof(int));
+            return BAH_ERR_CUDA;
+        }
+    }
     return first_fail;
 }
 

@@ -361,3 +361,24 @@ def test_fused_schedule_matches_oracle(prec, systems, monkeypatch):
     ref = pc.apply(W.padded_to_compact(r, p.n))
     assert rel(W.padded_to_compact(z, p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cooperative_levels_match_standalone_kernels(prec, monkeypatch):
+    """With BAH_COOP=1 levels 1..L-1 run in one cooperative launch; by
+    default they run as separate kernels.  Both schedules agree, and both match
+    the oracle's preconditioner (4 levels, bilinear transfers)."""
+    p = W.layered(128, 64, 5, seed=27, abc=8)
+    S = elastic.from_problem(p)
+    r = W.random_vector(p.n, 35)
+    out = {}
+    for mode in ("coop", "plain"):
+        monkeypatch.setenv("BAH_COOP", "1" if mode == "coop" else "0")
+        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=4)
+        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
+        s.close()
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert rel(out["coop"], out["plain"]) <= tol
+    pc = precond.multigrid(S, 4, precond.default_alpha(4), precision=prec)
+    ref = pc.apply(W.padded_to_compact(r, p.n))
+    assert rel(W.padded_to_compact(out["coop"], p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
