@@ -95,6 +95,8 @@ typedef struct {
     int    intergrid;        /* BAH_INTERGRID_* */
     int    restart;          /* FGMRES restart length m (1..64) */
     int    maxit;            /* maximum FGMRES iterations per right-hand side */
+    int    rhs_block;        /* right-hand sides solved together by bah_solve (1..256); the
+                                context's workspace grows in proportion */
 } bah_opts;
 
 typedef struct {
@@ -108,7 +110,7 @@ typedef struct {
 /* Fill *opts with the defaults: BAH_MIXED, automatic levels with at most 1024
  * coarsest cells, V(1,2), Jacobi weights 0.8, 0.8, 0.3 (Sec. 4.4.1), shift by
  * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels, 0.5 deeper; Sec. 4.4.3,
- * Table 4), bilinear intergrid, FGMRES(20), maxit 5000. */
+ * Table 4), bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1. */
 void bah_default_opts(bah_opts* opts);
 
 /* Build a solver for one grid, medium and frequency.  Copies the host medium
@@ -142,7 +144,11 @@ int bah_apply_operator(bah_ctx* ctx, const void* x, void* y, int nrhs, int conj_
 int bah_apply_preconditioner(bah_ctx* ctx, const void* r, void* z, int nrhs, void* stream);
 
 /* Solve H x = b to ||b - H x||_2 <= rtol ||b||_2 by FGMRES(m) with the
- * block-acoustic preconditioner, x_0 = 0, for nrhs right-hand sides.  b and x
+ * block-acoustic preconditioner, x_0 = 0, for nrhs right-hand sides.
+ * Right-hand sides are solved rhs_block at a time in one batch: each keeps its
+ * own Krylov basis and converges on its own, while every kernel launch
+ * (stencils, multigrid levels, Gram-Schmidt) serves the whole batch and
+ * skips the members that have converged.  b and x
  * may both be device pointers, or both host pointers (then the copies to and
  * from the device are part of the call).  Synchronises the stream before
  * returning.  stats (may be NULL) receives nrhs records.  Returns BAH_OK when

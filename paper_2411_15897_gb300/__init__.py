@@ -53,7 +53,8 @@ class bah_medium(C.Structure):
 class bah_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("levels", C.c_int), ("max_coarse_cells", C.c_int), ("cycle", C.c_int),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("jacobi_w", C.c_double * 8), ("n_jacobi_w", C.c_int),
-                ("shift_alpha", C.c_double), ("intergrid", C.c_int), ("restart", C.c_int), ("maxit", C.c_int)]
+                ("shift_alpha", C.c_double), ("intergrid", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
+                ("rhs_block", C.c_int)]
 
 
 class bah_stats(C.Structure):

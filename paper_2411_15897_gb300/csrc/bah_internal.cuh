@@ -96,11 +96,14 @@ template <class V, class CC> struct LvlBlk {
     const V* b;        // right-hand side
     const V* xin;      // current iterate
     V* xout;           // output iterate / residual
+    size_t sb, sxi, sxo;   // element strides between right-hand sides (blockIdx.z)
 };
 template <class V, class CC> struct LvlSet {
     int nb;            // blocks in the set (1..3)
     int n1, n2;        // level grid
     LvlBlk<V, CC> blk[3];
+    int nrhs;          // right-hand sides in the launch (blockIdx.z)
+    const int* active; // per right-hand side, or nullptr
 };
 
 // device-resident descriptor of one multigrid level for the cooperative cycle
@@ -121,6 +124,14 @@ struct CoopArgs {
     unsigned* bar_count;
     unsigned* bar_gen;
     int* err;
+};
+
+// right-hand-side batching: element strides between consecutive right-hand
+// sides for up to three pointers of a launch (blockIdx.y or .z is the
+// right-hand side), and an optional per-right-hand-side active flag
+struct RhsStride {
+    size_t s0 = 0, s1 = 0, s2 = 0;
+    const int* active = nullptr;
 };
 
 // FP64 stencil of one block on one level (setup and test hook)
@@ -149,7 +160,8 @@ int  coarse_invert(int type, const StencilF64& S, double2* inv, double2* work, i
 
 // operator (k_ops.cu)
 template <class Vin>
-void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st);
+void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st,
+                          int nrhs = 1, RhsStride rs = RhsStride());
 
 // multigrid (k_mg.cu)
 template <int MODE>
@@ -161,10 +173,10 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
                      const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, cudaStream_t st);
 template <int MODE>
 void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
-                     typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st);
+                     typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride = 0);
 template <int MODE>
 void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
-                        const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st);
+                        const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride = 0);
 template <int MODE>
 void launch_smooth_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
                             const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
@@ -177,38 +189,52 @@ template <int MODE>
 int launch_coop_cycle(const CoopArgs& a, int max_radius, int nsm, cudaStream_t st);
 template <int MODE>
 void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
-                         typename Prec<MODE>::V* const* x, cudaStream_t st);
+                         typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs = 1, RhsStride rs = RhsStride());
 template <int MODE>
 void launch_distributor(int n1, int n2, double ihx, double ihz,
                         const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5,
-                        const double2* r, typename Prec<MODE>::V* tp, cudaStream_t st);
+                        const double2* r, typename Prec<MODE>::V* tp, cudaStream_t st, int nrhs = 1,
+                        RhsStride rs = RhsStride());
 template <int MODE>
 void launch_u_rhs(int n1, int n2, double ihx, double ihz, const double2* r, const typename Prec<MODE>::V* ep,
-                  typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st);
+                  typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st, int nrhs = 1,
+                  RhsStride rs = RhsStride());
 void launch_sanitize(double2* v, int n1, int n2, int nvec, cudaStream_t st);
 template <class Vin, class Vout>
 void launch_convert(const Vin* x, Vout* y, size_t n, cudaStream_t st);
 
-// Krylov (k_krylov.cu)
+// Krylov (k_krylov.cu), batched over right-hand sides
 constexpr int RED_CTAS = 296;   // partial sums per reduction (2 per SM on 148+ SMs)
-void launch_multi_dot(const double2* V, size_t ldv, int k, const double2* w, size_t n,
-                      double2* partial, double2* out, cudaStream_t st);
-void launch_norm2(const double2* w, size_t n, double* partial, double* out, cudaStream_t st);
-void launch_dot_norm(const double2* V, size_t ldv, int k, const double2* w, size_t n, double2* partial, double2* out,
-                     const int* flag, cudaStream_t st);
-void launch_axpy_norm(const double2* V, size_t ldv, int k, const double2* coef, double2* w, size_t n, double* npart,
-                      const int* flag, cudaStream_t st);
-void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* wn, cudaStream_t st);
-void launch_pass2_norm(const double* npart, const int* flag, double* wn, cudaStream_t st);
-void launch_multi_axpy_sub(const double2* V, size_t ldv, int k, const double2* coef, double2* w, size_t n,
-                           cudaStream_t st);
+struct KS {                     // per-right-hand-side element strides and active flags
+    size_t sv = 0;              // basis V (m+1 vectors)
+    size_t sw = 0;              // work vector w
+    size_t sp = 0;              // dot partials
+    size_t so = 0;              // small per-rhs arrays (h1, h2, cs, sn, g, y)
+    size_t sh = 0;              // Hessenberg matrix
+    size_t sz = 0;              // flexible basis Z
+    size_t sx = 0;              // solution x
+    const int* active = nullptr;
+};
+void launch_dot_norm(const double2* V, int k, const double2* w, size_t n, double2* partial, double2* out,
+                     const int* flag, int nrhs, const KS& ks, cudaStream_t st);
+void launch_axpy_norm(const double2* V, int k, const double2* coef, double2* w, size_t n, double* npart,
+                      const int* flag, int nrhs, const KS& ks, cudaStream_t st);
+void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* sc, int nrhs,
+                        const KS& ks, cudaStream_t st);
+void launch_pass2_norm(const double* npart, const int* flag, double* sc, int nrhs, const KS& ks, cudaStream_t st);
+void launch_norm2(const double2* w, size_t n, double* partial, double* sc, int slot, int nrhs, const KS& ks,
+                  cudaStream_t st);
 template <class Vz>
-void launch_update_x(const Vz* Z, size_t ldz, int k, const double2* y, double2* x, size_t n, cudaStream_t st);
-void launch_scale_copy(const double2* w, const double* nrm, double2* v, size_t n, int inverse, cudaStream_t st);
-void launch_arnoldi_givens(double2* Hcol, const double2* h1, const double2* h2, const double* wnorm, int j,
-                           double2* cs, double2* sn, double2* g, double* status, cudaStream_t st);
-void launch_triangular_solve(const double2* Hm, int ldh, const double2* g, int k, double2* y, cudaStream_t st);
-void launch_init_arnoldi(const double* beta, double2* g, int m, double* status, cudaStream_t st);
+void launch_update_x(const Vz* Z, const int* kk, const double2* y, double2* x, size_t n, int nrhs, const KS& ks,
+                     cudaStream_t st);
+void launch_scale_copy(const double2* w, const double* sc, int slot, double2* v, size_t n, size_t sw, size_t sv,
+                       int nrhs, const KS& ks, cudaStream_t st);
+void launch_arnoldi_givens(double2* Hm, int ldh, const double2* h1, const double2* h2, const double* sc, int j,
+                           double2* cs, double2* sn, double2* g, double* status, int nrhs, const KS& ks,
+                           cudaStream_t st);
+void launch_triangular_solve(const double2* Hm, int ldh, const double2* g, const int* kk, double2* y, int nrhs,
+                             const KS& ks, cudaStream_t st);
+void launch_init_arnoldi(const double* sc, double2* g, int m, double* status, int nrhs, const KS& ks, cudaStream_t st);
 
 // error handling
 void set_error(const std::string& msg);

@@ -138,24 +138,26 @@ __global__ void __launch_bounds__(256) k_jacobi(LvlSet<typename MGT<MODE>::V, ty
     const auto& B = s.blk[blockIdx.y];
     const int n1 = s.n1, n2 = s.n2, np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= np) return;
+    const int rr = blockIdx.z;
+    if (t >= np || (s.active && !s.active[rr])) return;
+    V* __restrict__ xout = B.xout + rr * B.sxo;
     const int i = t % n1, j = t / n1;
-    if (!valid_pt(B.type, i, j)) { B.xout[t] = czero<V>(); return; }
-    const V b = B.b[t];
+    if (!valid_pt(B.type, i, j)) { xout[t] = czero<V>(); return; }
+    const V b = B.b[rr * B.sb + t];
     if (zero_init) {
         const V dg = diag_only<MODE>(L0 ? &f5 : nullptr, B, np, t);
-        B.xout[t] = cscale(cdiv(b, dg), w);
+        xout[t] = cscale(cdiv(b, dg), w);
         return;
     }
-    const V* __restrict__ xin = B.xin;
+    const V* __restrict__ xin = B.xin + rr * B.sxi;
     auto X = [&](int g) { return xin[g]; };
     V ax;
     if (L0) ax = apply_fine5_fn<MODE>(f5, B.type, i, j, t, X);
     else ax = apply_stencil_fn<MODE, RM>(B.S, B.rx, B.rz, n1, n2, i, j, t, X);
     const V dg = diag_only<MODE>(L0 ? &f5 : nullptr, B, np, t);
     const V corr = cdiv(csub(b, ax), dg);
-    const V x = B.xin[t];
-    B.xout[t] = cmk<V>(x.x + w * corr.x, x.y + w * corr.y);
+    const V x = xin[t];
+    xout[t] = cmk<V>(x.x + w * corr.x, x.y + w * corr.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,15 +170,17 @@ __global__ void __launch_bounds__(256) k_residual(LvlSet<typename MGT<MODE>::V, 
     const auto& B = s.blk[blockIdx.y];
     const int n1 = s.n1, n2 = s.n2, np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= np) return;
+    const int rr = blockIdx.z;
+    if (t >= np || (s.active && !s.active[rr])) return;
+    V* __restrict__ xout = B.xout + rr * B.sxo;
     const int i = t % n1, j = t / n1;
-    if (!valid_pt(B.type, i, j)) { B.xout[t] = czero<V>(); return; }
-    const V* __restrict__ xin = B.xin;
+    if (!valid_pt(B.type, i, j)) { xout[t] = czero<V>(); return; }
+    const V* __restrict__ xin = B.xin + rr * B.sxi;
     auto X = [&](int g) { return xin[g]; };
     V ax;
     if (L0) ax = apply_fine5_fn<MODE>(f5, B.type, i, j, t, X);
     else ax = apply_stencil_fn<MODE, RM>(B.S, B.rx, B.rz, n1, n2, i, j, t, X);
-    B.xout[t] = csub(B.b[t], ax);
+    xout[t] = csub(B.b[rr * B.sb + t], ax);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,7 +322,7 @@ void launch_jacobi(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>
                    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w, int zero_init,
                    cudaStream_t st) {
     const int np = s.n1 * s.n2;
-    dim3 g((np + 255) / 256, s.nb);
+    dim3 g((np + 255) / 256, s.nb, s.nrhs);
     using R = typename Prec<MODE>::R;
     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
     if (f5) k_jacobi<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5, (R)w, zero_init);
@@ -329,7 +333,7 @@ template <int MODE>
 void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
                      const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, cudaStream_t st) {
     const int np = s.n1 * s.n2;
-    dim3 g((np + 255) / 256, s.nb);
+    dim3 g((np + 255) / 256, s.nb, s.nrhs);
     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
     if (f5) k_residual<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5);
     else if (max_radius(s) <= 1) k_residual<MODE, false, 1><<<g, 256, 0, st>>>(s, nof);
@@ -339,7 +343,7 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 // ---------------------------------------------------------------------------
 // restriction: b_c = R r_f  (r_f in blk.xout of the fine set)
 // ---------------------------------------------------------------------------
-template <class V> struct PtrSet { V* p[3]; };
+template <class V> struct PtrSet { V* p[3]; size_t s = 0; };
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> fine,
@@ -349,12 +353,13 @@ __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, 
     const auto& B = fine.blk[blockIdx.y];
     const int n1 = fine.n1, n2 = fine.n2, n1c = n1 / 2, n2c = n2 / 2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n1c * n2c) return;
+    const int rr = blockIdx.z;
+    if (t >= n1c * n2c || (fine.active && !fine.active[rr])) return;
     const int I = t % n1c, J = t / n1c;
     V acc = czero<V>();
     if (valid_pt(B.type, I, J)) {
         const bool nodx = B.type == 0, nodz = B.type == 1;
-        const V* r = B.xout;
+        const V* r = B.xout + rr * B.sxo;
         for (int fj = 2 * J - 2; fj <= 2 * J + 3; ++fj) {
             const R wz = rw_axis_t<R>(nodz, intergrid, n2, J, fj);
             if (wz == R(0)) continue;
@@ -368,16 +373,17 @@ __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, 
             }
         }
     }
-    cb.p[blockIdx.y][t] = acc;
+    cb.p[blockIdx.y][rr * cb.s + t] = acc;
 }
 
 template <int MODE>
 void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
-                     typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st) {
+                     typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride) {
     PtrSet<typename Prec<MODE>::V> cb;
     for (int z = 0; z < 3; ++z) cb.p[z] = z < fine.nb ? coarse_b[z] : nullptr;
+    cb.s = coarse_stride;
     const int npc = (fine.n1 / 2) * (fine.n2 / 2);
-    dim3 g((npc + 255) / 256, fine.nb);
+    dim3 g((npc + 255) / 256, fine.nb, fine.nrhs);
     k_restrict<MODE><<<g, 256, 0, st>>>(fine, cb, intergrid);
 }
 
@@ -392,11 +398,13 @@ __global__ void __launch_bounds__(256) k_prolong_add(LvlSet<typename MGT<MODE>::
     const auto& B = fine.blk[blockIdx.y];
     const int n1 = fine.n1, n2 = fine.n2, n1c = n1 / 2, n2c = n2 / 2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n1 * n2) return;
+    const int rr = blockIdx.z;
+    if (t >= n1 * n2 || (fine.active && !fine.active[rr])) return;
     const int i = t % n1, j = t / n1;
     if (!valid_pt(B.type, i, j)) return;
     const bool nodx = B.type == 0, nodz = B.type == 1;
-    const V* e = ce.p[blockIdx.y];
+    const V* e = ce.p[blockIdx.y] + rr * ce.s;
+    V* xo = B.xout + rr * B.sxo;
     V acc = czero<V>();
     for (int cj = (j >> 1) - 1; cj <= (j >> 1) + 1; ++cj) {
         const R pz = pw_axis_t<R>(nodz, n2, j, cj);
@@ -410,17 +418,18 @@ __global__ void __launch_bounds__(256) k_prolong_add(LvlSet<typename MGT<MODE>::
             acc.y += wgt * v.y;
         }
     }
-    V x = B.xout[t];
-    B.xout[t] = cadd(x, acc);
+    V x = xo[t];
+    xo[t] = cadd(x, acc);
 }
 
 template <int MODE>
 void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
-                        const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st) {
+                        const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride) {
     PtrSet<typename Prec<MODE>::V> ce;
     for (int z = 0; z < 3; ++z) ce.p[z] = z < fine.nb ? const_cast<typename Prec<MODE>::V*>(coarse_x[z]) : nullptr;
+    ce.s = coarse_stride;
     const int np = fine.n1 * fine.n2;
-    dim3 g((np + 255) / 256, fine.nb);
+    dim3 g((np + 255) / 256, fine.nb, fine.nrhs);
     k_prolong_add<MODE><<<g, 256, 0, st>>>(fine, ce);
 }
 
@@ -432,13 +441,15 @@ constexpr int kCoarseSmem = 3072;   // points staged in shared memory (48 KB of 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const double2> inv,
                                                       PtrSet<const typename MGT<MODE>::V> b,
-                                                      PtrSet<typename MGT<MODE>::V> x) {
+                                                      PtrSet<typename MGT<MODE>::V> x, const int* active) {
     using V = typename MGT<MODE>::V;
     const int z = blockIdx.y;
+    const int rr = blockIdx.z;
+    if (active && !active[rr]) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     extern __shared__ double2 bsh[];
-    const V* bb = b.p[z];
+    const V* bb = b.p[z] + rr * b.s;
     const bool staged = npts <= kCoarseSmem;
     if (staged) {
         // the right-hand side in FP64, converted once per CTA
@@ -460,12 +471,12 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const dou
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) x.p[z][warp] = cmk<V>((typename MGT<MODE>::R)re, (typename MGT<MODE>::R)im);
+    if (lane == 0) x.p[z][rr * x.s + warp] = cmk<V>((typename MGT<MODE>::R)re, (typename MGT<MODE>::R)im);
 }
 
 template <int MODE>
 void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
-                         typename Prec<MODE>::V* const* x, cudaStream_t st) {
+                         typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs, RhsStride rs) {
     PtrSet<const double2> pi;
     PtrSet<const typename Prec<MODE>::V> pb;
     PtrSet<typename Prec<MODE>::V> px;
@@ -474,9 +485,11 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
         pb.p[z] = z < nb ? b[z] : nullptr;
         px.p[z] = z < nb ? x[z] : nullptr;
     }
-    dim3 g((npts * 32 + 255) / 256, nb);
+    pb.s = rs.s0;
+    px.s = rs.s1;
+    dim3 g((npts * 32 + 255) / 256, nb, nrhs);
     const size_t smem = npts <= kCoarseSmem ? (size_t)npts * sizeof(double2) : 0;
-    k_coarse_apply<MODE><<<g, 256, smem, st>>>(npts, pi, pb, px);
+    k_coarse_apply<MODE><<<g, 256, smem, st>>>(npts, pi, pb, px, rs.active);
 }
 
 #define INST(MODE)                                                                                                 \
@@ -485,11 +498,11 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
     template void launch_residual<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                              \
                                         const Fine5<Prec<MODE>::C, Prec<MODE>::CC>*, cudaStream_t);                \
     template void launch_restrict<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&, Prec<MODE>::V* const*, int,  \
-                                        cudaStream_t);                                                             \
+                                        cudaStream_t, size_t);                                                     \
     template void launch_prolong_add<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                           \
-                                           const Prec<MODE>::V* const*, cudaStream_t);                             \
+                                           const Prec<MODE>::V* const*, cudaStream_t, size_t);                     \
     template void launch_coarse_apply<MODE>(int, int, const double2* const*, const Prec<MODE>::V* const*,         \
-                                            Prec<MODE>::V* const*, cudaStream_t);                                  \
+                                            Prec<MODE>::V* const*, cudaStream_t, int, RhsStride);                 \
     template void launch_smooth_restrict<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                       \
                                                const Fine5<Prec<MODE>::C, Prec<MODE>::CC>*, double,                \
                                                Prec<MODE>::V* const*, int, cudaStream_t);                          \

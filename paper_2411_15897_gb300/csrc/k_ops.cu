@@ -20,10 +20,14 @@ __device__ __forceinline__ double2 ld64(const V* p, int idx) {
 // ---------------------------------------------------------------------------
 template <class Vin>
 __global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __restrict__ x, double2* __restrict__ y,
-                                                       const double2* __restrict__ b, int conj) {
+                                                       const double2* __restrict__ b, int conj, RhsStride rs) {
     const int n1 = c.n1, n2 = c.n2, np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= np) return;
+    const int rr = blockIdx.y;
+    if (t >= np || (rs.active && !rs.active[rr])) return;
+    x += rr * rs.s0;
+    y += rr * rs.s1;
+    if (b) b += rr * rs.s2;
     const int i = t % n1, j = t / n1;
     const Vin* x1 = x;
     const Vin* x2 = x + np;
@@ -83,12 +87,15 @@ __global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __re
 }
 
 template <class Vin>
-void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st) {
+void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st,
+                          int nrhs, RhsStride rs) {
     int np = c.n1 * c.n2;
-    k_elastic_apply<Vin><<<(np + 255) / 256, 256, 0, st>>>(c, x, y, b, conj);
+    k_elastic_apply<Vin><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(c, x, y, b, conj, rs);
 }
-template void launch_elastic_apply<double2>(const OpCoef&, const double2*, double2*, const double2*, int, cudaStream_t);
-template void launch_elastic_apply<float2>(const OpCoef&, const float2*, double2*, const double2*, int, cudaStream_t);
+template void launch_elastic_apply<double2>(const OpCoef&, const double2*, double2*, const double2*, int, cudaStream_t,
+                                            int, RhsStride);
+template void launch_elastic_apply<float2>(const OpCoef&, const float2*, double2*, const double2*, int, cudaStream_t,
+                                           int, RhsStride);
 
 // ---------------------------------------------------------------------------
 // t_p = B r_u - A_p r_p   (r in FP64, t_p in the preconditioner's precision)
@@ -97,12 +104,16 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_distributor(int n1, int n2, typename Prec<MODE>::R ihx,
                                                      typename Prec<MODE>::R ihz,
                                                      Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> f,
-                                                     const double2* __restrict__ r, typename Prec<MODE>::V* __restrict__ tp) {
+                                                     const double2* __restrict__ r, typename Prec<MODE>::V* __restrict__ tp,
+                                                     RhsStride rs) {
     using V = typename Prec<MODE>::V;
     using R = typename Prec<MODE>::R;
     const int np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= np) return;
+    const int rr = blockIdx.y;
+    if (t >= np || (rs.active && !rs.active[rr])) return;
+    r += rr * rs.s0;
+    tp += rr * rs.s1;
     const int i = t % n1, j = t / n1;
     auto L = [&](int idx) { double2 v = r[idx]; return cmk<V>((R)v.x, (R)v.y); };
     const V z = czero<V>();
@@ -125,15 +136,15 @@ __global__ void __launch_bounds__(256) k_distributor(int n1, int n2, typename Pr
 template <int MODE>
 void launch_distributor(int n1, int n2, double ihx, double ihz,
                         const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5, const double2* r,
-                        typename Prec<MODE>::V* tp, cudaStream_t st) {
+                        typename Prec<MODE>::V* tp, cudaStream_t st, int nrhs, RhsStride rs) {
     int np = n1 * n2;
-    k_distributor<MODE><<<(np + 255) / 256, 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
-                                                           (typename Prec<MODE>::R)ihz, f5, r, tp);
+    k_distributor<MODE><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
+                                                                       (typename Prec<MODE>::R)ihz, f5, r, tp, rs);
 }
 template void launch_distributor<BAH_FP64>(int, int, double, double, const Fine5<double, double2>&, const double2*,
-                                           double2*, cudaStream_t);
+                                           double2*, cudaStream_t, int, RhsStride);
 template void launch_distributor<BAH_MIXED>(int, int, double, double, const Fine5<__nv_bfloat16, __nv_bfloat162>&,
-                                            const double2*, float2*, cudaStream_t);
+                                            const double2*, float2*, cudaStream_t, int, RhsStride);
 
 // ---------------------------------------------------------------------------
 // s_u = r_u - B^T e_p  (B^T = grad_h onto the interior faces)
@@ -141,12 +152,17 @@ template void launch_distributor<BAH_MIXED>(int, int, double, double, const Fine
 template <int MODE>
 __global__ void __launch_bounds__(256) k_u_rhs(int n1, int n2, typename Prec<MODE>::R ihx, typename Prec<MODE>::R ihz,
                                                const double2* __restrict__ r, const typename Prec<MODE>::V* __restrict__ ep,
-                                               typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2) {
+                                               typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, RhsStride rs) {
     using V = typename Prec<MODE>::V;
     using R = typename Prec<MODE>::R;
     const int np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= np) return;
+    const int rr = blockIdx.y;
+    if (t >= np || (rs.active && !rs.active[rr])) return;
+    r += rr * rs.s0;
+    ep += rr * rs.s1;
+    su1 += rr * rs.s2;
+    su2 += rr * rs.s2;
     const int i = t % n1, j = t / n1;
     const V e = ep[t];
     V s1 = czero<V>(), s2 = czero<V>();
@@ -166,15 +182,15 @@ __global__ void __launch_bounds__(256) k_u_rhs(int n1, int n2, typename Prec<MOD
 
 template <int MODE>
 void launch_u_rhs(int n1, int n2, double ihx, double ihz, const double2* r, const typename Prec<MODE>::V* ep,
-                  typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st) {
+                  typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st, int nrhs, RhsStride rs) {
     int np = n1 * n2;
-    k_u_rhs<MODE><<<(np + 255) / 256, 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx, (typename Prec<MODE>::R)ihz,
-                                                     r, ep, su1, su2);
+    k_u_rhs<MODE><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
+                                                                 (typename Prec<MODE>::R)ihz, r, ep, su1, su2, rs);
 }
 template void launch_u_rhs<BAH_FP64>(int, int, double, double, const double2*, const double2*, double2*, double2*,
-                                     cudaStream_t);
+                                     cudaStream_t, int, RhsStride);
 template void launch_u_rhs<BAH_MIXED>(int, int, double, double, const double2*, const float2*, float2*, float2*,
-                                      cudaStream_t);
+                                      cudaStream_t, int, RhsStride);
 
 // ---------------------------------------------------------------------------
 // element-wise precision conversion

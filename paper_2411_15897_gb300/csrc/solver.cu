@@ -29,6 +29,7 @@ void set_error(const std::string& m) { g_err = m; }
     } while (0)
 
 static const double kAlphaByLevels[5] = {0.0, 0.0, 0.1, 0.2, 0.4};
+static const int kIntSlots = 8;
 
 struct Ctx {
     int dim = 2, n1 = 0, n2 = 0, np = 0;
@@ -61,6 +62,13 @@ struct Ctx {
     void* Z = nullptr;
     double* hstatus = nullptr;           // pinned host mirror of status
     void* ztmp = nullptr;                // preconditioner output in storage precision (apply hook)
+    // right-hand-side batching
+    int nbatch = 1;                      // right-hand sides solved together
+    int* active = nullptr;               // device, per right-hand side
+    int* jk = nullptr;                   // device, Krylov dimension per right-hand side at a restart
+    int* hint = nullptr;                 // pinned host staging ring for active / jk (kIntSlots * nbatch)
+    unsigned hint_slot = 0;
+    KS ks;                               // strides of the batched Krylov workspace
 
     // profiling: launch counts, algorithmic bytes, event timing per kernel class
     unsigned tmask = 0;
@@ -107,6 +115,7 @@ struct Ctx {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         for (void* p : allocs) cudaFree(p);
         if (hstatus) cudaFreeHost(hstatus);
+        if (hint) cudaFreeHost(hint);
     }
     int alloc(void** p, size_t bytes) {
         *p = nullptr;
@@ -209,6 +218,12 @@ struct Prof {
     }
 };
 
+// right-hand sides of one launch and their active flags
+struct Batch {
+    int nr = 1;
+    const int* active = nullptr;
+};
+
 // ---------------------------------------------------------------------------
 // multigrid cycle over a set of blocks (Algorithm 1 applied recursively)
 // ---------------------------------------------------------------------------
@@ -233,9 +248,14 @@ struct MG {
         return c.o.jacobi_w[k];
     }
 
-    static LvlSet<V, CC> set(const Ctx& c, int l, int b0, int nb, V* const* xin, V* const* xout) {
+    static LvlSet<V, CC> set(const Ctx& c, int l, int b0, int nb, V* const* xin, size_t sxi, V* const* xout,
+                             size_t sxo, const Batch& bt) {
         LvlSet<V, CC> s;
+        std::memset(&s, 0, sizeof(s));
         s.nb = nb; s.n1 = c.ln1[l]; s.n2 = c.ln2[l];
+        s.nrhs = bt.nr;
+        s.active = bt.active;
+        const size_t npl = (size_t)c.ln1[l] * c.ln2[l];
         for (int z = 0; z < nb; ++z) {
             const int b = b0 + z;
             auto& B = s.blk[z];
@@ -243,8 +263,11 @@ struct MG {
             B.S = l > 0 ? (const CC*)c.sst[l][b] : nullptr;
             B.rx = c.s64[l][b].rx; B.rz = c.s64[l][b].rz;
             B.b = (const V*)c.vB[l][b];
+            B.sb = npl;
             B.xin = xin ? xin[z] : nullptr;
+            B.sxi = sxi;
             B.xout = xout[z];
+            B.sxo = sxo;
         }
         return s;
     }
@@ -261,8 +284,8 @@ struct MG {
         return t;
     }
 
-    // levels 1..L-1 of the cycle in one cooperative launch: right-hand side in
-    // vB[1], result in vX[1]
+    // levels 1..L-1 of the cycle in one cooperative launch (one right-hand
+    // side): right-hand side in vB[1], result in vX[1]
     static void coop_levels(Ctx& c, int b0, int nb, cudaStream_t st) {
         CoopArgs a;
         std::memset(&a, 0, sizeof(a));
@@ -289,120 +312,140 @@ struct MG {
     }
 
     // Result of one cycle with zero initial guess on level l for blocks
-    // [b0, b0+nb): right-hand side in vB[l][b], result written to out[z].
-    static void cycle(Ctx& c, int l, int b0, int nb, V* const* out, cudaStream_t st) {
+    // [b0, b0+nb) and bt.nr right-hand sides: right-hand sides in vB[l][b]
+    // (stride npl), results written to out[z] with right-hand-side stride ostride.
+    static void cycle(Ctx& c, int l, int b0, int nb, V* const* out, size_t ostride, const Batch& bt,
+                      cudaStream_t st) {
         const size_t npl = (size_t)c.ln1[l] * c.ln2[l];
         const double vs = sizeof(V), ccs = sizeof(CC);
+        const double nr = bt.nr;
         if (l == c.L - 1) {
             const double2* inv[3];
             const V* bb[3];
             V* xx[3];
             for (int z = 0; z < nb; ++z) { inv[z] = c.inv[b0 + z]; bb[z] = (const V*)c.vB[l][b0 + z]; xx[z] = out[z]; }
-            Prof pr(c, BAH_K_COARSE, st, nb * ((double)npl * npl * 16.0 + 2.0 * npl * vs));
-            launch_coarse_apply<MODE>(nb, (int)npl, inv, bb, xx, st);
+            RhsStride rs;
+            rs.s0 = npl; rs.s1 = ostride; rs.active = bt.active;
+            Prof pr(c, BAH_K_COARSE, st, nr * nb * ((double)npl * npl * 16.0 + 2.0 * npl * vs));
+            launch_coarse_apply<MODE>(nb, (int)npl, inv, bb, xx, st, bt.nr, rs);
             return;
         }
         Fine5<C, CC> f5 = fine5(c);
         const Fine5<C, CC>* pf5 = l == 0 ? &f5 : nullptr;
         const double w = weight(c, l);
         const double cb_ = coef_bytes(c, l, b0, nb);
-        const double sweep = cb_ + 3.0 * vs * npl * nb;
+        const double sweep = cb_ + 3.0 * vs * npl * nb * nr;
+        const size_t nplc = npl / 4;
         V* cur[3];
         V* oth[3];
+        size_t cur_s = ostride, oth_s = npl;
         for (int z = 0; z < nb; ++z) { cur[z] = out[z]; oth[z] = (V*)c.vT[l][b0 + z]; }
-        auto swap_cur = [&]() { for (int z = 0; z < nb; ++z) std::swap(cur[z], oth[z]); };
+        auto swap_cur = [&]() {
+            for (int z = 0; z < nb; ++z) std::swap(cur[z], oth[z]);
+            std::swap(cur_s, oth_s);
+        };
         V* cb[3];
         V* cx[3];
         for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
-        if (c.fused && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
+        if (bt.nr == 1 && c.fused && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
             // pre-smoothing + residual + restriction in one launch
             {
                 Prof pr(c, BAH_K_RESTRICT, st, cb_ + nb * npl * vs * 2.25);
-                launch_smooth_restrict<MODE>(set(c, l, b0, nb, nullptr, cur), pf5, w, cb, c.o.intergrid, st);
+                launch_smooth_restrict<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), pf5, w, cb,
+                                             c.o.intergrid, st);
             }
-            cycle(c, l + 1, b0, nb, cx, st);
+            cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
             // prolongation + correction + first post-smoothing sweep
             {
                 Prof pr(c, BAH_K_PROLONG, st, sweep + nb * npl * vs * 0.25);
-                launch_prolong_smooth<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, cx, st);
+                launch_prolong_smooth<MODE>(set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt), pf5, w, cx, st);
                 swap_cur();
             }
             for (int s = 1; s < c.o.nu_post; ++s) {
                 Prof pr(c, BAH_K_JACOBI, st, sweep);
-                launch_jacobi<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, 0, st);
+                launch_jacobi<MODE>(set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt), pf5, w, 0, st);
                 swap_cur();
             }
         } else {
-        // pre-relaxation
-        if (c.o.nu_pre >= 1) {
+            // pre-relaxation
+            if (c.o.nu_pre >= 1) {
+                {
+                    Prof pr(c, BAH_K_JACOBI, st, nr * nb * npl * (2.0 * vs + ccs));
+                    launch_jacobi<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), pf5, w, 1, st);
+                }
+                for (int s = 1; s < c.o.nu_pre; ++s) {
+                    Prof pr(c, BAH_K_JACOBI, st, sweep);
+                    launch_jacobi<MODE>(set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt), pf5, w, 0, st);
+                    swap_cur();
+                }
+            } else {
+                Prof pr(c, BAH_K_SMALL, st, nr * nb * npl * vs, 0);
+                for (int z = 0; z < nb; ++z)
+                    cudaMemset2DAsync(cur[z], cur_s * sizeof(V), 0, npl * sizeof(V), bt.nr, st);
+            }
+            // residual and restriction
+            auto rs = set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt);
             {
-                Prof pr(c, BAH_K_JACOBI, st, nb * npl * (2.0 * vs + ccs));
-                launch_jacobi<MODE>(set(c, l, b0, nb, nullptr, cur), pf5, w, 1, st);
+                Prof pr(c, BAH_K_RESIDUAL, st, sweep);
+                launch_residual<MODE>(rs, pf5, st);
             }
-            for (int s = 1; s < c.o.nu_pre; ++s) {
+            {
+                Prof pr(c, BAH_K_RESTRICT, st, nr * nb * npl * vs * 1.25);
+                launch_restrict<MODE>(rs, cb, c.o.intergrid, st, nplc);
+            }
+            // coarse-grid correction
+            if (l == 0 && c.coop && bt.nr == 1) coop_levels(c, b0, nb, st);
+            else cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
+            {
+                Prof pr(c, BAH_K_PROLONG, st, nr * nb * npl * vs * 2.25);
+                launch_prolong_add<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), cx, st, nplc);
+            }
+            // post-relaxation
+            for (int s = 0; s < c.o.nu_post; ++s) {
                 Prof pr(c, BAH_K_JACOBI, st, sweep);
-                launch_jacobi<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, 0, st);
+                launch_jacobi<MODE>(set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt), pf5, w, 0, st);
                 swap_cur();
             }
-        } else {
-            Prof pr(c, BAH_K_SMALL, st, nb * npl * vs, 0);
-            for (int z = 0; z < nb; ++z) cudaMemsetAsync(cur[z], 0, npl * sizeof(V), st);
-        }
-        // residual and restriction
-        auto rs = set(c, l, b0, nb, cur, oth);
-        {
-            Prof pr(c, BAH_K_RESIDUAL, st, sweep);
-            launch_residual<MODE>(rs, pf5, st);
-        }
-        {
-            Prof pr(c, BAH_K_RESTRICT, st, nb * npl * vs * 1.25);
-            launch_restrict<MODE>(rs, cb, c.o.intergrid, st);
-        }
-        // coarse-grid correction
-        if (l == 0 && c.coop) coop_levels(c, b0, nb, st);
-        else cycle(c, l + 1, b0, nb, cx, st);
-        {
-            Prof pr(c, BAH_K_PROLONG, st, nb * npl * vs * 2.25);
-            launch_prolong_add<MODE>(set(c, l, b0, nb, nullptr, cur), cx, st);
-        }
-        // post-relaxation
-        for (int s = 0; s < c.o.nu_post; ++s) {
-            Prof pr(c, BAH_K_JACOBI, st, sweep);
-            launch_jacobi<MODE>(set(c, l, b0, nb, cur, oth), pf5, w, 0, st);
-            swap_cur();
-        }
         }
         for (int z = 0; z < nb; ++z)
             if (cur[z] != out[z]) {
-                Prof pr(c, BAH_K_SMALL, st, 2.0 * npl * vs, 0);
-                cudaMemcpyAsync(out[z], cur[z], npl * sizeof(V), cudaMemcpyDeviceToDevice, st);
+                Prof pr(c, BAH_K_SMALL, st, 2.0 * nr * npl * vs, 0);
+                cudaMemcpy2DAsync(out[z], ostride * sizeof(V), cur[z], cur_s * sizeof(V), npl * sizeof(V), bt.nr,
+                                  cudaMemcpyDeviceToDevice, st);
             }
     }
 
-    // z = P^{-1} D r  (r FP64 padded vector, z storage precision padded vector)
-    static void precond(Ctx& c, const double2* r, V* z, cudaStream_t st) {
+    // z = P^{-1} D r for bt.nr right-hand sides  (r FP64 padded vectors with
+    // stride rs, z storage-precision padded vectors with stride zs)
+    static void precond(Ctx& c, const double2* r, size_t rstride, V* z, size_t zstride, const Batch& bt,
+                        cudaStream_t st) {
         const int np = c.np;
         const double vs = sizeof(V);
         Fine5<C, CC> f5 = fine5(c);
         {
-            Prof pr(c, BAH_K_DISTRIB, st, (double)np * (48.0 + sizeof(C) + sizeof(CC) + vs));
-            launch_distributor<MODE>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, f5, r, (V*)c.vB[0][2], st);
+            RhsStride rs;
+            rs.s0 = rstride; rs.s1 = np; rs.active = bt.active;
+            Prof pr(c, BAH_K_DISTRIB, st, (double)bt.nr * np * (48.0 + sizeof(C) + sizeof(CC) + vs));
+            launch_distributor<MODE>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, f5, r, (V*)c.vB[0][2], st, bt.nr, rs);
         }
         V* outp[1] = {z + 2 * (size_t)np};
-        cycle(c, 0, 2, 1, outp, st);
+        cycle(c, 0, 2, 1, outp, zstride, bt, st);
         {
-            Prof pr(c, BAH_K_URHS, st, (double)np * (32.0 + 3.0 * vs));
+            RhsStride rs;
+            rs.s0 = rstride; rs.s1 = zstride; rs.s2 = np; rs.active = bt.active;
+            Prof pr(c, BAH_K_URHS, st, (double)bt.nr * np * (32.0 + 3.0 * vs));
             launch_u_rhs<MODE>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, r, z + 2 * (size_t)np, (V*)c.vB[0][0],
-                               (V*)c.vB[0][1], st);
+                               (V*)c.vB[0][1], st, bt.nr, rs);
         }
         V* outu[2] = {z, z + (size_t)np};
-        cycle(c, 0, 0, 2, outu, st);
+        cycle(c, 0, 0, 2, outu, zstride, bt, st);
     }
 };
 
-static void precond_any(Ctx& c, const double2* r, void* z, cudaStream_t st) {
-    if (c.mode == BAH_MIXED) MG<BAH_MIXED>::precond(c, r, (float2*)z, st);
-    else MG<BAH_FP64>::precond(c, r, (double2*)z, st);
+static void precond_any(Ctx& c, const double2* r, size_t rstride, void* z, size_t zstride, const Batch& bt,
+                        cudaStream_t st) {
+    if (c.mode == BAH_MIXED) MG<BAH_MIXED>::precond(c, r, rstride, (float2*)z, zstride, bt, st);
+    else MG<BAH_FP64>::precond(c, r, rstride, (double2*)z, zstride, bt, st);
 }
 // algorithmic bytes of one operator apply: input (3 components), FP64
 // output, coefficients cx, nx (z-aliases when h1 == h2), d1, d2, 1/(lambda+mu)
@@ -410,10 +453,13 @@ static double op_bytes(const Ctx& c, double in_bytes, bool residual) {
     const double coef = (c.h1 == c.h2 ? 16.0 : 32.0) + 32.0 + 8.0;
     return (double)c.np * (3.0 * in_bytes + 48.0 + coef + (residual ? 48.0 : 0.0));
 }
-static void op_apply_z(Ctx& c, const void* z, double2* y, cudaStream_t st) {
-    Prof pr(c, BAH_K_OPERATOR, st, op_bytes(c, (double)c.vsz, false));
-    if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, y, nullptr, 0, st);
-    else launch_elastic_apply<double2>(c.op, (const double2*)z, y, nullptr, 0, st);
+static void op_apply_z(Ctx& c, const void* z, size_t zstride, double2* y, size_t ystride, const Batch& bt,
+                       cudaStream_t st) {
+    Prof pr(c, BAH_K_OPERATOR, st, bt.nr * op_bytes(c, (double)c.vsz, false));
+    RhsStride rs;
+    rs.s0 = zstride; rs.s1 = ystride; rs.active = bt.active;
+    if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, y, nullptr, 0, st, bt.nr, rs);
+    else launch_elastic_apply<double2>(c.op, (const double2*)z, y, nullptr, 0, st, bt.nr, rs);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,13 +547,13 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     c.vB = c.vX; c.vT = c.vX;
     for (int l = 0; l < c.L; ++l)
         for (int b = 0; b < 3; ++b) {
-            const size_t npl = (size_t)c.ln1[l] * c.ln2[l];
-            TRY(c.alloc(&c.vX[l][b], npl * c.vsz));
-            TRY(c.alloc(&c.vB[l][b], npl * c.vsz));
-            TRY(c.alloc(&c.vT[l][b], npl * c.vsz));
-            BAH_CUDA_TRY(cudaMemsetAsync(c.vX[l][b], 0, npl * c.vsz, st));
-            BAH_CUDA_TRY(cudaMemsetAsync(c.vB[l][b], 0, npl * c.vsz, st));
-            BAH_CUDA_TRY(cudaMemsetAsync(c.vT[l][b], 0, npl * c.vsz, st));
+            const size_t bytes = (size_t)c.ln1[l] * c.ln2[l] * c.vsz * c.nbatch;
+            TRY(c.alloc(&c.vX[l][b], bytes));
+            TRY(c.alloc(&c.vB[l][b], bytes));
+            TRY(c.alloc(&c.vT[l][b], bytes));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.vX[l][b], 0, bytes, st));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.vB[l][b], 0, bytes, st));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.vT[l][b], 0, bytes, st));
         }
     // cooperative cycle descriptors
     {
@@ -547,19 +593,29 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     // Krylov workspace
     const size_t n = c.vec_len();
     const int m = c.m;
-    TRY(c.alloc_t(&c.V, n * (m + 1)));
-    TRY(c.alloc(&c.Z, n * m * c.vsz));
-    TRY(c.alloc_t(&c.W, n)); TRY(c.alloc_t(&c.R, n)); TRY(c.alloc_t(&c.Bs, n)); TRY(c.alloc_t(&c.X, n));
+    const size_t nbt = c.nbatch;
+    const size_t so = m + 2;
+    TRY(c.alloc_t(&c.V, n * (m + 1) * nbt));
+    TRY(c.alloc(&c.Z, n * m * c.vsz * nbt));
+    TRY(c.alloc_t(&c.W, n * nbt)); TRY(c.alloc_t(&c.R, n * nbt)); TRY(c.alloc_t(&c.Bs, n * nbt));
+    TRY(c.alloc_t(&c.X, n * nbt));
     TRY(c.alloc(&c.ztmp, n * c.vsz));
-    TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m));
-    TRY(c.alloc_t(&c.h1v, m + 2)); TRY(c.alloc_t(&c.h2v, m + 2));
-    TRY(c.alloc_t(&c.gsflag, 1));
-    TRY(c.alloc_t(&c.cs, m + 1)); TRY(c.alloc_t(&c.sn, m + 1)); TRY(c.alloc_t(&c.g, m + 2)); TRY(c.alloc_t(&c.y, m + 1));
-    TRY(c.alloc_t(&c.partial, (size_t)(m + 1) * RED_CTAS));
-    TRY(c.alloc_t(&c.dpart, RED_CTAS));
-    TRY(c.alloc_t(&c.nrm, 4));
-    TRY(c.alloc_t(&c.status, 4));
-    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hstatus, 8 * (size_t)(m + 2) * sizeof(double)));
+    TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m * nbt));
+    TRY(c.alloc_t(&c.h1v, so * nbt)); TRY(c.alloc_t(&c.h2v, so * nbt));
+    TRY(c.alloc_t(&c.gsflag, nbt));
+    TRY(c.alloc_t(&c.cs, so * nbt)); TRY(c.alloc_t(&c.sn, so * nbt)); TRY(c.alloc_t(&c.g, so * nbt));
+    TRY(c.alloc_t(&c.y, so * nbt));
+    TRY(c.alloc_t(&c.partial, so * RED_CTAS * nbt));
+    TRY(c.alloc_t(&c.dpart, (size_t)RED_CTAS * nbt));
+    TRY(c.alloc_t(&c.nrm, 8 * nbt));
+    TRY(c.alloc_t(&c.status, 4 * nbt));
+    TRY(c.alloc_t(&c.active, nbt));
+    TRY(c.alloc_t(&c.jk, nbt));
+    BAH_CUDA_TRY(cudaMemsetAsync(c.nrm, 0, 8 * nbt * sizeof(double), st));
+    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hstatus, (4 * (size_t)(m + 1) * nbt + 8 * nbt) * sizeof(double)));
+    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hint, kIntSlots * nbt * sizeof(int)));
+    c.ks.sv = (size_t)(m + 1) * n; c.ks.sw = n; c.ks.sp = so * RED_CTAS; c.ks.so = so;
+    c.ks.sh = (size_t)(m + 1) * m; c.ks.sz = (size_t)m * n; c.ks.sx = n; c.ks.active = c.active;
     BAH_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
     c.ig.assign(m, Ctx::IterGraph());
     c.itev.assign(m, nullptr);
@@ -572,54 +628,76 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// FGMRES for one right-hand side (device vectors b, x; b is sanitised)
+// FGMRES, nbatch right-hand sides in lockstep (device vectors b, x with
+// stride n; b sanitised).  Every right-hand side has its own Krylov basis,
+// Hessenberg matrix and rotations; the kernels of one step serve all of them
+// and skip the inactive ones.
 // ---------------------------------------------------------------------------
-static int read_scalar(Ctx& c, const double* d, double* h, cudaStream_t st) {
-    double* slot = c.hstatus + 8 * (size_t)(c.m + 1);
-    BAH_CUDA_TRY(cudaMemcpyAsync(slot, d, sizeof(double), cudaMemcpyDeviceToHost, st));
+static double* status_slot(Ctx& c, int j) { return c.hstatus + 4 * (size_t)j * c.nbatch; }
+static double* scalar_slot(Ctx& c) { return c.hstatus + 4 * (size_t)(c.m + 1) * c.nbatch; }
+
+// copy sc[r*8 + slot] of every right-hand side to the host (synchronises)
+static int read_scalars(Ctx& c, int slot, double* out, cudaStream_t st) {
+    double* h = scalar_slot(c);
+    BAH_CUDA_TRY(cudaMemcpy2DAsync(h, sizeof(double), c.nrm + slot, 8 * sizeof(double), sizeof(double), c.nbatch,
+                                   cudaMemcpyDeviceToHost, st));
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
-    *h = *slot;
+    for (int r = 0; r < c.nbatch; ++r) out[r] = h[r];
+    return BAH_OK;
+}
+// Host-to-device copy of one int per right-hand side through a ring of
+// pinned staging slots: at most a few uploads happen between two waits on
+// the stream, so a slot's copy has completed before the slot comes round again.
+static int upload_ints(Ctx& c, const std::vector<int>& v, int* dev, int /*which*/, cudaStream_t st) {
+    int* h = c.hint + (size_t)(c.hint_slot++ % kIntSlots) * c.nbatch;
+    for (int r = 0; r < c.nbatch; ++r) h[r] = v[r];
+    BAH_CUDA_TRY(cudaMemcpyAsync(dev, h, c.nbatch * sizeof(int), cudaMemcpyHostToDevice, st));
     return BAH_OK;
 }
 
-// One FGMRES step j (everything between two status reads): z_j = P^{-1} D v_j,
-// w = H z_j, Gram-Schmidt with selective reorthogonalisation, Givens update,
-// v_{j+1} = w / ||w||, and the copy of the step's status to pinned slot j.
+// One FGMRES step j for all right-hand sides (everything between two status
+// reads): z_j = P^{-1} D v_j, w = H z_j, Gram-Schmidt with selective
+// reorthogonalisation, Givens update, v_{j+1} = w / ||w||, and the copy of
+// the step's status to pinned slot j.
 static void iter_body(Ctx& c, int j, cudaStream_t st) {
     const size_t n = c.vec_len();
-    const int m = c.m;
+    const int m = c.m, nb = c.nbatch;
+    const KS& ks = c.ks;
+    Batch bt;
+    bt.nr = nb;
+    bt.active = c.active;
     double2* vj = c.V + (size_t)j * n;
     void* zj = (char*)c.Z + (size_t)j * n * c.vsz;
-    precond_any(c, vj, zj, st);
-    op_apply_z(c, zj, c.W, st);
+    precond_any(c, vj, ks.sv, zj, ks.sz, bt, st);
+    op_apply_z(c, zj, ks.sz, c.W, n, bt, st);
     const double k1 = j + 1;
     {
-        Prof pr(c, BAH_K_DOT, st, (k1 + 1) * n * 16.0, 2);
-        launch_dot_norm(c.V, n, j + 1, c.W, n, c.partial, c.h1v, nullptr, st);
+        Prof pr(c, BAH_K_DOT, st, nb * (k1 + 1) * n * 16.0, 2);
+        launch_dot_norm(c.V, j + 1, c.W, n, c.partial, c.h1v, nullptr, nb, ks, st);
     }
     {
-        Prof pr(c, BAH_K_AXPY, st, (k1 + 2) * n * 16.0);
-        launch_axpy_norm(c.V, n, j + 1, c.h1v, c.W, n, c.dpart, nullptr, st);
+        Prof pr(c, BAH_K_AXPY, st, nb * (k1 + 2) * n * 16.0);
+        launch_axpy_norm(c.V, j + 1, c.h1v, c.W, n, c.dpart, nullptr, nb, ks, st);
     }
     {
         Prof pr(c, BAH_K_NORM, st, 0.0);
-        launch_dgks_decide(c.dpart, c.h1v, j + 1, c.gsflag, c.nrm + 2, st);
+        launch_dgks_decide(c.dpart, c.h1v, j + 1, c.gsflag, c.nrm, nb, ks, st);
     }
     {
-        Prof pr(c, BAH_K_DOT, st, 0.0, 2);      // runs only when the flag is set (bytes counted as zero)
-        launch_dot_norm(c.V, n, j + 1, c.W, n, c.partial, c.h2v, c.gsflag, st);
+        Prof pr(c, BAH_K_DOT, st, 0.0, 2);      // runs only where the flag is set (bytes counted as zero)
+        launch_dot_norm(c.V, j + 1, c.W, n, c.partial, c.h2v, c.gsflag, nb, ks, st);
     }
     {
         Prof pr(c, BAH_K_AXPY, st, 0.0);
-        launch_axpy_norm(c.V, n, j + 1, c.h2v, c.W, n, c.dpart, c.gsflag, st);
+        launch_axpy_norm(c.V, j + 1, c.h2v, c.W, n, c.dpart, c.gsflag, nb, ks, st);
     }
     {
-        Prof pr(c, BAH_K_SMALL, st, n * 32.0, 3);
-        launch_pass2_norm(c.dpart, c.gsflag, c.nrm + 2, st);
-        launch_arnoldi_givens(c.Hm + (size_t)j * (m + 1), c.h1v, c.h2v, c.nrm + 2, j, c.cs, c.sn, c.g, c.status, st);
-        launch_scale_copy(c.W, c.nrm + 2, c.V + (size_t)(j + 1) * n, n, 1, st);
+        Prof pr(c, BAH_K_SMALL, st, nb * n * 32.0, 3);
+        launch_pass2_norm(c.dpart, c.gsflag, c.nrm, nb, ks, st);
+        launch_arnoldi_givens(c.Hm, m + 1, c.h1v, c.h2v, c.nrm, j, c.cs, c.sn, c.g, c.status, nb, ks, st);
+        launch_scale_copy(c.W, c.nrm, 2, c.V + (size_t)(j + 1) * n, n, n, ks.sv, nb, ks, st);
     }
-    cudaMemcpyAsync(c.hstatus + 8 * (size_t)j, c.status, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(status_slot(c, j), c.status, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 
 static int ensure_graph(Ctx& c, int j) {
@@ -683,82 +761,113 @@ static int finish_iter(Ctx& c, int j) {
     return BAH_OK;
 }
 
-static int fgmres_one(Ctx& c, const double2* b, double2* x, double rtol, bah_stats* out, cudaStream_t st) {
+static int fgmres_batch(Ctx& c, const double2* b, double2* x, int nr, double rtol, bah_stats* out, cudaStream_t st) {
     const size_t n = c.vec_len();
-    const int m = c.m;
-    bah_stats s{};
-    s.status = BAH_OK;
+    const int m = c.m, nb = c.nbatch;
+    const KS& ks = c.ks;
+    std::vector<bah_stats> S(nb);
+    std::vector<double> bn(nb, 0.0), beta(nb, 0.0), est(nb, 1.0), tmp(nb);
+    std::vector<int> act(nb, 0), cyc(nb, 0), jd(nb, 0);
+    for (int r = 0; r < nb; ++r) { S[r] = bah_stats{}; S[r].status = BAH_OK; act[r] = r < nr ? 1 : 0; }
+    TRY(upload_ints(c, act, c.active, 0, st));
     {
-        Prof pr(c, BAH_K_NORM, st, n * 16.0, 2);
-        launch_norm2(b, n, c.dpart, c.nrm + 1, st);
+        Prof pr(c, BAH_K_NORM, st, (double)nr * n * 16.0, 2);
+        launch_norm2(b, n, c.dpart, c.nrm, 1, nb, ks, st);
     }
-    double nb;
-    TRY(read_scalar(c, c.nrm + 1, &nb, st));
-    BAH_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
-    if (!(nb > 0.0)) {
-        s.relres_true = 0.0;
-        if (out) *out = s;
-        return std::isfinite(nb) ? BAH_OK : BAH_ERR_NONFINITE;
+    TRY(read_scalars(c, 1, bn.data(), st));
+    BAH_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nr * n * sizeof(double2), st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.R, b, (size_t)nr * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    // beta = ||b|| (x_0 = 0)
+    BAH_CUDA_TRY(cudaMemcpy2DAsync(c.nrm, 8 * sizeof(double), c.nrm + 1, 8 * sizeof(double), sizeof(double), nb,
+                                   cudaMemcpyDeviceToDevice, st));
+    BAH_CUDA_TRY(cudaMemset2DAsync(c.nrm + 3, 8 * sizeof(double), 0, sizeof(double), nb, st));
+    for (int r = 0; r < nr; ++r) {
+        beta[r] = bn[r];
+        if (!std::isfinite(bn[r])) { S[r].status = BAH_ERR_NONFINITE; act[r] = 0; }
+        else if (!(bn[r] > 0.0)) { act[r] = 0; }                  // b = 0: x = 0
+        else if (beta[r] <= rtol * bn[r]) act[r] = 0;
     }
-    BAH_CUDA_TRY(cudaMemcpyAsync(c.R, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    BAH_CUDA_TRY(cudaMemcpyAsync(c.nrm, c.nrm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    BAH_CUDA_TRY(cudaMemsetAsync(c.nrm + 3, 0, sizeof(double), st));
-    double beta = nb;
     int total = 0;
-    double est = 1.0;
-    while (beta > rtol * nb && total < c.o.maxit) {
+    auto any = [&](const std::vector<int>& v) { for (int q : v) if (q) return true; return false; };
+    while (any(act) && total < c.o.maxit) {
+        TRY(upload_ints(c, act, c.active, 0, st));
         // v_0 = r / beta, g = beta e_1
         {
-            Prof pr(c, BAH_K_SMALL, st, n * 32.0, 2);
-            launch_scale_copy(c.R, c.nrm, c.V, n, 1, st);
-            launch_init_arnoldi(c.nrm, c.g, m, c.status, st);
+            Prof pr(c, BAH_K_SMALL, st, (double)nr * n * 32.0, 2);
+            launch_scale_copy(c.R, c.nrm, 0, c.V, n, n, ks.sv, nb, ks, st);
+            launch_init_arnoldi(c.nrm, c.g, m, c.status, nb, ks, st);
         }
         const int mm = std::min(m, c.o.maxit - total);
-        int jdone = 0;
-        bool stop = false;
+        cyc = act;
+        std::fill(jd.begin(), jd.end(), 0);
         TRY(launch_iter(c, 0, st));
         for (int j = 0; j < mm; ++j) {
             if (j + 1 < mm) TRY(launch_iter(c, j + 1, st));    // queued behind step j
             TRY(finish_iter(c, j));
-            const double* hs = c.hstatus + 8 * (size_t)j;
+            const double* hs = status_slot(c, j);
             ++total;
-            jdone = j + 1;
-            est = hs[0] / nb;
-            if (hs[2] != 0.0 || !std::isfinite(est)) { s.status = BAH_ERR_NONFINITE; stop = true; break; }
-            if (est <= rtol) break;
-            if (hs[1] <= 1e-14 * nb) break;     // (lucky) breakdown: the Krylov space is invariant
+            bool changed = false;
+            for (int r = 0; r < nb; ++r) {
+                if (!cyc[r]) continue;
+                S[r].iters++;
+                jd[r] = j + 1;
+                est[r] = hs[4 * r] / bn[r];
+                bool stop = false;
+                if (hs[4 * r + 2] != 0.0 || !std::isfinite(est[r])) { S[r].status = BAH_ERR_NONFINITE; stop = true; }
+                else if (est[r] <= rtol) stop = true;
+                else if (hs[4 * r + 1] <= 1e-14 * bn[r]) stop = true;    // (lucky) breakdown
+                if (stop) { cyc[r] = 0; changed = true; }
+            }
+            if (!any(cyc)) break;
+            if (changed && j + 2 < mm) TRY(upload_ints(c, cyc, c.active, 0, st));   // takes effect from step j+2
         }
-        if (s.status == BAH_ERR_NONFINITE) break;   // x keeps the last finite iterate
+        // solution update and true residual for the right-hand sides of this cycle
+        for (int r = 0; r < nb; ++r) if (S[r].status == BAH_ERR_NONFINITE) jd[r] = 0;
+        TRY(upload_ints(c, jd, c.jk, 1, st));
+        std::vector<int> upd(nb);
+        for (int r = 0; r < nb; ++r) upd[r] = (act[r] && S[r].status != BAH_ERR_NONFINITE) ? 1 : 0;
+        TRY(upload_ints(c, upd, c.active, 0, st));
         {
             Prof pr(c, BAH_K_SMALL, st, 0.0);
-            launch_triangular_solve(c.Hm, m + 1, c.g, jdone, c.y, st);
+            launch_triangular_solve(c.Hm, m + 1, c.g, c.jk, c.y, nb, ks, st);
         }
         {
-            Prof pr(c, BAH_K_UPDATE, st, (double)jdone * n * c.vsz + 32.0 * n);
-            if (c.mode == BAH_MIXED) launch_update_x<float2>((const float2*)c.Z, n, jdone, c.y, x, n, st);
-            else launch_update_x<double2>((const double2*)c.Z, n, jdone, c.y, x, n, st);
-        }
-        // true residual in FP64
-        {
-            Prof pr(c, BAH_K_OPERATOR, st, op_bytes(c, 16.0, true));
-            launch_elastic_apply<double2>(c.op, x, c.R, b, 0, st);
+            double kk = 0;
+            for (int r = 0; r < nb; ++r) kk += jd[r];
+            Prof pr(c, BAH_K_UPDATE, st, kk * n * c.vsz + 32.0 * n * nr);
+            if (c.mode == BAH_MIXED) launch_update_x<float2>((const float2*)c.Z, c.jk, c.y, x, n, nb, ks, st);
+            else launch_update_x<double2>((const double2*)c.Z, c.jk, c.y, x, n, nb, ks, st);
         }
         {
-            Prof pr(c, BAH_K_NORM, st, n * 16.0, 2);
-            launch_norm2(c.R, n, c.dpart, c.nrm, st);
+            RhsStride rs;
+            rs.s0 = n; rs.s1 = n; rs.s2 = n; rs.active = c.active;
+            Prof pr(c, BAH_K_OPERATOR, st, nr * op_bytes(c, 16.0, true));
+            launch_elastic_apply<double2>(c.op, x, c.R, b, 0, st, nb, rs);
+        }
+        {
+            Prof pr(c, BAH_K_NORM, st, (double)nr * n * 16.0, 2);
+            launch_norm2(c.R, n, c.dpart, c.nrm, 0, nb, ks, st);
         }
         BAH_CUDA_TRY(cudaGetLastError());
-        TRY(read_scalar(c, c.nrm, &beta, st));
-        s.restarts++;
-        if (!std::isfinite(beta)) { s.status = BAH_ERR_NONFINITE; break; }
-        if (stop) break;
+        TRY(read_scalars(c, 0, tmp.data(), st));
+        for (int r = 0; r < nb; ++r) {
+            if (!upd[r]) { act[r] = 0; continue; }
+            beta[r] = tmp[r];
+            S[r].restarts++;
+            if (!std::isfinite(beta[r])) { S[r].status = BAH_ERR_NONFINITE; act[r] = 0; }
+            else if (beta[r] <= rtol * bn[r]) act[r] = 0;
+        }
+        for (int r = 0; r < nb; ++r) if (S[r].status == BAH_ERR_NONFINITE) act[r] = 0;
     }
-    s.iters = total;
-    s.relres_true = beta / nb;
-    s.relres_est = est;
-    if (s.status == BAH_OK && !(s.relres_true <= rtol)) s.status = BAH_ERR_NOT_CONVERGED;
-    if (out) *out = s;
-    return s.status;
+    int first = BAH_OK;
+    for (int r = 0; r < nr; ++r) {
+        S[r].relres_true = bn[r] > 0.0 ? beta[r] / bn[r] : 0.0;
+        S[r].relres_est = bn[r] > 0.0 ? est[r] : 0.0;
+        if (S[r].status == BAH_OK && !(S[r].relres_true <= rtol)) S[r].status = BAH_ERR_NOT_CONVERGED;
+        if (out) out[r] = S[r];
+        if (S[r].status != BAH_OK && first == BAH_OK) first = S[r].status;
+    }
+    return first;
 }
 
 static bool is_device_ptr(const void* p) {
@@ -803,6 +912,7 @@ void bah_default_opts(bah_opts* o) {
     o->intergrid = BAH_INTERGRID_BILINEAR;
     o->restart = 20;
     o->maxit = 5000;
+    o->rhs_block = 1;
 }
 
 const char* bah_status_string(int s) {
@@ -838,6 +948,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     if (o.precision != BAH_FP64 && o.precision != BAH_MIXED) { set_error("bad precision"); return BAH_ERR_ARG; }
     if (o.restart < 1 || o.restart > 64) { set_error("restart must be in 1..64"); return BAH_ERR_ARG; }
     if (o.maxit < 1) { set_error("maxit must be >= 1"); return BAH_ERR_ARG; }
+    if (o.rhs_block < 1 || o.rhs_block > 256) { set_error("rhs_block must be in 1..256"); return BAH_ERR_ARG; }
     if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre > 8 || o.nu_post > 8) { set_error("bad nu"); return BAH_ERR_ARG; }
     if (o.n_jacobi_w < 1 || o.n_jacobi_w > 8) { set_error("n_jacobi_w must be in 1..8"); return BAH_ERR_ARG; }
     if (o.intergrid != BAH_INTERGRID_BILINEAR && o.intergrid != BAH_INTERGRID_MIXED) {
@@ -856,6 +967,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     c.mode = o.precision;
     c.vsz = c.mode == BAH_MIXED ? sizeof(float2) : sizeof(double2);
     c.m = o.restart;
+    c.nbatch = o.rhs_block;
     // levels
     int L = 1;
     {
@@ -925,14 +1037,15 @@ int bah_apply_preconditioner(bah_ctx* h, const void* r, void* z, int nrhs, void*
     Ctx& c = h->c;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = c.vec_len();
+    Batch one;
     for (int k = 0; k < nrhs; ++k) {
         const double2* rk = (const double2*)r + k * n;
         double2* zk = (double2*)z + k * n;
         if (c.mode == BAH_MIXED) {
-            precond_any(c, rk, c.ztmp, st);
+            precond_any(c, rk, n, c.ztmp, n, one, st);
             launch_convert<float2, double2>((const float2*)c.ztmp, zk, n, st);
         } else {
-            precond_any(c, rk, zk, st);
+            precond_any(c, rk, n, zk, n, one, st);
         }
     }
     BAH_CUDA_TRY(cudaGetLastError());
@@ -944,15 +1057,16 @@ int bah_block_cycle(bah_ctx* h, int block, const void* b, void* x, void* stream)
     Ctx& c = h->c;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t np = c.np;
+    Batch one;
     if (c.mode == BAH_MIXED) {
         launch_convert<double2, float2>((const double2*)b, (float2*)c.vB[0][block], np, st);
         float2* o[1] = {(float2*)c.ztmp};
-        MG<BAH_MIXED>::cycle(c, 0, block, 1, o, st);
+        MG<BAH_MIXED>::cycle(c, 0, block, 1, o, np, one, st);
         launch_convert<float2, double2>((const float2*)c.ztmp, (double2*)x, np, st);
     } else {
         BAH_CUDA_TRY(cudaMemcpyAsync(c.vB[0][block], b, np * sizeof(double2), cudaMemcpyDeviceToDevice, st));
         double2* o[1] = {(double2*)x};
-        MG<BAH_FP64>::cycle(c, 0, block, 1, o, st);
+        MG<BAH_FP64>::cycle(c, 0, block, 1, o, np, one, st);
     }
     BAH_CUDA_TRY(cudaGetLastError());
     return BAH_OK;
@@ -1006,19 +1120,21 @@ int bah_solve(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_sta
     const bool dev_b = is_device_ptr(b), dev_x = is_device_ptr(x);
     if (dev_b != dev_x) { set_error("b and x must both be device or both be host pointers"); return BAH_ERR_ARG; }
     int first_fail = BAH_OK;
-    for (int k = 0; k < nrhs; ++k) {
-        const double2* bk = (const double2*)b + k * n;
-        double2* xk = (double2*)x + k * n;
-        BAH_CUDA_TRY(cudaMemcpyAsync(c.Bs, bk, n * sizeof(double2),
+    for (int k0 = 0; k0 < nrhs; k0 += c.nbatch) {
+        const int nr = std::min(c.nbatch, nrhs - k0);
+        const double2* bk = (const double2*)b + (size_t)k0 * n;
+        double2* xk = (double2*)x + (size_t)k0 * n;
+        BAH_CUDA_TRY(cudaMemcpyAsync(c.Bs, bk, (size_t)nr * n * sizeof(double2),
                                      dev_b ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         {
-            Prof pr(c, BAH_K_SMALL, st, (double)c.np * 32.0);
-            launch_sanitize(c.Bs, c.n1, c.n2, 1, st);
+            Prof pr(c, BAH_K_SMALL, st, (double)nr * c.np * 32.0);
+            launch_sanitize(c.Bs, c.n1, c.n2, nr, st);
         }
         double2* xd = dev_x ? xk : c.X;
-        int s = fgmres_one(c, c.Bs, xd, rtol, stats ? stats + k : nullptr, st);
+        int s = fgmres_batch(c, c.Bs, xd, nr, rtol, stats ? stats + k0 : nullptr, st);
         if (s == BAH_ERR_CUDA || s == BAH_ERR_OOM || s == BAH_ERR_ARG) return s;
-        if (!dev_x) BAH_CUDA_TRY(cudaMemcpyAsync(xk, c.X, n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        if (!dev_x)
+            BAH_CUDA_TRY(cudaMemcpyAsync(xk, c.X, (size_t)nr * n * sizeof(double2), cudaMemcpyDeviceToHost, st));
         if (s != BAH_OK && first_fail == BAH_OK) first_fail = s;
     }
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
