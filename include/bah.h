@@ -156,6 +156,34 @@ int bah_apply_preconditioner(bah_ctx* ctx, const void* r, void* z, int nrhs, voi
  * (BAH_ERR_NOT_CONVERGED / BAH_ERR_NONFINITE) after solving all of them. */
 int bah_solve(bah_ctx* ctx, const void* b, void* x, int nrhs, double rtol, bah_stats* stats, void* stream);
 
+/* Solve the adjoint system H^H y = b (same options and stopping rule as
+ * bah_solve).  H is complex symmetric (Eq. 2.6), so H^H = conj(H) and the
+ * call solves H conj(y) = conj(b) with the same preconditioner. */
+int bah_solve_adjoint(bah_ctx* ctx, const void* b, void* y, int nrhs, double rtol, bah_stats* stats, void* stream);
+
+/* Receiver misfit of a least-squares data fit.  Q samples the entries
+ * rec[0..nrec-1] (device int array of indices into one padded vector, e.g.
+ * the u_d faces of a receiver line) of each solution x_s; d holds the
+ * observed data, nrec complex values per source (device).  Writes
+ * adj_s = Q^H (Q x_s - d_s) (nrhs full padded vectors, zero off the
+ * receivers) and misfit[s] = 1/2 ||Q x_s - d_s||^2 (device, nrhs doubles).
+ * Indices must lie in [0, vector_len); they are not checked on the device. */
+int bah_misfit(bah_ctx* ctx, const void* x, const void* d, const int* rec, int nrec, int nrhs, void* adj_src,
+               double* misfit, void* stream);
+
+/* Gradient of J = sum_s 1/2 ||Q x_s - d_s||^2 with respect to the cell values
+ * of lambda, mu and rho, given the forward solutions x_s (H x_s = b_s) and
+ * the adjoint solutions y_s (H^H y_s = Q^H (Q x_s - d_s)):
+ *     dJ/dm_k = -Re sum_s y_s^H (dH/dm_k) x_s .
+ * dH/dm_k follows Eq. 2.6: lambda enters -C = -diag(1/(lambda+mu)), mu enters
+ * the edge-averaged A_e(mu) and C, rho the face mass A_f(rho(1 - i gamma/omega)).
+ * The paper does not write this gradient (it uses the solver inside
+ * full-waveform inversion); this is the adjoint-state derivative of the
+ * discrete system.  g_lambda, g_mu, g_rho: device arrays of cells doubles,
+ * ACCUMULATED into (zero them first).  FP64, one kernel. */
+int bah_gradient(bah_ctx* ctx, const void* x_fwd, const void* y_adj, int nrhs, double* g_lambda, double* g_mu,
+                 double* g_rho, void* stream);
+
 /* Test hook: one multigrid cycle (the context's cycle type) on acoustic block
  * `block` (0..dim-1 = A_{block+1},s; dim = H_p,s) with zero initial guess.
  * b and x are device arrays of cells complex FP64 values in the padded

@@ -37,7 +37,7 @@ BAH_INTERGRID_MIXED = 1
 EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_apply_operator",
            "bah_apply_preconditioner", "bah_solve", "bah_block_cycle", "bah_level_stencil",
            "bah_status_string", "bah_last_error", "bah_profile_control", "bah_profile_read",
-           "bah_residual_norm_static")
+           "bah_residual_norm_static", "bah_solve_adjoint", "bah_misfit", "bah_gradient")
 BAH_STATIC_MAX_RHS = 64
 
 
@@ -106,6 +106,12 @@ def lib():
         L.bah_profile_control.restype = C.c_int
         L.bah_profile_read.argtypes = [vp, vp]
         L.bah_profile_read.restype = C.c_int
+        L.bah_solve_adjoint.argtypes = [vp, vp, vp, C.c_int, C.c_double, C.POINTER(bah_stats), vp]
+        L.bah_solve_adjoint.restype = C.c_int
+        L.bah_misfit.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp]
+        L.bah_misfit.restype = C.c_int
+        L.bah_gradient.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp]
+        L.bah_gradient.restype = C.c_int
         L.bah_residual_norm_static.argtypes = [vp, vp, vp, C.c_int, vp, vp]
         L.bah_residual_norm_static.restype = C.c_int
         L.bah_status_string.argtypes = [C.c_int]
@@ -243,6 +249,25 @@ def bah_profile_read(ctx):
     p = bah_profile()
     _check(lib().bah_profile_read(ctx, C.byref(p)), "bah_profile_read")
     return p.as_dict()
+
+
+def bah_solve_adjoint(ctx, b, y, nrhs=1, rtol=1e-6, stream=None):
+    """Solve H^H y = b; returns (status, [stats dict per rhs])."""
+    st = (bah_stats * max(1, nrhs))()
+    s = lib().bah_solve_adjoint(ctx, _ptr(b), _ptr(y), int(nrhs), float(rtol), st, _stream(stream))
+    if s not in (BAH_OK, BAH_ERR_NOT_CONVERGED, BAH_ERR_NONFINITE):
+        raise BahError(s, "bah_solve_adjoint")
+    return s, [st[k].as_dict() for k in range(nrhs)]
+
+
+def bah_misfit(ctx, x, d, rec, nrec, nrhs, adj, misfit, stream=None):
+    return _check(lib().bah_misfit(ctx, _ptr(x), _ptr(d), _ptr(rec), int(nrec), int(nrhs), _ptr(adj), _ptr(misfit),
+                                   _stream(stream)), "bah_misfit")
+
+
+def bah_gradient(ctx, x, y, nrhs, g_lambda, g_mu, g_rho, stream=None):
+    return _check(lib().bah_gradient(ctx, _ptr(x), _ptr(y), int(nrhs), _ptr(g_lambda), _ptr(g_mu), _ptr(g_rho),
+                                     _stream(stream)), "bah_gradient")
 
 
 def bah_residual_norm_static(ctx, b, x, nrhs, relres, stream=None):

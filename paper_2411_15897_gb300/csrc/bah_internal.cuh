@@ -236,6 +236,14 @@ void launch_triangular_solve(const double2* Hm, int ldh, const double2* g, const
                              const KS& ks, cudaStream_t st);
 void launch_init_arnoldi(const double* sc, double2* g, int m, double* status, int nrhs, const KS& ks, cudaStream_t st);
 
+// adjoint gradient (k_grad.cu)
+void launch_conj(double2* v, size_t n, cudaStream_t st);
+void launch_misfit(const double2* x, const double2* d, const int* rec, int nrec, int nrhs, size_t vlen, double2* adj,
+                   double* misfit, cudaStream_t st);
+void launch_gradient(int n1, int n2, double h1, double h2, double omega, const double* cinv, const double* gamma,
+                     size_t vlen, int nrhs, const double2* X, const double2* Y, double* gl, double* gm, double* gr,
+                     cudaStream_t st);
+
 // error handling
 void set_error(const std::string& msg);
 }  // namespace bah

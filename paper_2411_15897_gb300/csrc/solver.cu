@@ -43,6 +43,7 @@ struct Ctx {
     // FP64 coefficient arrays (cells)
     double *cx = nullptr, *cz = nullptr, *nx = nullptr, *nz = nullptr, *wx = nullptr, *wz = nullptr, *cinv = nullptr;
     double2 *d1 = nullptr, *d2 = nullptr, *dg[3] = {nullptr, nullptr, nullptr}, *dAp = nullptr;
+    double* gam = nullptr;               // attenuation at cells (device), for the gradient
     OpCoef op{};
     // level-0 arrays in storage precision
     void *s_cx = nullptr, *s_cz = nullptr, *s_nx = nullptr, *s_nz = nullptr, *s_wx = nullptr, *s_wz = nullptr;
@@ -479,6 +480,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     TRY(c.alloc_t(&c.wx, np)); TRY(c.alloc_t(&c.wz, np)); TRY(c.alloc_t(&c.cinv, np));
     TRY(c.alloc_t(&c.d1, np)); TRY(c.alloc_t(&c.d2, np)); TRY(c.alloc_t(&c.dAp, np));
     for (int b = 0; b < 3; ++b) TRY(c.alloc_t(&c.dg[b], np));
+    c.gam = gam;
     launch_medium_prep(c.n1, c.n2, c.h1, c.h2, c.omega, c.alpha, lam, mu, rho, gam, c.cx, c.cz, c.nx, c.nz, c.wx,
                        c.wz, c.d1, c.d2, c.cinv, c.dg[0], c.dg[1], c.dg[2], c.dAp, st);
     BAH_CUDA_TRY(cudaGetLastError());
@@ -1112,7 +1114,11 @@ int bah_profile_read(bah_ctx* h, bah_profile* out) {
     return BAH_OK;
 }
 
-int bah_solve(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_stats* stats, void* stream) {
+}  // extern "C"
+
+// H x = b (adjoint = 0) or H^H x = b, i.e. H conj(x) = conj(b) (adjoint = 1)
+static int solve_impl(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_stats* stats, void* stream,
+                      int adjoint) {
     if (!h || !b || !x || nrhs < 0 || !(rtol > 0.0)) { set_error("bad argument"); return BAH_ERR_ARG; }
     Ctx& c = h->c;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1129,10 +1135,15 @@ int bah_solve(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_sta
         {
             Prof pr(c, BAH_K_SMALL, st, (double)nr * c.np * 32.0);
             launch_sanitize(c.Bs, c.n1, c.n2, nr, st);
+            if (adjoint) launch_conj(c.Bs, (size_t)nr * n, st);
         }
         double2* xd = dev_x ? xk : c.X;
         int s = fgmres_batch(c, c.Bs, xd, nr, rtol, stats ? stats + k0 : nullptr, st);
         if (s == BAH_ERR_CUDA || s == BAH_ERR_OOM || s == BAH_ERR_ARG) return s;
+        if (adjoint) {
+            Prof pr(c, BAH_K_SMALL, st, (double)nr * n * 32.0);
+            launch_conj(xd, (size_t)nr * n, st);
+        }
         if (!dev_x)
             BAH_CUDA_TRY(cudaMemcpyAsync(xk, c.X, (size_t)nr * n * sizeof(double2), cudaMemcpyDeviceToHost, st));
         if (s != BAH_OK && first_fail == BAH_OK) first_fail = s;
@@ -1148,6 +1159,40 @@ int bah_solve(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_sta
         }
     }
     return first_fail;
+}
+
+extern "C" {
+
+int bah_solve(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_stats* stats, void* stream) {
+    return solve_impl(h, b, x, nrhs, rtol, stats, stream, 0);
+}
+
+int bah_solve_adjoint(bah_ctx* h, const void* b, void* y, int nrhs, double rtol, bah_stats* stats, void* stream) {
+    return solve_impl(h, b, y, nrhs, rtol, stats, stream, 1);
+}
+
+int bah_misfit(bah_ctx* h, const void* x, const void* d, const int* rec, int nrec, int nrhs, void* adj,
+               double* misfit, void* stream) {
+    if (!h || !x || !d || !rec || !adj || !misfit || nrec < 1 || nrhs < 0) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = c.vec_len();
+    BAH_CUDA_TRY(cudaMemsetAsync(adj, 0, (size_t)nrhs * n * sizeof(double2), st));
+    if (nrhs == 0) return BAH_OK;
+    launch_misfit((const double2*)x, (const double2*)d, rec, nrec, nrhs, n, (double2*)adj, misfit, st);
+    BAH_CUDA_TRY(cudaGetLastError());
+    return BAH_OK;
+}
+
+int bah_gradient(bah_ctx* h, const void* x_fwd, const void* y_adj, int nrhs, double* g_lambda, double* g_mu,
+                 double* g_rho, void* stream) {
+    if (!h || !x_fwd || !y_adj || !g_lambda || !g_mu || !g_rho || nrhs < 0) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    if (nrhs == 0) return BAH_OK;
+    launch_gradient(c.n1, c.n2, c.h1, c.h2, c.omega, c.cinv, c.gam, c.vec_len(), nrhs, (const double2*)x_fwd,
+                    (const double2*)y_adj, g_lambda, g_mu, g_rho, (cudaStream_t)stream);
+    BAH_CUDA_TRY(cudaGetLastError());
+    return BAH_OK;
 }
 
 }  // extern "C"
