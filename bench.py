@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--levels", type=int, default=0)
     ap.add_argument("--max-coarse", type=int, default=1024)
     ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--krylov", default="df", choices=["fp64", "df"])
+    ap.add_argument("--krylov-fp64-steps", type=int, default=2,
+                    help="also time the same solve with the Krylov basis in IEEE FP64")
     return ap.parse_args()
 
 
@@ -207,7 +210,8 @@ def run_bah(args):
     import paper_2411_15897_gb300 as bah
 
     prob = W.config(args.config)
-    opts = dict(precision=bah.BAH_MIXED, levels=args.levels, max_coarse_cells=args.max_coarse, restart=args.restart)
+    opts = dict(precision=bah.BAH_MIXED, levels=args.levels, max_coarse_cells=args.max_coarse, restart=args.restart,
+                krylov_arith=bah.BAH_KRYLOV_DF if args.krylov == "df" else bah.BAH_KRYLOV_FP64)
     solver = bah.Solver.from_problem(prob, **opts)
     levels = solver.levels
     b_host = W.point_source(prob)
@@ -298,6 +302,26 @@ def run_bah(args):
                 "ms_per_step": statistics.mean(ms64), "relres_true": stt["relres_true"]}
         s64.close()
 
+    # the same mixed solve with the Krylov basis in IEEE FP64 instead of double-FP32
+    kfp64 = None
+    if args.krylov == "df" and args.krylov_fp64_steps > 0:
+        sk = bah.Solver.from_problem(prob, **dict(opts, krylov_arith=bah.BAH_KRYLOV_FP64))
+        xk = torch.zeros_like(b)
+        solve_once(sk, b, xk)
+        msk = []
+        for _ in range(args.krylov_fp64_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stk, sttk = solve_once(sk, b, xk)
+            e1.record(stream)
+            e1.synchronize()
+            msk.append(e0.elapsed_time(e1))
+        kfp64 = {"value": world * args.krylov_fp64_steps / (sum(msk) / 1e3), "unit": UNIT, "iters": sttk["iters"],
+                 "ms_per_step": statistics.mean(msk), "relres_true": sttk["relres_true"]}
+        sk.close()
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     bp = torch.from_numpy(b_host.copy()).pin_memory()
     xp = torch.zeros_like(bp).pin_memory()
@@ -355,12 +379,15 @@ def run_bah(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "mixed: bf16 coef / f32 multigrid / f64 FGMRES+operator+coarsest", "data": "synthetic",
+        "dtype": ("mixed: bf16 coefficients, f32 multigrid, f64 operator / Hessenberg / true residual / coarsest "
+                  "solve, " + ("double-f32 (48-bit) Gram-Schmidt" if args.krylov == "df" else "f64 Gram-Schmidt")),
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(prob.n), "unknowns": int(sum(W.compact_sizes(prob.n))),
                    "levels": levels, "cycle": "V(1,2)", "restart": args.restart, "iters": iters[-1],
                    "relres_true": relres, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"independent solves per GPU x{world}"},
         "fp64": fp64,
+        "krylov_fp64": kfp64,
         "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": e2e,
         "gpu_launches": prof_timed["launches"],

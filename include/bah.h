@@ -61,6 +61,12 @@ extern "C" {
 #define BAH_FP64   0   /* multigrid in complex FP64 with FP64 coefficients */
 #define BAH_MIXED  1   /* multigrid in complex FP32, coefficients stored in bfloat16 */
 
+/* arithmetic of the Krylov basis (Gram-Schmidt dots and updates); the
+ * Hessenberg least-squares update, the true residual and x are FP64 always */
+#define BAH_KRYLOV_FP64 0  /* IEEE FP64 */
+#define BAH_KRYLOV_DF   1  /* double-FP32: each real is an FP32 pair hi + lo (48-bit significand),
+                              products and sums by error-free FP32 transformations */
+
 #define BAH_CYCLE_V 0
 #define BAH_CYCLE_W 1
 
@@ -97,6 +103,7 @@ typedef struct {
     int    maxit;            /* maximum FGMRES iterations per right-hand side */
     int    rhs_block;        /* right-hand sides solved together by bah_solve (1..256); the
                                 context's workspace grows in proportion */
+    int    krylov_arith;     /* BAH_KRYLOV_FP64 or BAH_KRYLOV_DF */
 } bah_opts;
 
 typedef struct {
@@ -110,7 +117,8 @@ typedef struct {
 /* Fill *opts with the defaults: BAH_MIXED, automatic levels with at most 1024
  * coarsest cells, V(1,2), Jacobi weights 0.8, 0.8, 0.3 (Sec. 4.4.1), shift by
  * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels, 0.5 deeper; Sec. 4.4.3,
- * Table 4), bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1. */
+ * Table 4), bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1,
+ * BAH_KRYLOV_FP64. */
 void bah_default_opts(bah_opts* opts);
 
 /* Build a solver for one grid, medium and frequency.  Copies the host medium

@@ -32,6 +32,8 @@ BAH_CYCLE_V = 0
 BAH_CYCLE_W = 1
 BAH_INTERGRID_BILINEAR = 0
 BAH_INTERGRID_MIXED = 1
+BAH_KRYLOV_FP64 = 0
+BAH_KRYLOV_DF = 1
 
 # every symbol include/bah.h declares
 EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_apply_operator",
@@ -54,7 +56,7 @@ class bah_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("levels", C.c_int), ("max_coarse_cells", C.c_int), ("cycle", C.c_int),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("jacobi_w", C.c_double * 8), ("n_jacobi_w", C.c_int),
                 ("shift_alpha", C.c_double), ("intergrid", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
-                ("rhs_block", C.c_int)]
+                ("rhs_block", C.c_int), ("krylov_arith", C.c_int)]
 
 
 class bah_stats(C.Structure):

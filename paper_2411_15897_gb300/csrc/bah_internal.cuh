@@ -162,6 +162,9 @@ int  coarse_invert(int type, const StencilF64& S, double2* inv, double2* work, i
 template <class Vin>
 void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st,
                           int nrhs = 1, RhsStride rs = RhsStride());
+// y = H x written as double-float (float4) for the double-float Krylov basis
+template <class Vin>
+void launch_elastic_apply_df(const OpCoef& c, const Vin* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs);
 
 // multigrid (k_mg.cu)
 template <int MODE>
@@ -190,13 +193,13 @@ int launch_coop_cycle(const CoopArgs& a, int max_radius, int nsm, cudaStream_t s
 template <int MODE>
 void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
                          typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs = 1, RhsStride rs = RhsStride());
-template <int MODE>
+template <int MODE, class RIN = double2>
 void launch_distributor(int n1, int n2, double ihx, double ihz,
                         const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5,
-                        const double2* r, typename Prec<MODE>::V* tp, cudaStream_t st, int nrhs = 1,
+                        const RIN* r, typename Prec<MODE>::V* tp, cudaStream_t st, int nrhs = 1,
                         RhsStride rs = RhsStride());
-template <int MODE>
-void launch_u_rhs(int n1, int n2, double ihx, double ihz, const double2* r, const typename Prec<MODE>::V* ep,
+template <int MODE, class RIN = double2>
+void launch_u_rhs(int n1, int n2, double ihx, double ihz, const RIN* r, const typename Prec<MODE>::V* ep,
                   typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st, int nrhs = 1,
                   RhsStride rs = RhsStride());
 void launch_sanitize(double2* v, int n1, int n2, int nvec, cudaStream_t st);
@@ -235,6 +238,14 @@ void launch_arnoldi_givens(double2* Hm, int ldh, const double2* h1, const double
 void launch_triangular_solve(const double2* Hm, int ldh, const double2* g, const int* kk, double2* y, int nrhs,
                              const KS& ks, cudaStream_t st);
 void launch_init_arnoldi(const double* sc, double2* g, int m, double* status, int nrhs, const KS& ks, cudaStream_t st);
+
+// double-float Krylov kernels (k_krylov_df.cu)
+void launch_dot_norm_df(const float4* V, int k, const float4* w, size_t n, double2* partial, double2* out,
+                        const int* flag, int nrhs, const KS& ks, cudaStream_t st);
+void launch_axpy_norm_df(const float4* V, int k, const double2* coef, float4* w, size_t n, double* npart,
+                         const int* flag, int nrhs, const KS& ks, cudaStream_t st);
+void launch_scale_copy_df(const void* w, bool from64, const double* sc, int slot, float4* v, size_t n, size_t sw,
+                          size_t sv, int nrhs, const KS& ks, cudaStream_t st);
 
 // adjoint gradient (k_grad.cu)
 void launch_conj(double2* v, size_t n, cudaStream_t st);

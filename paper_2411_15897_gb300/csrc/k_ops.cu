@@ -5,6 +5,7 @@
 //   * s_u = r_u - B^T e_p, the back-substitution of the block-triangular
 //     solve with P = [A B^T; 0 H_p] (Eq. 3.5).
 #include "bah_internal.cuh"
+#include "df.cuh"
 
 namespace bah {
 
@@ -13,13 +14,28 @@ __device__ __forceinline__ double2 ld64(const V* p, int idx) {
     V v = p[idx];
     return make_double2((double)v.x, (double)v.y);
 }
+__device__ __forceinline__ double2 ld64(const float4* p, int idx) { return cdf_to_double2(p[idx]); }
+// preconditioner input in the preconditioner's real type R
+template <class R> __device__ __forceinline__ R ldr_in(const double2& v, int c) { return (R)(c ? v.y : v.x); }
+__device__ __forceinline__ float ldf_in(const double2& v, bool im) { return (float)(im ? v.y : v.x); }
+template <class R> struct InLoad;
+template <> struct InLoad<double> {
+    __device__ static double2 get(const double2* p, size_t i) { return p[i]; }
+    __device__ static double2 get(const float4* p, size_t i) { return cdf_to_double2(p[i]); }
+};
+template <> struct InLoad<float> {
+    __device__ static float2 get(const double2* p, size_t i) { const double2 v = p[i]; return make_float2((float)v.x, (float)v.y); }
+    __device__ static float2 get(const float4* p, size_t i) { const float4 v = p[i]; return make_float2(v.x + v.y, v.z + v.w); }
+};
+__device__ __forceinline__ void st_out(double2* y, size_t i, double2 v) { y[i] = v; }
+__device__ __forceinline__ void st_out(float4* y, size_t i, double2 v) { y[i] = cdf_from_double2(v); }
 
 // ---------------------------------------------------------------------------
 // y = H x  (b == nullptr)  or  y = b - H x,  one cell per thread.
 // conj != 0 applies H^H = conj(H) (H is complex symmetric).
 // ---------------------------------------------------------------------------
-template <class Vin>
-__global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __restrict__ x, double2* __restrict__ y,
+template <class Vin, class Vout>
+__global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __restrict__ x, Vout* __restrict__ y,
                                                        const double2* __restrict__ b, int conj, RhsStride rs) {
     const int n1 = c.n1, n2 = c.n2, np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,17 +97,24 @@ __global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __re
         if (j >= 1) y2 = csub(b[np + t], y2);
         yp = csub(b[2 * np + t], yp);
     }
-    y[t] = y1;
-    y[np + t] = y2;
-    y[2 * np + t] = yp;
+    st_out(y, t, y1);
+    st_out(y, np + t, y2);
+    st_out(y, 2 * np + t, yp);
 }
 
 template <class Vin>
 void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st,
                           int nrhs, RhsStride rs) {
     int np = c.n1 * c.n2;
-    k_elastic_apply<Vin><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(c, x, y, b, conj, rs);
+    k_elastic_apply<Vin, double2><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(c, x, y, b, conj, rs);
 }
+template <class Vin>
+void launch_elastic_apply_df(const OpCoef& c, const Vin* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs) {
+    int np = c.n1 * c.n2;
+    k_elastic_apply<Vin, float4><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(c, x, y, nullptr, 0, rs);
+}
+template void launch_elastic_apply_df<double2>(const OpCoef&, const double2*, float4*, cudaStream_t, int, RhsStride);
+template void launch_elastic_apply_df<float2>(const OpCoef&, const float2*, float4*, cudaStream_t, int, RhsStride);
 template void launch_elastic_apply<double2>(const OpCoef&, const double2*, double2*, const double2*, int, cudaStream_t,
                                             int, RhsStride);
 template void launch_elastic_apply<float2>(const OpCoef&, const float2*, double2*, const double2*, int, cudaStream_t,
@@ -100,11 +123,11 @@ template void launch_elastic_apply<float2>(const OpCoef&, const float2*, double2
 // ---------------------------------------------------------------------------
 // t_p = B r_u - A_p r_p   (r in FP64, t_p in the preconditioner's precision)
 // ---------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, class RIN>
 __global__ void __launch_bounds__(256) k_distributor(int n1, int n2, typename Prec<MODE>::R ihx,
                                                      typename Prec<MODE>::R ihz,
                                                      Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> f,
-                                                     const double2* __restrict__ r, typename Prec<MODE>::V* __restrict__ tp,
+                                                     const RIN* __restrict__ r, typename Prec<MODE>::V* __restrict__ tp,
                                                      RhsStride rs) {
     using V = typename Prec<MODE>::V;
     using R = typename Prec<MODE>::R;
@@ -115,7 +138,7 @@ __global__ void __launch_bounds__(256) k_distributor(int n1, int n2, typename Pr
     r += rr * rs.s0;
     tp += rr * rs.s1;
     const int i = t % n1, j = t / n1;
-    auto L = [&](int idx) { double2 v = r[idx]; return cmk<V>((R)v.x, (R)v.y); };
+    auto L = [&](int idx) { return InLoad<R>::get(r, idx); };
     const V z = czero<V>();
     const V u1c = (i >= 1) ? L(t) : z;
     const V u1e = (i + 1 < n1) ? L(t + 1) : z;
@@ -133,25 +156,31 @@ __global__ void __launch_bounds__(256) k_distributor(int n1, int n2, typename Pr
     tp[t] = csub(acc, ap);
 }
 
-template <int MODE>
+template <int MODE, class RIN>
 void launch_distributor(int n1, int n2, double ihx, double ihz,
-                        const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5, const double2* r,
+                        const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5, const RIN* r,
                         typename Prec<MODE>::V* tp, cudaStream_t st, int nrhs, RhsStride rs) {
     int np = n1 * n2;
-    k_distributor<MODE><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
+    k_distributor<MODE, RIN><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
                                                                        (typename Prec<MODE>::R)ihz, f5, r, tp, rs);
 }
-template void launch_distributor<BAH_FP64>(int, int, double, double, const Fine5<double, double2>&, const double2*,
-                                           double2*, cudaStream_t, int, RhsStride);
-template void launch_distributor<BAH_MIXED>(int, int, double, double, const Fine5<__nv_bfloat16, __nv_bfloat162>&,
-                                            const double2*, float2*, cudaStream_t, int, RhsStride);
+template void launch_distributor<BAH_FP64, double2>(int, int, double, double, const Fine5<double, double2>&,
+                                                    const double2*, double2*, cudaStream_t, int, RhsStride);
+template void launch_distributor<BAH_MIXED, double2>(int, int, double, double,
+                                                     const Fine5<__nv_bfloat16, __nv_bfloat162>&, const double2*,
+                                                     float2*, cudaStream_t, int, RhsStride);
+template void launch_distributor<BAH_FP64, float4>(int, int, double, double, const Fine5<double, double2>&,
+                                                   const float4*, double2*, cudaStream_t, int, RhsStride);
+template void launch_distributor<BAH_MIXED, float4>(int, int, double, double,
+                                                    const Fine5<__nv_bfloat16, __nv_bfloat162>&, const float4*,
+                                                    float2*, cudaStream_t, int, RhsStride);
 
 // ---------------------------------------------------------------------------
 // s_u = r_u - B^T e_p  (B^T = grad_h onto the interior faces)
 // ---------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, class RIN>
 __global__ void __launch_bounds__(256) k_u_rhs(int n1, int n2, typename Prec<MODE>::R ihx, typename Prec<MODE>::R ihz,
-                                               const double2* __restrict__ r, const typename Prec<MODE>::V* __restrict__ ep,
+                                               const RIN* __restrict__ r, const typename Prec<MODE>::V* __restrict__ ep,
                                                typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, RhsStride rs) {
     using V = typename Prec<MODE>::V;
     using R = typename Prec<MODE>::R;
@@ -167,12 +196,12 @@ __global__ void __launch_bounds__(256) k_u_rhs(int n1, int n2, typename Prec<MOD
     const V e = ep[t];
     V s1 = czero<V>(), s2 = czero<V>();
     if (i >= 1) {
-        double2 rv = r[t];
+        const auto rv = InLoad<R>::get(r, t);
         V ew = ep[t - 1];
         s1 = cmk<V>((R)rv.x - ihx * (e.x - ew.x), (R)rv.y - ihx * (e.y - ew.y));
     }
     if (j >= 1) {
-        double2 rv = r[np + t];
+        const auto rv = InLoad<R>::get(r, np + t);
         V es = ep[t - n1];
         s2 = cmk<V>((R)rv.x - ihz * (e.x - es.x), (R)rv.y - ihz * (e.y - es.y));
     }
@@ -180,17 +209,21 @@ __global__ void __launch_bounds__(256) k_u_rhs(int n1, int n2, typename Prec<MOD
     su2[t] = s2;
 }
 
-template <int MODE>
-void launch_u_rhs(int n1, int n2, double ihx, double ihz, const double2* r, const typename Prec<MODE>::V* ep,
+template <int MODE, class RIN>
+void launch_u_rhs(int n1, int n2, double ihx, double ihz, const RIN* r, const typename Prec<MODE>::V* ep,
                   typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st, int nrhs, RhsStride rs) {
     int np = n1 * n2;
-    k_u_rhs<MODE><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
+    k_u_rhs<MODE, RIN><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
                                                                  (typename Prec<MODE>::R)ihz, r, ep, su1, su2, rs);
 }
-template void launch_u_rhs<BAH_FP64>(int, int, double, double, const double2*, const double2*, double2*, double2*,
-                                     cudaStream_t, int, RhsStride);
-template void launch_u_rhs<BAH_MIXED>(int, int, double, double, const double2*, const float2*, float2*, float2*,
-                                      cudaStream_t, int, RhsStride);
+template void launch_u_rhs<BAH_FP64, double2>(int, int, double, double, const double2*, const double2*, double2*,
+                                              double2*, cudaStream_t, int, RhsStride);
+template void launch_u_rhs<BAH_MIXED, double2>(int, int, double, double, const double2*, const float2*, float2*,
+                                               float2*, cudaStream_t, int, RhsStride);
+template void launch_u_rhs<BAH_FP64, float4>(int, int, double, double, const float4*, const double2*, double2*,
+                                             double2*, cudaStream_t, int, RhsStride);
+template void launch_u_rhs<BAH_MIXED, float4>(int, int, double, double, const float4*, const float2*, float2*,
+                                              float2*, cudaStream_t, int, RhsStride);
 
 // ---------------------------------------------------------------------------
 // element-wise precision conversion

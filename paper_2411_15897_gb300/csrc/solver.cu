@@ -65,6 +65,7 @@ struct Ctx {
     void* ztmp = nullptr;                // preconditioner output in storage precision (apply hook)
     // right-hand-side batching
     int nbatch = 1;                      // right-hand sides solved together
+    bool kdf = false;                    // Krylov basis in double-float (BAH_KRYLOV_DF)
     int* active = nullptr;               // device, per right-hand side
     int* jk = nullptr;                   // device, Krylov dimension per right-hand side at a restart
     int* hint = nullptr;                 // pinned host staging ring for active / jk (kIntSlots * nbatch)
@@ -418,7 +419,8 @@ struct MG {
 
     // z = P^{-1} D r for bt.nr right-hand sides  (r FP64 padded vectors with
     // stride rs, z storage-precision padded vectors with stride zs)
-    static void precond(Ctx& c, const double2* r, size_t rstride, V* z, size_t zstride, const Batch& bt,
+    template <class RIN>
+    static void precond(Ctx& c, const RIN* r, size_t rstride, V* z, size_t zstride, const Batch& bt,
                         cudaStream_t st) {
         const int np = c.np;
         const double vs = sizeof(V);
@@ -427,7 +429,7 @@ struct MG {
             RhsStride rs;
             rs.s0 = rstride; rs.s1 = np; rs.active = bt.active;
             Prof pr(c, BAH_K_DISTRIB, st, (double)bt.nr * np * (48.0 + sizeof(C) + sizeof(CC) + vs));
-            launch_distributor<MODE>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, f5, r, (V*)c.vB[0][2], st, bt.nr, rs);
+            launch_distributor<MODE, RIN>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, f5, r, (V*)c.vB[0][2], st, bt.nr, rs);
         }
         V* outp[1] = {z + 2 * (size_t)np};
         cycle(c, 0, 2, 1, outp, zstride, bt, st);
@@ -435,18 +437,19 @@ struct MG {
             RhsStride rs;
             rs.s0 = rstride; rs.s1 = zstride; rs.s2 = np; rs.active = bt.active;
             Prof pr(c, BAH_K_URHS, st, (double)bt.nr * np * (32.0 + 3.0 * vs));
-            launch_u_rhs<MODE>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, r, z + 2 * (size_t)np, (V*)c.vB[0][0],
-                               (V*)c.vB[0][1], st, bt.nr, rs);
+            launch_u_rhs<MODE, RIN>(c.n1, c.n2, 1.0 / c.h1, 1.0 / c.h2, r, z + 2 * (size_t)np, (V*)c.vB[0][0],
+                                    (V*)c.vB[0][1], st, bt.nr, rs);
         }
         V* outu[2] = {z, z + (size_t)np};
         cycle(c, 0, 0, 2, outu, zstride, bt, st);
     }
 };
 
-static void precond_any(Ctx& c, const double2* r, size_t rstride, void* z, size_t zstride, const Batch& bt,
+template <class RIN>
+static void precond_any(Ctx& c, const RIN* r, size_t rstride, void* z, size_t zstride, const Batch& bt,
                         cudaStream_t st) {
-    if (c.mode == BAH_MIXED) MG<BAH_MIXED>::precond(c, r, rstride, (float2*)z, zstride, bt, st);
-    else MG<BAH_FP64>::precond(c, r, rstride, (double2*)z, zstride, bt, st);
+    if (c.mode == BAH_MIXED) MG<BAH_MIXED>::template precond<RIN>(c, r, rstride, (float2*)z, zstride, bt, st);
+    else MG<BAH_FP64>::template precond<RIN>(c, r, rstride, (double2*)z, zstride, bt, st);
 }
 // algorithmic bytes of one operator apply: input (3 components), FP64
 // output, coefficients cx, nx (z-aliases when h1 == h2), d1, d2, 1/(lambda+mu)
@@ -454,13 +457,18 @@ static double op_bytes(const Ctx& c, double in_bytes, bool residual) {
     const double coef = (c.h1 == c.h2 ? 16.0 : 32.0) + 32.0 + 8.0;
     return (double)c.np * (3.0 * in_bytes + 48.0 + coef + (residual ? 48.0 : 0.0));
 }
-static void op_apply_z(Ctx& c, const void* z, size_t zstride, double2* y, size_t ystride, const Batch& bt,
+static void op_apply_z(Ctx& c, const void* z, size_t zstride, void* y, size_t ystride, const Batch& bt,
                        cudaStream_t st) {
     Prof pr(c, BAH_K_OPERATOR, st, bt.nr * op_bytes(c, (double)c.vsz, false));
     RhsStride rs;
     rs.s0 = zstride; rs.s1 = ystride; rs.active = bt.active;
-    if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, y, nullptr, 0, st, bt.nr, rs);
-    else launch_elastic_apply<double2>(c.op, (const double2*)z, y, nullptr, 0, st, bt.nr, rs);
+    if (c.kdf) {
+        if (c.mode == BAH_MIXED) launch_elastic_apply_df<float2>(c.op, (const float2*)z, (float4*)y, st, bt.nr, rs);
+        else launch_elastic_apply_df<double2>(c.op, (const double2*)z, (float4*)y, st, bt.nr, rs);
+    } else {
+        if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
+        else launch_elastic_apply<double2>(c.op, (const double2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -668,18 +676,22 @@ static void iter_body(Ctx& c, int j, cudaStream_t st) {
     Batch bt;
     bt.nr = nb;
     bt.active = c.active;
-    double2* vj = c.V + (size_t)j * n;
     void* zj = (char*)c.Z + (size_t)j * n * c.vsz;
-    precond_any(c, vj, ks.sv, zj, ks.sz, bt, st);
+    float4* Vd = (float4*)c.V;
+    float4* Wd = (float4*)c.W;
+    if (c.kdf) precond_any(c, Vd + (size_t)j * n, ks.sv, zj, ks.sz, bt, st);
+    else precond_any(c, c.V + (size_t)j * n, ks.sv, zj, ks.sz, bt, st);
     op_apply_z(c, zj, ks.sz, c.W, n, bt, st);
     const double k1 = j + 1;
     {
         Prof pr(c, BAH_K_DOT, st, nb * (k1 + 1) * n * 16.0, 2);
-        launch_dot_norm(c.V, j + 1, c.W, n, c.partial, c.h1v, nullptr, nb, ks, st);
+        if (c.kdf) launch_dot_norm_df(Vd, j + 1, Wd, n, c.partial, c.h1v, nullptr, nb, ks, st);
+        else launch_dot_norm(c.V, j + 1, c.W, n, c.partial, c.h1v, nullptr, nb, ks, st);
     }
     {
         Prof pr(c, BAH_K_AXPY, st, nb * (k1 + 2) * n * 16.0);
-        launch_axpy_norm(c.V, j + 1, c.h1v, c.W, n, c.dpart, nullptr, nb, ks, st);
+        if (c.kdf) launch_axpy_norm_df(Vd, j + 1, c.h1v, Wd, n, c.dpart, nullptr, nb, ks, st);
+        else launch_axpy_norm(c.V, j + 1, c.h1v, c.W, n, c.dpart, nullptr, nb, ks, st);
     }
     {
         Prof pr(c, BAH_K_NORM, st, 0.0);
@@ -687,17 +699,20 @@ static void iter_body(Ctx& c, int j, cudaStream_t st) {
     }
     {
         Prof pr(c, BAH_K_DOT, st, 0.0, 2);      // runs only where the flag is set (bytes counted as zero)
-        launch_dot_norm(c.V, j + 1, c.W, n, c.partial, c.h2v, c.gsflag, nb, ks, st);
+        if (c.kdf) launch_dot_norm_df(Vd, j + 1, Wd, n, c.partial, c.h2v, c.gsflag, nb, ks, st);
+        else launch_dot_norm(c.V, j + 1, c.W, n, c.partial, c.h2v, c.gsflag, nb, ks, st);
     }
     {
         Prof pr(c, BAH_K_AXPY, st, 0.0);
-        launch_axpy_norm(c.V, j + 1, c.h2v, c.W, n, c.dpart, c.gsflag, nb, ks, st);
+        if (c.kdf) launch_axpy_norm_df(Vd, j + 1, c.h2v, Wd, n, c.dpart, c.gsflag, nb, ks, st);
+        else launch_axpy_norm(c.V, j + 1, c.h2v, c.W, n, c.dpart, c.gsflag, nb, ks, st);
     }
     {
         Prof pr(c, BAH_K_SMALL, st, nb * n * 32.0, 3);
         launch_pass2_norm(c.dpart, c.gsflag, c.nrm, nb, ks, st);
         launch_arnoldi_givens(c.Hm, m + 1, c.h1v, c.h2v, c.nrm, j, c.cs, c.sn, c.g, c.status, nb, ks, st);
-        launch_scale_copy(c.W, c.nrm, 2, c.V + (size_t)(j + 1) * n, n, n, ks.sv, nb, ks, st);
+        if (c.kdf) launch_scale_copy_df(c.W, false, c.nrm, 2, Vd + (size_t)(j + 1) * n, n, n, ks.sv, nb, ks, st);
+        else launch_scale_copy(c.W, c.nrm, 2, c.V + (size_t)(j + 1) * n, n, n, ks.sv, nb, ks, st);
     }
     cudaMemcpyAsync(status_slot(c, j), c.status, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st);
 }
@@ -796,7 +811,8 @@ static int fgmres_batch(Ctx& c, const double2* b, double2* x, int nr, double rto
         // v_0 = r / beta, g = beta e_1
         {
             Prof pr(c, BAH_K_SMALL, st, (double)nr * n * 32.0, 2);
-            launch_scale_copy(c.R, c.nrm, 0, c.V, n, n, ks.sv, nb, ks, st);
+            if (c.kdf) launch_scale_copy_df(c.R, true, c.nrm, 0, (float4*)c.V, n, n, ks.sv, nb, ks, st);
+            else launch_scale_copy(c.R, c.nrm, 0, c.V, n, n, ks.sv, nb, ks, st);
             launch_init_arnoldi(c.nrm, c.g, m, c.status, nb, ks, st);
         }
         const int mm = std::min(m, c.o.maxit - total);
@@ -915,6 +931,7 @@ void bah_default_opts(bah_opts* o) {
     o->restart = 20;
     o->maxit = 5000;
     o->rhs_block = 1;
+    o->krylov_arith = BAH_KRYLOV_FP64;
 }
 
 const char* bah_status_string(int s) {
@@ -951,6 +968,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     if (o.restart < 1 || o.restart > 64) { set_error("restart must be in 1..64"); return BAH_ERR_ARG; }
     if (o.maxit < 1) { set_error("maxit must be >= 1"); return BAH_ERR_ARG; }
     if (o.rhs_block < 1 || o.rhs_block > 256) { set_error("rhs_block must be in 1..256"); return BAH_ERR_ARG; }
+    if (o.krylov_arith != BAH_KRYLOV_FP64 && o.krylov_arith != BAH_KRYLOV_DF) { set_error("bad krylov_arith"); return BAH_ERR_ARG; }
     if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre > 8 || o.nu_post > 8) { set_error("bad nu"); return BAH_ERR_ARG; }
     if (o.n_jacobi_w < 1 || o.n_jacobi_w > 8) { set_error("n_jacobi_w must be in 1..8"); return BAH_ERR_ARG; }
     if (o.intergrid != BAH_INTERGRID_BILINEAR && o.intergrid != BAH_INTERGRID_MIXED) {
@@ -970,6 +988,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     c.vsz = c.mode == BAH_MIXED ? sizeof(float2) : sizeof(double2);
     c.m = o.restart;
     c.nbatch = o.rhs_block;
+    c.kdf = o.krylov_arith == BAH_KRYLOV_DF;
     // levels
     int L = 1;
     {

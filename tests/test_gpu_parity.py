@@ -214,10 +214,10 @@ def test_preconditioner_matches_oracle(prec, name, systems):
 # ----------------------------------------------------------------------------
 # solves
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_solve_c1_reaches_tolerance(prec, systems):
+@pytest.mark.parametrize("prec,krylov", [("fp64", 0), ("mixed", 0), ("fp64", 1), ("mixed", 1)])
+def test_solve_c1_reaches_tolerance(prec, krylov, systems):
     p, S = get("c1", systems)
-    s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED)
+    s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, krylov_arith=krylov)
     b = W.point_source(p)
     x, status, st = s.solve(to_dev(b), rtol=1e-6)
     assert status == bah.BAH_OK, st
@@ -231,12 +231,15 @@ def test_solve_c1_reaches_tolerance(prec, systems):
     s.close()
 
 
-def test_solve_fp64_iterates_match_oracle_fgmres(systems):
-    """FP64 mode: the GPU's FGMRES(20) iterate after k steps equals the oracle's
-    (same preconditioner, same Krylov space; CGS2 vs MGS orthogonalisation)."""
+@pytest.mark.parametrize("krylov", [bah.BAH_KRYLOV_FP64, bah.BAH_KRYLOV_DF])
+def test_solve_fp64_iterates_match_oracle_fgmres(krylov, systems):
+    """FP64 multigrid: the GPU's FGMRES(20) iterate after k steps equals the
+    oracle's (same preconditioner, same Krylov space; selective
+    reorthogonalisation vs MGS), with the Krylov basis in FP64 or in
+    double-FP32 (48-bit) arithmetic."""
     p, S = get("layered_64x32", systems)
     for k in (3, 7, 25):
-        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, maxit=k, levels=3)
+        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, maxit=k, levels=3, krylov_arith=krylov)
         b = W.point_source(p)
         x, status, st = s.solve(to_dev(b), rtol=1e-12)
         pc = precond.multigrid(S, 3, precond.default_alpha(3))
@@ -247,14 +250,15 @@ def test_solve_fp64_iterates_match_oracle_fgmres(systems):
         s.close()
 
 
-def test_solve_c2_full_size_mixed_and_host_buffers():
+@pytest.mark.parametrize("krylov", [bah.BAH_KRYLOV_FP64, bah.BAH_KRYLOV_DF])
+def test_solve_c2_full_size_mixed_and_host_buffers(krylov):
     """The benchmark workload (512x512 layered) in the launch configuration the
     benchmark times: mixed precision, default options; the residual is
     recomputed by the oracle's assembled operator.  The same solve through host
     buffers gives the same iterate."""
     p = W.config("c2")
     S = elastic.from_problem(p)
-    s = bah.Solver.from_problem(p, precision=bah.BAH_MIXED)
+    s = bah.Solver.from_problem(p, precision=bah.BAH_MIXED, krylov_arith=krylov)
     b = W.point_source(p)
     x, status, st = s.solve(to_dev(b), rtol=1e-6)
     assert status == bah.BAH_OK, st
@@ -387,17 +391,17 @@ def test_cooperative_levels_match_standalone_kernels(prec, monkeypatch):
 # ----------------------------------------------------------------------------
 # batched right-hand sides
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [bah.BAH_MIXED, bah.BAH_FP64])
-def test_batched_solve_equals_sequential(prec, systems):
+@pytest.mark.parametrize("prec,krylov", [(bah.BAH_MIXED, 0), (bah.BAH_FP64, 0), (bah.BAH_MIXED, 1)])
+def test_batched_solve_equals_sequential(prec, krylov, systems):
     """rhs_block > 1 advances independent FGMRES recurrences in lockstep with
     the same per-right-hand-side arithmetic: identical iterates and counts,
     including a ragged last batch (5 right-hand sides, batches of 3)."""
     p, S = get("layered_64x32", systems)
     srcs = [(8 + 12 * k, 6) for k in range(5)]
     b = np.stack([W.point_source(p, s) for s in srcs])
-    s1 = bah.Solver.from_problem(p, precision=prec, levels=3)
+    s1 = bah.Solver.from_problem(p, precision=prec, levels=3, krylov_arith=krylov)
     x1, st1, stats1 = s1.solve(to_dev(b), rtol=1e-7)
-    s3 = bah.Solver.from_problem(p, precision=prec, levels=3, rhs_block=3)
+    s3 = bah.Solver.from_problem(p, precision=prec, levels=3, rhs_block=3, krylov_arith=krylov)
     x3, st3, stats3 = s3.solve(to_dev(b), rtol=1e-7)
     assert st1 == st3 == bah.BAH_OK
     assert [q["iters"] for q in stats1] == [q["iters"] for q in stats3]
