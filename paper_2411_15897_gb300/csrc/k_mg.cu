@@ -61,7 +61,9 @@ __device__ __forceinline__ void apply_fine5(const Fine5<typename MGT<MODE>::C, t
 }
 
 
-// A x at point (i, j) of a level-0 block where x is given by an accessor X(index)
+// A x at point (i, j) of a level-0 block where x is given by an accessor X(index).
+// The four neighbour terms are loaded unconditionally with clamped indices and
+// masked, so the loads issue together.
 template <int MODE, class XF>
 __device__ __forceinline__ typename MGT<MODE>::V apply_fine5_fn(const Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC>& f,
                                                                int type, int i, int j, int t, XF X) {
@@ -69,49 +71,76 @@ __device__ __forceinline__ typename MGT<MODE>::V apply_fine5_fn(const Fine5<type
     using R = typename MGT<MODE>::R;
     const int n1 = f.n1, n2 = f.n2;
     const auto* dgp = type == 0 ? f.dg0 : (type == 1 ? f.dg1 : f.dg2);
-    V acc = cmul(ldc(dgp[t]), X(t));
-    auto sub = [&](R k, V v) { acc.x -= k * v.x; acc.y -= k * v.y; };
+    // neighbours W, E, S, N: existence, coefficient index and array per block type
+    bool ok[4];
+    int ci[4];
+    const typename MGT<MODE>::C* arr[4];
     if (type == 0) {
-        if (i - 1 >= 1) sub(ldr(f.cx[t - 1]), X(t - 1));
-        if (i + 1 <= n1 - 1) sub(ldr(f.cx[t]), X(t + 1));
-        if (j >= 1) sub(ldr(f.nz[t]), X(t - n1));
-        if (j + 1 <= n2 - 1) sub(ldr(f.nz[t + n1]), X(t + n1));
+        ok[0] = i - 1 >= 1;       ci[0] = t - 1;  arr[0] = f.cx;
+        ok[1] = i + 1 <= n1 - 1;  ci[1] = t;      arr[1] = f.cx;
+        ok[2] = j >= 1;           ci[2] = t;      arr[2] = f.nz;
+        ok[3] = j + 1 <= n2 - 1;  ci[3] = t + n1; arr[3] = f.nz;
     } else if (type == 1) {
-        if (j - 1 >= 1) sub(ldr(f.cz[t - n1]), X(t - n1));
-        if (j + 1 <= n2 - 1) sub(ldr(f.cz[t]), X(t + n1));
-        if (i >= 1) sub(ldr(f.nx[t]), X(t - 1));
-        if (i + 1 <= n1 - 1) sub(ldr(f.nx[t + 1]), X(t + 1));
+        ok[0] = i >= 1;           ci[0] = t;      arr[0] = f.nx;
+        ok[1] = i + 1 <= n1 - 1;  ci[1] = t + 1;  arr[1] = f.nx;
+        ok[2] = j - 1 >= 1;       ci[2] = t - n1; arr[2] = f.cz;
+        ok[3] = j + 1 <= n2 - 1;  ci[3] = t;      arr[3] = f.cz;
     } else {
-        if (i >= 1) sub(ldr(f.wx[t - 1]), X(t - 1));
-        if (i + 1 < n1) sub(ldr(f.wx[t + 1]), X(t + 1));
-        if (j >= 1) sub(ldr(f.wz[t - n1]), X(t - n1));
-        if (j + 1 < n2) sub(ldr(f.wz[t + n1]), X(t + n1));
+        ok[0] = i >= 1;           ci[0] = t - 1;  arr[0] = f.wx;
+        ok[1] = i + 1 < n1;       ci[1] = t + 1;  arr[1] = f.wx;
+        ok[2] = j >= 1;           ci[2] = t - n1; arr[2] = f.wz;
+        ok[3] = j + 1 < n2;       ci[3] = t + n1; arr[3] = f.wz;
+    }
+    const int nb[4] = {t - 1, t + 1, t - n1, t + n1};
+    R k[4];
+    V xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        k[q] = ldr(arr[q][ok[q] ? ci[q] : t]);
+        xv[q] = X(ok[q] ? nb[q] : t);
+    }
+    const V dg = ldc(dgp[t]);
+    V acc = cmul(dg, X(t));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const R kk = ok[q] ? k[q] : R(0);
+        acc.x -= kk * xv[q].x;
+        acc.y -= kk * xv[q].y;
     }
     return acc;
 }
 
 // RM is the compile-time maximum radius (1 or 2); rx, rz <= RM are the block's
-// radii, so the loops unroll fully and the loads issue back to back.
+// radii.  The loops unroll fully and every candidate load is issued with an
+// index clamped into range (out-of-range terms are masked to zero), so all
+// loads go out back to back instead of waiting behind per-neighbour branches.
 template <int MODE, int RM, class XF>
 __device__ __forceinline__ typename MGT<MODE>::V apply_stencil_fn(const typename MGT<MODE>::CC* __restrict__ S, int rx,
                                                                  int rz, int n1, int n2, int i, int j, int t, XF X) {
     using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
     const size_t np = (size_t)n1 * n2;
     const int wx = 2 * rx + 1;
-    V acc = czero<V>();
+    V sv[(2 * RM + 1) * (2 * RM + 1)], xv[(2 * RM + 1) * (2 * RM + 1)];
+    bool in[(2 * RM + 1) * (2 * RM + 1)];
 #pragma unroll
     for (int dz = -RM; dz <= RM; ++dz) {
-        const int jj = j + dz;
-        if (dz < -rz || dz > rz || jj < 0 || jj >= n2) continue;
 #pragma unroll
         for (int dx = -RM; dx <= RM; ++dx) {
-            const int ii = i + dx;
-            if (dx < -rx || dx > rx || ii < 0 || ii >= n1) continue;
-            const V sv = ldc(S[(size_t)((dz + rz) * wx + (dx + rx)) * np + t]);
-            const V v = X(jj * n1 + ii);
-            acc.x += sv.x * v.x - sv.y * v.y;
-            acc.y += sv.x * v.y + sv.y * v.x;
+            const int q = (dz + RM) * (2 * RM + 1) + (dx + RM);
+            const int ii = i + dx, jj = j + dz;
+            in[q] = dx >= -rx && dx <= rx && dz >= -rz && dz <= rz && ii >= 0 && ii < n1 && jj >= 0 && jj < n2;
+            const int slot = in[q] ? (dz + rz) * wx + (dx + rx) : 0;
+            sv[q] = ldc(S[(size_t)slot * np + t]);
+            xv[q] = X(in[q] ? jj * n1 + ii : t);
         }
+    }
+    V acc = czero<V>();
+#pragma unroll
+    for (int q = 0; q < (2 * RM + 1) * (2 * RM + 1); ++q) {
+        const R m = in[q] ? R(1) : R(0);
+        acc.x += m * (sv[q].x * xv[q].x - sv[q].y * xv[q].y);
+        acc.y += m * (sv[q].x * xv[q].y + sv[q].y * xv[q].x);
     }
     return acc;
 }
@@ -345,6 +374,11 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 // ---------------------------------------------------------------------------
 template <class V> struct PtrSet { V* p[3]; size_t s = 0; };
 
+// support of a 1-D restriction row for coarse index c: first fine index
+__host__ __device__ __forceinline__ int rbase(bool nodal, int intergrid, int c) {
+    return nodal ? 2 * c - 1 : (intergrid == BAH_INTERGRID_MIXED ? 2 * c : 2 * c - 1);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> fine,
                                                   PtrSet<typename MGT<MODE>::V> cb, int intergrid) {
@@ -360,18 +394,29 @@ __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, 
     if (valid_pt(B.type, I, J)) {
         const bool nodx = B.type == 0, nodz = B.type == 1;
         const V* r = B.xout + rr * B.sxo;
-        for (int fj = 2 * J - 2; fj <= 2 * J + 3; ++fj) {
-            const R wz = rw_axis_t<R>(nodz, intergrid, n2, J, fj);
-            if (wz == R(0)) continue;
-            for (int fi = 2 * I - 2; fi <= 2 * I + 3; ++fi) {
-                const R wxw = rw_axis_t<R>(nodx, intergrid, n1, I, fi);
-                if (wxw == R(0)) continue;
-                const R wgt = wz * wxw;
-                const V v = r[fj * n1 + fi];
-                acc.x += wgt * v.x;
-                acc.y += wgt * v.y;
-            }
+        const int bx = rbase(nodx, intergrid, I), bz = rbase(nodz, intergrid, J);
+        R wxs[4], wzs[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            wxs[q] = rw_axis_t<R>(nodx, intergrid, n1, I, bx + q);
+            wzs[q] = rw_axis_t<R>(nodz, intergrid, n2, J, bz + q);
         }
+        V v[16];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool ok = wzs[a] != R(0) && wxs[q] != R(0);
+                v[a * 4 + q] = r[ok ? (bz + a) * n1 + (bx + q) : 0];
+            }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const R wgt = wzs[a] * wxs[q];
+                acc.x += wgt * v[a * 4 + q].x;
+                acc.y += wgt * v[a * 4 + q].y;
+            }
     }
     cb.p[blockIdx.y][rr * cb.s + t] = acc;
 }
@@ -396,7 +441,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(LvlSet<typename MGT<MODE>::
     using V = typename MGT<MODE>::V;
     using R = typename MGT<MODE>::R;
     const auto& B = fine.blk[blockIdx.y];
-    const int n1 = fine.n1, n2 = fine.n2, n1c = n1 / 2, n2c = n2 / 2;
+    const int n1 = fine.n1, n2 = fine.n2, n1c = n1 / 2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int rr = blockIdx.z;
     if (t >= n1 * n2 || (fine.active && !fine.active[rr])) return;
@@ -405,21 +450,30 @@ __global__ void __launch_bounds__(256) k_prolong_add(LvlSet<typename MGT<MODE>::
     const bool nodx = B.type == 0, nodz = B.type == 1;
     const V* e = ce.p[blockIdx.y] + rr * ce.s;
     V* xo = B.xout + rr * B.sxo;
-    V acc = czero<V>();
-    for (int cj = (j >> 1) - 1; cj <= (j >> 1) + 1; ++cj) {
-        const R pz = pw_axis_t<R>(nodz, n2, j, cj);
-        if (pz == R(0)) continue;
-        for (int ci = (i >> 1) - 1; ci <= (i >> 1) + 1; ++ci) {
-            const R px = pw_axis_t<R>(nodx, n1, i, ci);
-            if (px == R(0)) continue;
-            const R wgt = px * pz;
-            const V v = e[cj * n1c + ci];
-            acc.x += wgt * v.x;
-            acc.y += wgt * v.y;
-        }
+    R px[3], pz[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        px[q] = pw_axis_t<R>(nodx, n1, i, (i >> 1) - 1 + q);
+        pz[q] = pw_axis_t<R>(nodz, n2, j, (j >> 1) - 1 + q);
     }
-    V x = xo[t];
-    xo[t] = cadd(x, acc);
+    V v[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const bool ok = pz[a] != R(0) && px[q] != R(0);
+            v[a * 3 + q] = e[ok ? ((j >> 1) - 1 + a) * n1c + ((i >> 1) - 1 + q) : 0];
+        }
+    V acc = xo[t];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const R wgt = pz[a] * px[q];
+            acc.x += wgt * v[a * 3 + q].x;
+            acc.y += wgt * v[a * 3 + q].y;
+        }
+    xo[t] = acc;
 }
 
 template <int MODE>
