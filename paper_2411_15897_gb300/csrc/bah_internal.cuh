@@ -13,11 +13,40 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/bah.h"
 
 namespace bah {
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Hot kernels begin with pdl_prologue(): wait
+// until the preceding kernel of the stream has completed and flushed its
+// memory (so nothing produced upstream is read early and nothing read
+// upstream is overwritten early), then allow the next kernel to start
+// launching.  Launched with launch_pdl(), the next kernel's launch overlaps
+// this kernel's execution; launched normally, both instructions are no-ops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // precision traits: V = complex vector element, R = real arithmetic type,

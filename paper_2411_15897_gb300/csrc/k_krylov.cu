@@ -46,6 +46,7 @@ __device__ __forceinline__ bool inactive(const KS& ks, int r) { return ks.active
 __global__ void __launch_bounds__(256) k_dot_norm_partial(const double2* __restrict__ V, int k,
                                                           const double2* __restrict__ w, size_t n,
                                                           double2* __restrict__ partial, const int* flag, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.z;
     if (inactive(ks, r) || (flag && flag[r] == 0)) return;
     V += r * ks.sv;
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(256) k_dot_norm_partial(const double2* __restr
 }
 __global__ void __launch_bounds__(256) k_reduce_rows(const double2* __restrict__ partial, int np, double2* out,
                                                      const int* flag, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.z;
     if (inactive(ks, r)) return;
     partial += r * ks.sp;
@@ -90,14 +92,15 @@ __global__ void __launch_bounds__(256) k_reduce_rows(const double2* __restrict__
 }
 void launch_dot_norm(const double2* V, int k, const double2* w, size_t n, double2* partial, double2* out,
                      const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    k_dot_norm_partial<<<dim3(RED_CTAS, k + 1, nrhs), 256, 0, st>>>(V, k, w, n, partial, flag, ks);
-    k_reduce_rows<<<dim3(1, k + 1, nrhs), 256, 0, st>>>(partial, RED_CTAS, out, flag, ks);
+    launch_pdl(k_dot_norm_partial, dim3(dim3(RED_CTAS, k + 1, nrhs)), dim3(256), 0, st, V, k, w, n, partial, flag, ks);
+    launch_pdl(k_reduce_rows, dim3(dim3(1, k + 1, nrhs)), dim3(256), 0, st, partial, RED_CTAS, out, flag, ks);
 }
 
 // w -= sum_i coef[i] V_i, and per-CTA partial sums of |w_new|^2
 __global__ void __launch_bounds__(256) k_axpy_norm(const double2* __restrict__ V, int k,
                                                    const double2* __restrict__ coef, double2* __restrict__ w, size_t n,
                                                    double* __restrict__ npart, const int* flag, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.z;
     if (inactive(ks, r) || (flag && flag[r] == 0)) return;
     V += r * ks.sv;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(256) k_axpy_norm(const double2* __restrict__ V
 }
 void launch_axpy_norm(const double2* V, int k, const double2* coef, double2* w, size_t n, double* npart,
                       const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    k_axpy_norm<<<dim3(RED_CTAS, 1, nrhs), 256, 0, st>>>(V, k, coef, w, n, npart, flag, ks);
+    launch_pdl(k_axpy_norm, dim3(dim3(RED_CTAS, 1, nrhs)), dim3(256), 0, st, V, k, coef, w, n, npart, flag, ks);
 }
 
 // reduce the pass-1 norm, decide on the second pass, set ||w|| for the Givens
@@ -131,6 +134,7 @@ void launch_axpy_norm(const double2* V, int k, const double2* coef, double2* w, 
 // ||w'||^2 < ||w||^2 / 2
 __global__ void __launch_bounds__(256) k_dgks_decide(const double* npart, int np, const double2* h1norm, int k,
                                                      int* flag, double* sc, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.x;
     if (inactive(ks, r)) return;
     npart += r * RED_CTAS;
@@ -147,10 +151,11 @@ __global__ void __launch_bounds__(256) k_dgks_decide(const double* npart, int np
 }
 void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* sc, int nrhs,
                         const KS& ks, cudaStream_t st) {
-    k_dgks_decide<<<nrhs, 256, 0, st>>>(npart, RED_CTAS, h1norm, k, flag, sc, ks);
+    launch_pdl(k_dgks_decide, dim3(nrhs), dim3(256), 0, st, npart, RED_CTAS, h1norm, k, flag, sc, ks);
 }
 // after pass 2: ||w''|| replaces ||w'||
 __global__ void __launch_bounds__(256) k_pass2_norm(const double* npart, int np, const int* flag, double* sc, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.x;
     if (inactive(ks, r) || flag[r] == 0) return;
     npart += r * RED_CTAS;
@@ -160,13 +165,14 @@ __global__ void __launch_bounds__(256) k_pass2_norm(const double* npart, int np,
     if (threadIdx.x == 0) sc[r * 8 + 2] = sqrt(s.x);
 }
 void launch_pass2_norm(const double* npart, const int* flag, double* sc, int nrhs, const KS& ks, cudaStream_t st) {
-    k_pass2_norm<<<nrhs, 256, 0, st>>>(npart, RED_CTAS, flag, sc, ks);
+    launch_pdl(k_pass2_norm, dim3(nrhs), dim3(256), 0, st, npart, RED_CTAS, flag, sc, ks);
 }
 
 // ---------------------------------------------------------------------------
 // 2-norm of w per right-hand side: sc[r*8 + slot] = ||w_r||
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_norm2_partial(const double2* __restrict__ w, size_t n, double* partial, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.y;
     if (inactive(ks, r)) return;
     w += r * ks.sw;
@@ -179,6 +185,7 @@ __global__ void __launch_bounds__(256) k_norm2_partial(const double2* __restrict
     if (threadIdx.x == 0) partial[r * RED_CTAS + blockIdx.x] = s.x;
 }
 __global__ void __launch_bounds__(256) k_norm2_final(const double* partial, int np, double* sc, int slot, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.x;
     if (inactive(ks, r)) return;
     double acc = 0.0;
@@ -188,14 +195,15 @@ __global__ void __launch_bounds__(256) k_norm2_final(const double* partial, int 
 }
 void launch_norm2(const double2* w, size_t n, double* partial, double* sc, int slot, int nrhs, const KS& ks,
                   cudaStream_t st) {
-    k_norm2_partial<<<dim3(RED_CTAS, nrhs), 256, 0, st>>>(w, n, partial, ks);
-    k_norm2_final<<<nrhs, 256, 0, st>>>(partial, RED_CTAS, sc, slot, ks);
+    launch_pdl(k_norm2_partial, dim3(dim3(RED_CTAS, nrhs)), dim3(256), 0, st, w, n, partial, ks);
+    launch_pdl(k_norm2_final, dim3(nrhs), dim3(256), 0, st, partial, RED_CTAS, sc, slot, ks);
 }
 
 // x += sum_i y_i Z_i  (Z in the preconditioner's precision, x in FP64), k per right-hand side
 template <class Vz>
 __global__ void __launch_bounds__(256) k_update_x(const Vz* __restrict__ Z, const int* kk, const double2* __restrict__ y,
                                                   double2* __restrict__ x, size_t n, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.y;
     const int k = kk[r];
     if (k <= 0) return;
@@ -219,7 +227,7 @@ __global__ void __launch_bounds__(256) k_update_x(const Vz* __restrict__ Z, cons
 template <class Vz>
 void launch_update_x(const Vz* Z, const int* kk, const double2* y, double2* x, size_t n, int nrhs, const KS& ks,
                      cudaStream_t st) {
-    k_update_x<Vz><<<dim3(RED_CTAS * 2, nrhs), 256, 0, st>>>(Z, kk, y, x, n, ks);
+    launch_pdl(k_update_x<Vz>, dim3(dim3(RED_CTAS * 2, nrhs)), dim3(256), 0, st, Z, kk, y, x, n, ks);
 }
 template void launch_update_x<double2>(const double2*, const int*, const double2*, double2*, size_t, int, const KS&,
                                        cudaStream_t);
@@ -229,6 +237,7 @@ template void launch_update_x<float2>(const float2*, const int*, const double2*,
 // v = w / sc[slot]  (per right-hand side)
 __global__ void k_scale_copy(const double2* __restrict__ w, const double* sc, int slot, double2* __restrict__ v,
                              size_t n, size_t sw, size_t sv, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.y;
     if (inactive(ks, r)) return;
     w += r * sw;
@@ -241,7 +250,7 @@ __global__ void k_scale_copy(const double2* __restrict__ w, const double* sc, in
 }
 void launch_scale_copy(const double2* w, const double* sc, int slot, double2* v, size_t n, size_t sw, size_t sv,
                        int nrhs, const KS& ks, cudaStream_t st) {
-    k_scale_copy<<<dim3(RED_CTAS * 2, nrhs), 256, 0, st>>>(w, sc, slot, v, n, sw, sv, ks);
+    launch_pdl(k_scale_copy, dim3(dim3(RED_CTAS * 2, nrhs)), dim3(256), 0, st, w, sc, slot, v, n, sw, sv, ks);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,6 +261,7 @@ void launch_scale_copy(const double2* w, const double* sc, int slot, double2* v,
 // ---------------------------------------------------------------------------
 __global__ void k_arnoldi_givens(double2* Hm, int ldh, const double2* h1, const double2* h2, const double* sc, int j,
                                  double2* cs, double2* sn, double2* g, double* status, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.x;
     if (inactive(ks, r)) return;
     double2* Hcol = Hm + r * ks.sh + (size_t)j * ldh;
@@ -310,11 +320,12 @@ __global__ void k_arnoldi_givens(double2* Hm, int ldh, const double2* h1, const 
 void launch_arnoldi_givens(double2* Hm, int ldh, const double2* h1, const double2* h2, const double* sc, int j,
                            double2* cs, double2* sn, double2* g, double* status, int nrhs, const KS& ks,
                            cudaStream_t st) {
-    k_arnoldi_givens<<<nrhs, 32, 0, st>>>(Hm, ldh, h1, h2, sc, j, cs, sn, g, status, ks);
+    launch_pdl(k_arnoldi_givens, dim3(nrhs), dim3(32), 0, st, Hm, ldh, h1, h2, sc, j, cs, sn, g, status, ks);
 }
 
 // R y = g(0..k-1), R upper triangular stored column-major with leading dimension ldh
 __global__ void k_triangular_solve(const double2* Hm, int ldh, const double2* g, const int* kk, double2* y, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.x;
     const int k = kk[r];
     if (threadIdx.x != 0 || k <= 0) return;
@@ -329,11 +340,12 @@ __global__ void k_triangular_solve(const double2* Hm, int ldh, const double2* g,
 }
 void launch_triangular_solve(const double2* Hm, int ldh, const double2* g, const int* kk, double2* y, int nrhs,
                              const KS& ks, cudaStream_t st) {
-    k_triangular_solve<<<nrhs, 32, 0, st>>>(Hm, ldh, g, kk, y, ks);
+    launch_pdl(k_triangular_solve, dim3(nrhs), dim3(32), 0, st, Hm, ldh, g, kk, y, ks);
 }
 
 // g = beta e_1, status = (beta, 0, 0)
 __global__ void k_init_arnoldi(const double* sc, double2* g, int m, double* status, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.x;
     if (inactive(ks, r)) return;
     g += r * ks.so;
@@ -342,7 +354,7 @@ __global__ void k_init_arnoldi(const double* sc, double2* g, int m, double* stat
     if (threadIdx.x == 0) { status[r * 4 + 0] = beta; status[r * 4 + 1] = 0.0; status[r * 4 + 2] = 0.0; }
 }
 void launch_init_arnoldi(const double* sc, double2* g, int m, double* status, int nrhs, const KS& ks, cudaStream_t st) {
-    k_init_arnoldi<<<nrhs, 128, 0, st>>>(sc, g, m, status, ks);
+    launch_pdl(k_init_arnoldi, dim3(nrhs), dim3(128), 0, st, sc, g, m, status, ks);
 }
 
 }  // namespace bah

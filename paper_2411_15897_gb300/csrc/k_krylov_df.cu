@@ -36,6 +36,7 @@ __device__ __forceinline__ bool inactive_df(const KS& ks, int r) { return ks.act
 __global__ void __launch_bounds__(256) k_dot_norm_partial_df(const float4* __restrict__ V, int k,
                                                              const float4* __restrict__ w, size_t n,
                                                              double2* __restrict__ partial, const int* flag, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.z;
     if (inactive_df(ks, r) || (flag && flag[r] == 0)) return;
     V += r * ks.sv;
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(256) k_dot_norm_partial_df(const float4* __res
 }
 __global__ void __launch_bounds__(256) k_reduce_rows_df(const double2* __restrict__ partial, int np, double2* out,
                                                         const int* flag, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.z;
     if (inactive_df(ks, r)) return;
     partial += r * ks.sp;
@@ -86,14 +88,15 @@ __global__ void __launch_bounds__(256) k_reduce_rows_df(const double2* __restric
 }
 void launch_dot_norm_df(const float4* V, int k, const float4* w, size_t n, double2* partial, double2* out,
                         const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    k_dot_norm_partial_df<<<dim3(RED_CTAS, k + 1, nrhs), 256, 0, st>>>(V, k, w, n, partial, flag, ks);
-    k_reduce_rows_df<<<dim3(1, k + 1, nrhs), 256, 0, st>>>(partial, RED_CTAS, out, flag, ks);
+    launch_pdl(k_dot_norm_partial_df, dim3(dim3(RED_CTAS, k + 1, nrhs)), dim3(256), 0, st, V, k, w, n, partial, flag, ks);
+    launch_pdl(k_reduce_rows_df, dim3(dim3(1, k + 1, nrhs)), dim3(256), 0, st, partial, RED_CTAS, out, flag, ks);
 }
 
 // w -= sum_i coef[i] V_i (coef FP64, split once per CTA), per-CTA |w_new|^2
 __global__ void __launch_bounds__(256) k_axpy_norm_df(const float4* __restrict__ V, int k,
                                                       const double2* __restrict__ coef, float4* __restrict__ w,
                                                       size_t n, double* __restrict__ npart, const int* flag, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.z;
     if (inactive_df(ks, r) || (flag && flag[r] == 0)) return;
     V += r * ks.sv;
@@ -127,13 +130,14 @@ __global__ void __launch_bounds__(256) k_axpy_norm_df(const float4* __restrict__
 }
 void launch_axpy_norm_df(const float4* V, int k, const double2* coef, float4* w, size_t n, double* npart,
                          const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    k_axpy_norm_df<<<dim3(RED_CTAS, 1, nrhs), 256, 0, st>>>(V, k, coef, w, n, npart, flag, ks);
+    launch_pdl(k_axpy_norm_df, dim3(dim3(RED_CTAS, 1, nrhs)), dim3(256), 0, st, V, k, coef, w, n, npart, flag, ks);
 }
 
 // v = w / sc[slot]: from a double-float w, or (from64) from an FP64 vector
 template <bool FROM64>
 __global__ void k_scale_copy_df(const void* __restrict__ wsrc, const double* sc, int slot, float4* __restrict__ v,
                                 size_t n, size_t sw, size_t sv, KS ks) {
+    pdl_prologue();
     const int r = blockIdx.y;
     if (inactive_df(ks, r)) return;
     v += r * sv;
@@ -147,8 +151,8 @@ __global__ void k_scale_copy_df(const void* __restrict__ wsrc, const double* sc,
 }
 void launch_scale_copy_df(const void* w, bool from64, const double* sc, int slot, float4* v, size_t n, size_t sw,
                           size_t sv, int nrhs, const KS& ks, cudaStream_t st) {
-    if (from64) k_scale_copy_df<true><<<dim3(RED_CTAS * 2, nrhs), 256, 0, st>>>(w, sc, slot, v, n, sw, sv, ks);
-    else k_scale_copy_df<false><<<dim3(RED_CTAS * 2, nrhs), 256, 0, st>>>(w, sc, slot, v, n, sw, sv, ks);
+    if (from64) launch_pdl(k_scale_copy_df<true>, dim3(dim3(RED_CTAS * 2, nrhs)), dim3(256), 0, st, w, sc, slot, v, n, sw, sv, ks);
+    else launch_pdl(k_scale_copy_df<false>, dim3(dim3(RED_CTAS * 2, nrhs)), dim3(256), 0, st, w, sc, slot, v, n, sw, sv, ks);
 }
 
 }  // namespace bah

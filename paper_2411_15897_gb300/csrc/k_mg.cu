@@ -163,6 +163,7 @@ template <int MODE, bool L0, int RM>
 __global__ void __launch_bounds__(256) k_jacobi(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
                                                 Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC> f5,
                                                 typename MGT<MODE>::R w, int zero_init) {
+    pdl_prologue();
     using V = typename MGT<MODE>::V;
     const auto& B = s.blk[blockIdx.y];
     const int n1 = s.n1, n2 = s.n2, np = n1 * n2;
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(256) k_jacobi(LvlSet<typename MGT<MODE>::V, ty
 template <int MODE, bool L0, int RM>
 __global__ void __launch_bounds__(256) k_residual(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
                                                   Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC> f5) {
+    pdl_prologue();
     using V = typename MGT<MODE>::V;
     const auto& B = s.blk[blockIdx.y];
     const int n1 = s.n1, n2 = s.n2, np = n1 * n2;
@@ -354,9 +356,9 @@ void launch_jacobi(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>
     dim3 g((np + 255) / 256, s.nb, s.nrhs);
     using R = typename Prec<MODE>::R;
     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
-    if (f5) k_jacobi<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5, (R)w, zero_init);
-    else if (max_radius(s) <= 1) k_jacobi<MODE, false, 1><<<g, 256, 0, st>>>(s, nof, (R)w, zero_init);
-    else k_jacobi<MODE, false, 2><<<g, 256, 0, st>>>(s, nof, (R)w, zero_init);
+    if (f5) launch_pdl(k_jacobi<MODE, true, 1>, dim3(g), dim3(256), 0, st, s, *f5, (R)w, zero_init);
+    else if (max_radius(s) <= 1) launch_pdl(k_jacobi<MODE, false, 1>, dim3(g), dim3(256), 0, st, s, nof, (R)w, zero_init);
+    else launch_pdl(k_jacobi<MODE, false, 2>, dim3(g), dim3(256), 0, st, s, nof, (R)w, zero_init);
 }
 template <int MODE>
 void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
@@ -364,9 +366,9 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
     const int np = s.n1 * s.n2;
     dim3 g((np + 255) / 256, s.nb, s.nrhs);
     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
-    if (f5) k_residual<MODE, true, 1><<<g, 256, 0, st>>>(s, *f5);
-    else if (max_radius(s) <= 1) k_residual<MODE, false, 1><<<g, 256, 0, st>>>(s, nof);
-    else k_residual<MODE, false, 2><<<g, 256, 0, st>>>(s, nof);
+    if (f5) launch_pdl(k_residual<MODE, true, 1>, dim3(g), dim3(256), 0, st, s, *f5);
+    else if (max_radius(s) <= 1) launch_pdl(k_residual<MODE, false, 1>, dim3(g), dim3(256), 0, st, s, nof);
+    else launch_pdl(k_residual<MODE, false, 2>, dim3(g), dim3(256), 0, st, s, nof);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,6 +384,7 @@ __host__ __device__ __forceinline__ int rbase(bool nodal, int intergrid, int c) 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> fine,
                                                   PtrSet<typename MGT<MODE>::V> cb, int intergrid) {
+    pdl_prologue();
     using V = typename MGT<MODE>::V;
     using R = typename MGT<MODE>::R;
     const auto& B = fine.blk[blockIdx.y];
@@ -429,7 +432,7 @@ void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
     cb.s = coarse_stride;
     const int npc = (fine.n1 / 2) * (fine.n2 / 2);
     dim3 g((npc + 255) / 256, fine.nb, fine.nrhs);
-    k_restrict<MODE><<<g, 256, 0, st>>>(fine, cb, intergrid);
+    launch_pdl(k_restrict<MODE>, dim3(g), dim3(256), 0, st, fine, cb, intergrid);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,6 +441,7 @@ void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 template <int MODE>
 __global__ void __launch_bounds__(256) k_prolong_add(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> fine,
                                                      PtrSet<typename MGT<MODE>::V> ce) {
+    pdl_prologue();
     using V = typename MGT<MODE>::V;
     using R = typename MGT<MODE>::R;
     const auto& B = fine.blk[blockIdx.y];
@@ -484,7 +488,7 @@ void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>
     ce.s = coarse_stride;
     const int np = fine.n1 * fine.n2;
     dim3 g((np + 255) / 256, fine.nb, fine.nrhs);
-    k_prolong_add<MODE><<<g, 256, 0, st>>>(fine, ce);
+    launch_pdl(k_prolong_add<MODE>, dim3(g), dim3(256), 0, st, fine, ce);
 }
 
 // ---------------------------------------------------------------------------
@@ -496,6 +500,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const double2> inv,
                                                       PtrSet<const typename MGT<MODE>::V> b,
                                                       PtrSet<typename MGT<MODE>::V> x, const int* active) {
+    pdl_prologue();
     using V = typename MGT<MODE>::V;
     const int z = blockIdx.y;
     const int rr = blockIdx.z;
@@ -543,7 +548,7 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
     px.s = rs.s1;
     dim3 g((npts * 32 + 255) / 256, nb, nrhs);
     const size_t smem = npts <= kCoarseSmem ? (size_t)npts * sizeof(double2) : 0;
-    k_coarse_apply<MODE><<<g, 256, smem, st>>>(npts, pi, pb, px, rs.active);
+    launch_pdl(k_coarse_apply<MODE>, dim3(g), dim3(256), smem, st, npts, pi, pb, px, rs.active);
 }
 
 #define INST(MODE)                                                                                                 \

@@ -37,6 +37,7 @@ __device__ __forceinline__ void st_out(float4* y, size_t i, double2 v) { y[i] = 
 template <class Vin, class Vout>
 __global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __restrict__ x, Vout* __restrict__ y,
                                                        const double2* __restrict__ b, int conj, RhsStride rs) {
+    pdl_prologue();
     const int n1 = c.n1, n2 = c.n2, np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int rr = blockIdx.y;
@@ -106,12 +107,12 @@ template <class Vin>
 void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st,
                           int nrhs, RhsStride rs) {
     int np = c.n1 * c.n2;
-    k_elastic_apply<Vin, double2><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(c, x, y, b, conj, rs);
+    launch_pdl(k_elastic_apply<Vin, double2>, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, c, x, y, b, conj, rs);
 }
 template <class Vin>
 void launch_elastic_apply_df(const OpCoef& c, const Vin* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs) {
     int np = c.n1 * c.n2;
-    k_elastic_apply<Vin, float4><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(c, x, y, nullptr, 0, rs);
+    launch_pdl(k_elastic_apply<Vin, float4>, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, c, x, y, nullptr, 0, rs);
 }
 template void launch_elastic_apply_df<double2>(const OpCoef&, const double2*, float4*, cudaStream_t, int, RhsStride);
 template void launch_elastic_apply_df<float2>(const OpCoef&, const float2*, float4*, cudaStream_t, int, RhsStride);
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(256) k_distributor(int n1, int n2, typename Pr
                                                      Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> f,
                                                      const RIN* __restrict__ r, typename Prec<MODE>::V* __restrict__ tp,
                                                      RhsStride rs) {
+    pdl_prologue();
     using V = typename Prec<MODE>::V;
     using R = typename Prec<MODE>::R;
     const int np = n1 * n2;
@@ -161,7 +163,7 @@ void launch_distributor(int n1, int n2, double ihx, double ihz,
                         const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>& f5, const RIN* r,
                         typename Prec<MODE>::V* tp, cudaStream_t st, int nrhs, RhsStride rs) {
     int np = n1 * n2;
-    k_distributor<MODE, RIN><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
+    launch_pdl(k_distributor<MODE, RIN>, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, n1, n2, (typename Prec<MODE>::R)ihx,
                                                                        (typename Prec<MODE>::R)ihz, f5, r, tp, rs);
 }
 template void launch_distributor<BAH_FP64, double2>(int, int, double, double, const Fine5<double, double2>&,
@@ -182,6 +184,7 @@ template <int MODE, class RIN>
 __global__ void __launch_bounds__(256) k_u_rhs(int n1, int n2, typename Prec<MODE>::R ihx, typename Prec<MODE>::R ihz,
                                                const RIN* __restrict__ r, const typename Prec<MODE>::V* __restrict__ ep,
                                                typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, RhsStride rs) {
+    pdl_prologue();
     using V = typename Prec<MODE>::V;
     using R = typename Prec<MODE>::R;
     const int np = n1 * n2;
@@ -213,7 +216,7 @@ template <int MODE, class RIN>
 void launch_u_rhs(int n1, int n2, double ihx, double ihz, const RIN* r, const typename Prec<MODE>::V* ep,
                   typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st, int nrhs, RhsStride rs) {
     int np = n1 * n2;
-    k_u_rhs<MODE, RIN><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(n1, n2, (typename Prec<MODE>::R)ihx,
+    launch_pdl(k_u_rhs<MODE, RIN>, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, n1, n2, (typename Prec<MODE>::R)ihx,
                                                                  (typename Prec<MODE>::R)ihz, r, ep, su1, su2, rs);
 }
 template void launch_u_rhs<BAH_FP64, double2>(int, int, double, double, const double2*, const double2*, double2*,
