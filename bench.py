@@ -41,15 +41,25 @@ import workloads as W  # noqa: E402
 
 METRIC = "elastic solves/s to rel-res 1e-6 (mixed vs FP64); stencil+V-cycle HBM GB/s"
 UNIT = "solves/s"
-WORKLOAD = ("2D 512x512 layered medium (6 layers, Vp U[1.5,4.5], nu U[0.25,0.45], rho=0.31 Vp^0.25), "
-            "10 points per shear wavelength, 20-cell absorbing layer, one top-centre point source, "
-            "FGMRES(20) to rel-res 1e-6")
+WORKLOADS = {
+    "c1": "2D 64x64 homogeneous medium (rho=1, Vp=2, nu=0.25), 10 points per shear wavelength, 8-cell absorbing "
+          "layer, centre point source, FGMRES(20) to rel-res 1e-6",
+    "c2": "2D 512x512 layered medium (6 layers, Vp U[1.5,4.5], nu U[0.25,0.45], rho=0.31 Vp^0.25), "
+          "10 points per shear wavelength, 20-cell absorbing layer, one top-centre point source, "
+          "FGMRES(20) to rel-res 1e-6",
+    "c3": "2D 1024x1024 smooth random medium (log Vp Gaussian random field, correlation 32 cells, std 0.2, mean "
+          "log 3; nu in [0.3,0.49]), 10 points per shear wavelength, 20-cell absorbing layer, top-centre source, "
+          "FGMRES(20) to rel-res 1e-6",
+    "c4": "2D 1024x512 layered medium (6 layers, seed 5), 64 point sources along row 20 solved as one batch, "
+          "FGMRES(20) to rel-res 1e-6 per source",
+}
+WORKLOAD = WORKLOADS["c2"]
 L2_FLUSH_BYTES = 512 << 20
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA/clk/SM at the 2070 MHz maximum clock (1.26 TFLOP/s)
 KERNEL_NAMES = {0: "k_elastic_apply", 1: "k_distributor", 2: "k_u_rhs", 3: "k_jacobi", 4: "k_residual",
                 5: "k_restrict", 6: "k_prolong_add", 7: "k_coarse_apply", 8: "k_dot_norm_partial",
                 9: "k_axpy_norm", 10: "k_norm2_partial", 11: "k_update_x", 12: "small kernels",
-                13: "k_coop_cycle"}
+                13: "k_coop_cycle", 14: "k_cluster_cycle"}
 # FP64 flops per algorithmic byte of the FP64 classes (2 flops per real FMA):
 #   dot/axpy: 8 flops per complex MAC on 16 streamed bytes; operator: ~84 flops per cell on ~200 bytes
 FP64_FLOP_PER_BYTE = {"dot": 0.5, "axpy": 0.5, "update": 8.0 / 8.0, "operator": 84.0 / 200.0}
@@ -71,6 +81,9 @@ def parse():
     ap.add_argument("--max-coarse", type=int, default=1024)
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--krylov", default="df", choices=["fp64", "df"])
+    ap.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per batch (default: all sources)")
+    ap.add_argument("--gradient", action="store_true", help="also time the adjoint gradient of a receiver misfit")
+    ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--krylov-fp64-steps", type=int, default=2,
                     help="also time the same solve with the Krylov basis in IEEE FP64")
     return ap.parse_args()
@@ -210,22 +223,32 @@ def run_bah(args):
     import paper_2411_15897_gb300 as bah
 
     prob = W.config(args.config)
+    nsrc = len(prob.sources)
+    rhs_block = args.rhs_block if args.rhs_block > 0 else nsrc
     opts = dict(precision=bah.BAH_MIXED, levels=args.levels, max_coarse_cells=args.max_coarse, restart=args.restart,
-                krylov_arith=bah.BAH_KRYLOV_DF if args.krylov == "df" else bah.BAH_KRYLOV_FP64)
+                krylov_arith=bah.BAH_KRYLOV_DF if args.krylov == "df" else bah.BAH_KRYLOV_FP64,
+                rhs_block=rhs_block, maxit=args.maxit)
     solver = bah.Solver.from_problem(prob, **opts)
     levels = solver.levels
-    b_host = W.point_source(prob)
+    b_host = W.all_sources(prob) if nsrc > 1 else W.point_source(prob)
     b = torch.from_numpy(b_host).cuda()
+    if nsrc > 1 and args.fp64_steps > 0:
+        args.fp64_steps = 0          # the all-FP64 comparison is run on the single-source workloads
     x = torch.zeros_like(b)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def solve_once(s, bb, xx):
-        st, stats = bah.bah_solve(s.ctx, bb, xx, 1, 1e-6)
-        return st, stats[0]
+        nr = bb.shape[0] if bb.ndim == 4 else 1
+        st, stats = bah.bah_solve(s.ctx, bb, xx, nr, 1e-6)
+        if nr == 1:
+            return st, stats[0]
+        agg = {"iters": max(q["iters"] for q in stats), "iters_mean": statistics.mean(q["iters"] for q in stats),
+               "relres_true": max(q["relres_true"] for q in stats)}
+        return st, agg
 
     # warm-up, with every kernel class timed once to find the dominant one
-    bah.bah_profile_control(solver.ctx, (1 << 14) - 1, True)
+    bah.bah_profile_control(solver.ctx, (1 << 15) - 1, True)
     st0, stats0 = solve_once(solver, b, x)
     prof_all = bah.bah_profile_read(solver.ctx)
     for _ in range(max(0, args.warmup - 1)):
@@ -262,7 +285,7 @@ def run_bah(args):
         t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
-    value = world * args.steps / total_s
+    value = world * args.steps * nsrc / total_s
 
     # the dominant kernel class, timed launch by launch with CUDA events recorded
     # on the launching stream, over the same number of solves right after the
@@ -298,7 +321,7 @@ def run_bah(args):
             e1.synchronize()
             ms64.append(e0.elapsed_time(e1))
             it64.append(stt["iters"])
-        fp64 = {"value": world * args.fp64_steps / (sum(ms64) / 1e3), "unit": UNIT, "iters": it64[-1],
+        fp64 = {"value": world * args.fp64_steps * nsrc / (sum(ms64) / 1e3), "unit": UNIT, "iters": it64[-1],
                 "ms_per_step": statistics.mean(ms64), "relres_true": stt["relres_true"]}
         s64.close()
 
@@ -318,25 +341,60 @@ def run_bah(args):
             e1.record(stream)
             e1.synchronize()
             msk.append(e0.elapsed_time(e1))
-        kfp64 = {"value": world * args.krylov_fp64_steps / (sum(msk) / 1e3), "unit": UNIT, "iters": sttk["iters"],
+        kfp64 = {"value": world * args.krylov_fp64_steps * nsrc / (sum(msk) / 1e3), "unit": UNIT, "iters": sttk["iters"],
                  "ms_per_step": statistics.mean(msk), "relres_true": sttk["relres_true"]}
         sk.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    bp = torch.from_numpy(b_host.copy()).pin_memory()
-    xp = torch.zeros_like(bp).pin_memory()
-    bnp, xnp = bp.numpy(), xp.numpy()
-    solve_once(solver, bnp, xnp)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e = None
+    if args.e2e_steps > 0:
+        bp = torch.from_numpy(b_host.copy()).pin_memory()
+        xp = torch.zeros_like(bp).pin_memory()
+        bnp, xnp = bp.numpy(), xp.numpy()
         solve_once(solver, bnp, xnp)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    barrier()
-    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(b_host.nbytes),
-           "d2h_bytes_per_step": int(b_host.nbytes)}
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            solve_once(solver, bnp, xnp)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * args.e2e_steps * nsrc / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes),
+               "timing": "host wall clock around the C-ABI call with pinned host buffers (copies inside)"}
+
+    # adjoint gradient of a receiver misfit (forward solve, adjoint solve, gradient kernel)
+    grad = None
+    if args.gradient:
+        from paper_2411_15897_gb300 import misfit as MF
+        rec = torch.from_numpy(MF.receiver_indices(prob.n, prob.sources[0][1])).cuda()
+        # observed data: the true medium's wavefield at the receivers; the misfit is
+        # evaluated at a smoothed medium (Gaussian filter of 8 cells)
+        st_true = bah.Solver.from_problem(prob, **opts)
+        xt = torch.zeros_like(b)
+        bah.bah_solve(st_true.ctx, b, xt, nsrc, 1e-6)
+        dobs = xt.reshape(nsrc, -1)[:, rec.long()].contiguous()
+        st_true.close()
+        from scipy.ndimage import gaussian_filter
+        sm = lambda a: torch.tensor(gaussian_filter(a, 8.0, mode="nearest"), dtype=torch.float64, requires_grad=True)
+        lam_t, mu_t, rho_t = sm(prob.lam), sm(prob.mu), sm(prob.rho)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = MF.misfit(lam_t, mu_t, rho_t, prob.gamma, prob.omega, prob.n, prob.h, b, dobs, rec, opts, 1e-6)
+        t1 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        grad = {"misfit": float(J.item()), "forward_s": t1 - t0, "backward_s": t2 - t1,
+                "grad_norms": [float(lam_t.grad.norm()), float(mu_t.grad.norm()), float(rho_t.grad.norm())],
+                "sources": nsrc, "receivers": int(rec.numel()),
+                "note": "forward includes context setup for the smoothed medium and the batched solve; backward "
+                        "the batched adjoint solve and the gradient kernel"}
 
     # roofline of the dominant kernel class
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -382,7 +440,8 @@ def run_bah(args):
         "dtype": ("mixed: bf16 coefficients, f32 multigrid, f64 operator / Hessenberg / true residual / coarsest "
                   "solve, " + ("double-f32 (48-bit) Gram-Schmidt" if args.krylov == "df" else "f64 Gram-Schmidt")),
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(prob.n), "unknowns": int(sum(W.compact_sizes(prob.n))),
+        "config": {"workload": WORKLOADS.get(args.config, args.config), "grid": list(prob.n),
+                   "unknowns": int(sum(W.compact_sizes(prob.n))), "sources": nsrc, "rhs_block": rhs_block,
                    "levels": levels, "cycle": "V(1,2)", "restart": args.restart, "iters": iters[-1],
                    "relres_true": relres, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"independent solves per GPU x{world}"},
@@ -395,6 +454,7 @@ def run_bah(args):
         "roofline": roof,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "gradient": grad,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

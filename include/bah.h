@@ -228,7 +228,8 @@ int bah_level_stencil(const bah_ctx* ctx, int block, int level, double* out, int
 #define BAH_K_UPDATE   11   /* x += Z y */
 #define BAH_K_SMALL    12   /* Givens update, triangular solve, scaling, copies, conversions */
 #define BAH_K_COOP     13   /* cooperative launch running all levels below the fine grid */
-#define BAH_NKCLASS    14
+#define BAH_K_CLUSTER  14   /* thread-block-cluster launch running the small levels of a V-cycle */
+#define BAH_NKCLASS    15
 
 typedef struct {
     long long launches;             /* kernels launched since the last reset */

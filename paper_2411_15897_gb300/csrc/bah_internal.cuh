@@ -148,12 +148,29 @@ struct CoopLevel {
 struct CoopArgs {
     const CoopLevel* lv;      // device array indexed by level
     int l0, L, b0, nb, nu_pre, nu_post, intergrid;
-    const double2* inv[3];    // coarsest FP64 inverses
+    const void* inv[3];       // coarsest inverses in the cycle's vector type (FP64 or FP32 complex)
     double2* bc64[3];         // coarsest right-hand side in FP64
     unsigned* bar_count;
     unsigned* bar_gen;
     int* err;
 };
+
+// cluster cycle: levels l0..L-1 of one block set, one cluster per block and
+// right-hand side (per-level buffers hold consecutive right-hand sides at a
+// stride of the level's point count)
+constexpr int kMaxLevels = 16;
+struct ClusterArgs {
+    const CoopLevel* lv;      // device array indexed by level
+    int l0, L, b0, nb, nu_pre, nu_post, intergrid;
+    int wcycle;               // 0: V-cycle, 1: W-cycle
+    int warm;                 // 1: start level l0 from the values in its x buffer
+    const void* inv[3];       // coarsest inverses in the cycle's vector type
+    const int* active;        // per-right-hand-side flags, or null
+};
+template <int MODE>
+int cluster_size_for(int max_radius, int want, int coarse_pts);
+template <int MODE>
+int launch_cluster_cycle(const ClusterArgs& a, int max_radius, int nrhs, int csize, int coarse_pts, cudaStream_t st);
 
 // right-hand-side batching: element strides between consecutive right-hand
 // sides for up to three pointers of a launch (blockIdx.y or .z is the
@@ -220,7 +237,7 @@ void launch_prolong_smooth(const LvlSet<typename Prec<MODE>::V, typename Prec<MO
 template <int MODE>
 int launch_coop_cycle(const CoopArgs& a, int max_radius, int nsm, cudaStream_t st);
 template <int MODE>
-void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
+void launch_coarse_apply(int nb, int npts, const typename Prec<MODE>::V* const* inv, const typename Prec<MODE>::V* const* b,
                          typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs = 1, RhsStride rs = RhsStride());
 template <int MODE, class RIN = double2>
 void launch_distributor(int n1, int n2, double ihx, double ihz,

@@ -492,37 +492,39 @@ void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>
 }
 
 // ---------------------------------------------------------------------------
-// coarsest level: x = A_c^{-1} b with the stored FP64 inverse (one warp per row)
+// coarsest level: x = A_c^{-1} b with the stored inverse (one warp per row).
+// The inverse is computed in FP64 at setup and stored in the cycle's vector
+// type: FP64 in the FP64 mode, rounded once to FP32 in the mixed mode, where
+// the product is accumulated in FP32 like the rest of the cycle.
 // ---------------------------------------------------------------------------
 constexpr int kCoarseSmem = 3072;   // points staged in shared memory (48 KB of FP64 complex)
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const double2> inv,
+__global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const typename MGT<MODE>::V> inv,
                                                       PtrSet<const typename MGT<MODE>::V> b,
                                                       PtrSet<typename MGT<MODE>::V> x, const int* active) {
     pdl_prologue();
     using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
     const int z = blockIdx.y;
     const int rr = blockIdx.z;
     if (active && !active[rr]) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    extern __shared__ double2 bsh[];
+    extern __shared__ __align__(16) unsigned char coarse_raw[];
+    V* bsh = reinterpret_cast<V*>(coarse_raw);
     const V* bb = b.p[z] + rr * b.s;
     const bool staged = npts <= kCoarseSmem;
     if (staged) {
-        // the right-hand side in FP64, converted once per CTA
-        for (int c = threadIdx.x; c < npts; c += blockDim.x) bsh[c] = make_double2((double)bb[c].x, (double)bb[c].y);
+        for (int c = threadIdx.x; c < npts; c += blockDim.x) bsh[c] = bb[c];
         __syncthreads();
     }
     if (warp >= npts) return;
-    const double2* row = inv.p[z] + (size_t)warp * npts;
-    double re = 0.0, im = 0.0;
+    const V* row = inv.p[z] + (size_t)warp * npts;
+    R re = 0, im = 0;
     for (int c = lane; c < npts; c += 32) {
-        const double2 a = row[c];
-        double2 v;
-        if (staged) v = bsh[c];
-        else v = make_double2((double)bb[c].x, (double)bb[c].y);
+        const V a = row[c];
+        const V v = staged ? bsh[c] : bb[c];
         re += a.x * v.x - a.y * v.y;
         im += a.x * v.y + a.y * v.x;
     }
@@ -530,13 +532,14 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const dou
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) x.p[z][rr * x.s + warp] = cmk<V>((typename MGT<MODE>::R)re, (typename MGT<MODE>::R)im);
+    if (lane == 0) x.p[z][rr * x.s + warp] = cmk<V>(re, im);
 }
 
 template <int MODE>
-void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
-                         typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs, RhsStride rs) {
-    PtrSet<const double2> pi;
+void launch_coarse_apply(int nb, int npts, const typename Prec<MODE>::V* const* inv,
+                         const typename Prec<MODE>::V* const* b, typename Prec<MODE>::V* const* x, cudaStream_t st,
+                         int nrhs, RhsStride rs) {
+    PtrSet<const typename Prec<MODE>::V> pi;
     PtrSet<const typename Prec<MODE>::V> pb;
     PtrSet<typename Prec<MODE>::V> px;
     for (int z = 0; z < 3; ++z) {
@@ -547,7 +550,7 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
     pb.s = rs.s0;
     px.s = rs.s1;
     dim3 g((npts * 32 + 255) / 256, nb, nrhs);
-    const size_t smem = npts <= kCoarseSmem ? (size_t)npts * sizeof(double2) : 0;
+    const size_t smem = npts <= kCoarseSmem ? (size_t)npts * sizeof(typename Prec<MODE>::V) : 0;
     launch_pdl(k_coarse_apply<MODE>, dim3(g), dim3(256), smem, st, npts, pi, pb, px, rs.active);
 }
 
@@ -560,7 +563,7 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
                                         cudaStream_t, size_t);                                                     \
     template void launch_prolong_add<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                           \
                                            const Prec<MODE>::V* const*, cudaStream_t, size_t);                     \
-    template void launch_coarse_apply<MODE>(int, int, const double2* const*, const Prec<MODE>::V* const*,         \
+    template void launch_coarse_apply<MODE>(int, int, const Prec<MODE>::V* const*, const Prec<MODE>::V* const*,   \
                                             Prec<MODE>::V* const*, cudaStream_t, int, RhsStride);                 \
     template void launch_smooth_restrict<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                       \
                                                const Fine5<Prec<MODE>::C, Prec<MODE>::CC>*, double,                \
@@ -722,20 +725,21 @@ __global__ void __launch_bounds__(256) k_coop_cycle(CoopArgs a) {
             x[z][t] = cadd(x[z][t], acc);
         }
     };
-    auto coarse = [&]() {                            // x_{L-1} = A_c^{-1} b_{L-1} (FP64), one warp per row
+    auto coarse = [&]() {                            // x_{L-1} = A_c^{-1} b_{L-1} (FP64 sums), one warp per row
         const CoopLevel& L = lvl(a.L - 1);
         const int npts = L.n1 * L.n2;
         const long long warp = gtid >> 5, nwarps = gsz >> 5;
         const int lane = threadIdx.x & 31;
         for (long long row = warp; row < (long long)nb * npts; row += nwarps) {
             const int z = (int)(row / npts), rr = (int)(row % npts);
-            const double2* arow = a.inv[z] + (size_t)rr * npts;
+            const V* arow = (const V*)a.inv[z] + (size_t)rr * npts;
             const double2* bb = a.bc64[z];
             double re = 0.0, im = 0.0;
             for (int c = lane; c < npts; c += 32) {
-                const double2 m = arow[c], v = bb[c];
-                re += m.x * v.x - m.y * v.y;
-                im += m.x * v.y + m.y * v.x;
+                const V m = arow[c];
+                const double2 v = bb[c];
+                re += (double)m.x * v.x - (double)m.y * v.y;
+                im += (double)m.x * v.y + (double)m.y * v.x;
             }
             for (int o = 16; o > 0; o >>= 1) {
                 re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -827,5 +831,321 @@ int launch_coop_cycle(const CoopArgs& a, int max_radius, int nsm, cudaStream_t s
 }
 template int launch_coop_cycle<BAH_FP64>(const CoopArgs&, int, int, cudaStream_t);
 template int launch_coop_cycle<BAH_MIXED>(const CoopArgs&, int, int, cudaStream_t);
+
+// ===========================================================================
+// Cluster multigrid: the levels l0..L-1 of a V-cycle for one block and one
+// right-hand side in one thread-block cluster.  The small levels of the
+// hierarchy (a few thousand points) cannot fill the GPU, so separate launches
+// cost their launch latency and tail many times per cycle.  Here the cluster
+// walks the same phases as the separate kernels -- zero-guess Jacobi, Jacobi,
+// residual, restriction, the coarsest solve, prolongation and correction --
+// each phase spread over the cluster's threads, with the hardware cluster
+// barrier (release/acquire at cluster scope, which orders the global-memory
+// writes of one phase before the reads of the next) between phases.  All
+// CTAs of a cluster are co-scheduled by the hardware, every thread of every
+// CTA reaches every barrier (no early exit except a whole cluster at once),
+// so the barrier always completes.  Clusters are independent: the grid is
+// (cluster size) x (blocks) x (right-hand sides) CTAs.
+// ===========================================================================
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_nrank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+template <int MODE, int RM>
+__global__ void __launch_bounds__(256) k_cluster_cycle(ClusterArgs a) {
+    pdl_prologue();
+    using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
+    using CC = typename MGT<MODE>::CC;
+    const unsigned cid = cluster_index();
+    const int z = (int)(cid % (unsigned)a.nb), rr = (int)(cid / (unsigned)a.nb);
+    if (a.active && !a.active[rr]) return;          // uniform over the cluster
+    const int tid = (int)(cluster_rank() * blockDim.x + threadIdx.x);
+    const int nth = (int)(cluster_nrank() * blockDim.x);
+    const int type = a.b0 + z;
+    const bool nodx = type == 0, nodz = type == 1;
+    extern __shared__ __align__(16) unsigned char cluster_raw[];
+    V* bsh = reinterpret_cast<V*>(cluster_raw);     // coarsest right-hand side, staged per CTA
+
+    struct Lv { int n1, n2, rx, rz; R w; const CC* S; V* b; V* x; V* t; };
+    auto level = [&](int l) {
+        const CoopLevel& q = a.lv[l];
+        const size_t off = (size_t)rr * q.n1 * q.n2;
+        Lv v;
+        v.n1 = q.n1; v.n2 = q.n2; v.rx = q.rx[z]; v.rz = q.rz[z]; v.w = (R)q.w;
+        v.S = (const CC*)q.S[z];
+        v.b = (V*)q.b[z] + off; v.x = (V*)q.x[z] + off; v.t = (V*)q.t[z] + off;
+        return v;
+    };
+    auto diag = [&](const Lv& L, int t) -> V {
+        return ldc(L.S[(size_t)(L.rz * (2 * L.rx + 1) + L.rx) * L.n1 * L.n2 + t]);
+    };
+    auto jacobi = [&](const Lv& L, const V* xin, V* xout, bool zero) {
+        const int np = L.n1 * L.n2;
+        for (int t = tid; t < np; t += nth) {
+            const int i = t % L.n1, j = t / L.n1;
+            if (!valid_pt(type, i, j)) { xout[t] = czero<V>(); continue; }
+            const V dg = diag(L, t);
+            const V b = L.b[t];
+            if (zero) { xout[t] = cscale(cdiv(b, dg), L.w); continue; }
+            auto X = [&](int g) { return xin[g]; };
+            const V ax = apply_stencil_fn<MODE, RM>(L.S, L.rx, L.rz, L.n1, L.n2, i, j, t, X);
+            const V corr = cdiv(csub(b, ax), dg);
+            const V xv = xin[t];
+            xout[t] = cmk<V>(xv.x + L.w * corr.x, xv.y + L.w * corr.y);
+        }
+    };
+    auto residual = [&](const Lv& L, const V* x, V* r) {
+        const int np = L.n1 * L.n2;
+        for (int t = tid; t < np; t += nth) {
+            const int i = t % L.n1, j = t / L.n1;
+            if (!valid_pt(type, i, j)) { r[t] = czero<V>(); continue; }
+            auto X = [&](int g) { return x[g]; };
+            r[t] = csub(L.b[t], apply_stencil_fn<MODE, RM>(L.S, L.rx, L.rz, L.n1, L.n2, i, j, t, X));
+        }
+    };
+    auto restrict_ = [&](const Lv& L, const V* r, V* bc) {     // b_c = R r
+        const int n1c = L.n1 / 2, npc = n1c * (L.n2 / 2);
+        for (int t = tid; t < npc; t += nth) {
+            const int I = t % n1c, J = t / n1c;
+            V acc = czero<V>();
+            if (valid_pt(type, I, J)) {
+                const int bx = rbase(nodx, a.intergrid, I), bz = rbase(nodz, a.intergrid, J);
+                R wxs[4], wzs[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    wxs[q] = rw_axis_t<R>(nodx, a.intergrid, L.n1, I, bx + q);
+                    wzs[q] = rw_axis_t<R>(nodz, a.intergrid, L.n2, J, bz + q);
+                }
+                V v[16];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool ok = wzs[e] != R(0) && wxs[q] != R(0);
+                        v[e * 4 + q] = r[ok ? (bz + e) * L.n1 + (bx + q) : 0];
+                    }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const R wgt = wzs[e] * wxs[q];
+                        acc.x += wgt * v[e * 4 + q].x;
+                        acc.y += wgt * v[e * 4 + q].y;
+                    }
+            }
+            bc[t] = acc;
+        }
+    };
+    auto prolong = [&](const Lv& L, V* x, const V* e) {         // x += P e
+        const int np = L.n1 * L.n2, n1c = L.n1 / 2;
+        for (int t = tid; t < np; t += nth) {
+            const int i = t % L.n1, j = t / L.n1;
+            if (!valid_pt(type, i, j)) continue;
+            R px[3], pz[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                px[q] = pw_axis_t<R>(nodx, L.n1, i, (i >> 1) - 1 + q);
+                pz[q] = pw_axis_t<R>(nodz, L.n2, j, (j >> 1) - 1 + q);
+            }
+            V v[9];
+#pragma unroll
+            for (int e2 = 0; e2 < 3; ++e2)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const bool ok = pz[e2] != R(0) && px[q] != R(0);
+                    v[e2 * 3 + q] = e[ok ? ((j >> 1) - 1 + e2) * n1c + ((i >> 1) - 1 + q) : 0];
+                }
+            V acc = x[t];
+#pragma unroll
+            for (int e2 = 0; e2 < 3; ++e2)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const R wgt = pz[e2] * px[q];
+                    acc.x += wgt * v[e2 * 3 + q].x;
+                    acc.y += wgt * v[e2 * 3 + q].y;
+                }
+            x[t] = acc;
+        }
+    };
+    auto coarse = [&](const Lv& L) {                             // x = A_c^{-1} b, one warp per row
+        const int npts = L.n1 * L.n2;
+        const bool staged = npts <= kCoarseSmem;
+        if (staged) {
+            for (int c = threadIdx.x; c < npts; c += blockDim.x) bsh[c] = L.b[c];
+            __syncthreads();
+        }
+        const V* inv = (const V*)a.inv[z];
+        const int lane = threadIdx.x & 31;
+        for (int row = tid >> 5; row < npts; row += nth >> 5) {
+            const V* arow = inv + (size_t)row * npts;
+            R re = 0, im = 0;
+            for (int c = lane; c < npts; c += 32) {
+                const V m = arow[c];
+                const V v = staged ? bsh[c] : L.b[c];
+                re += m.x * v.x - m.y * v.y;
+                im += m.x * v.y + m.y * v.x;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (lane == 0) L.x[row] = cmk<V>(re, im);
+        }
+    };
+
+    // The cycle from level l0 down and back up, as an explicit walk over the
+    // recursion: one visit of the coarse problem for a V-cycle; two for a
+    // W-cycle (the second starting from the first one's result), except where
+    // the coarse level is the coarsest, solved exactly once.  Every visit
+    // leaves its result in the level's x buffer.
+    V* xs[kMaxLevels];
+    V* ts[kMaxLevels];
+    int stage[kMaxLevels];
+    bool warm[kMaxLevels];
+    int l = a.l0;
+    stage[l] = 0;
+    warm[l] = a.warm != 0;
+    while (true) {
+        if (l == a.L - 1) {
+            coarse(level(l));
+            cluster_barrier();
+            --l;
+            continue;
+        }
+        const Lv L = level(l);
+        if (stage[l] == 0) {
+            // pre-smoothing (from zero, or from the x buffer on a warm visit), residual, restriction
+            V* x = L.x;
+            V* t = L.t;
+            int s0 = 0;
+            if (!warm[l]) {
+                if (a.nu_pre >= 1) {
+                    jacobi(L, nullptr, x, true);
+                    s0 = 1;
+                } else {
+                    for (int g = tid; g < L.n1 * L.n2; g += nth) x[g] = czero<V>();
+                }
+                cluster_barrier();
+            }
+            for (int s = s0; s < a.nu_pre; ++s) {
+                jacobi(L, x, t, false);
+                cluster_barrier();
+                V* q = x; x = t; t = q;
+            }
+            residual(L, x, t);
+            cluster_barrier();
+            restrict_(L, t, level(l + 1).b);
+            cluster_barrier();
+            xs[l] = x;
+            ts[l] = t;
+            stage[l] = 1;
+            ++l;
+            stage[l] = 0;
+            warm[l] = false;
+            continue;
+        }
+        if (stage[l] == 1 && a.wcycle && l + 1 < a.L - 1) {
+            stage[l] = 2;
+            ++l;
+            stage[l] = 0;
+            warm[l] = true;
+            continue;
+        }
+        // prolongation and correction, post-smoothing
+        V* x = xs[l];
+        V* t = ts[l];
+        prolong(L, x, level(l + 1).x);
+        cluster_barrier();
+        for (int s = 0; s < a.nu_post; ++s) {
+            jacobi(L, x, t, false);
+            cluster_barrier();
+            V* q = x; x = t; t = q;
+        }
+        if (x != L.x) {
+            for (int g = tid; g < L.n1 * L.n2; g += nth) L.x[g] = x[g];
+            cluster_barrier();
+        }
+        if (l == a.l0) break;
+        --l;
+    }
+}
+
+template <int MODE>
+static const void* cluster_fn(int max_radius) {
+    return max_radius <= 1 ? (const void*)k_cluster_cycle<MODE, 1> : (const void*)k_cluster_cycle<MODE, 2>;
+}
+
+template <int MODE>
+int cluster_size_for(int max_radius, int want, int coarse_pts) {
+    const void* fn = cluster_fn<MODE>(max_radius);
+    if (want > 8) {
+        // both radius variants: a block set may launch either
+        for (int r = 1; r <= 2; ++r)
+            if (cudaFuncSetAttribute(cluster_fn<MODE>(r), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                want = 8;
+            }
+    }
+    const size_t smem = coarse_pts <= kCoarseSmem ? (size_t)coarse_pts * sizeof(typename Prec<MODE>::V) : 0;
+    for (int cs = want; cs >= 2; cs /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) return cs;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+template <int MODE>
+int launch_cluster_cycle(const ClusterArgs& a, int max_radius, int nrhs, int csize, int coarse_pts, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize * a.nb * nrhs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = coarse_pts <= kCoarseSmem ? (size_t)coarse_pts * sizeof(typename Prec<MODE>::V) : 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    cudaError_t e = max_radius <= 1 ? cudaLaunchKernelEx(&cfg, k_cluster_cycle<MODE, 1>, a)
+                                    : cudaLaunchKernelEx(&cfg, k_cluster_cycle<MODE, 2>, a);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+template int cluster_size_for<BAH_FP64>(int, int, int);
+template int cluster_size_for<BAH_MIXED>(int, int, int);
+template int launch_cluster_cycle<BAH_FP64>(const ClusterArgs&, int, int, int, int, cudaStream_t);
+template int launch_cluster_cycle<BAH_MIXED>(const ClusterArgs&, int, int, int, int, cudaStream_t);
 
 }  // namespace bah

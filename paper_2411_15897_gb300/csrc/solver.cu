@@ -53,6 +53,7 @@ struct Ctx {
     std::vector<std::array<StencilF64, 3>> s64;   // FP64 stencils per level (level 0: 3x3 fine operator)
     std::vector<std::array<void*, 3>> sst;        // storage-precision stencils, levels >= 1
     double2* inv[3] = {nullptr, nullptr, nullptr};
+    void* invs[3] = {nullptr, nullptr, nullptr};  // inverse in the multigrid's storage type (FP32 copy when mixed)
     std::vector<std::array<void*, 3>> vX, vB, vT; // multigrid vectors per level and block
     // Krylov workspace
     int m = 20;
@@ -98,6 +99,8 @@ struct Ctx {
     bool fused = false;                  // fused multigrid kernels (BAH_FUSED=1) when nu_pre == 1 and nu_post >= 1
     // cooperative cycle over levels 1..L-1 (one launch per block set)
     bool coop = false;                   // opt-in (BAH_COOP=1): measured slower than separate launches
+    int cl_l0 = 0;                       // first level run by the cluster kernel (0: off)
+    int cl_size = 0;                     // CTAs per cluster
     int nsm = 0;
     CoopLevel* coop_lv[4] = {nullptr, nullptr, nullptr, nullptr};   // device descriptors per block set
     double2* bc64[3] = {nullptr, nullptr, nullptr};
@@ -296,7 +299,7 @@ struct MG {
         a.nu_pre = c.o.nu_pre; a.nu_post = c.o.nu_post; a.intergrid = c.o.intergrid;
         int rmax = 1;
         for (int z = 0; z < nb; ++z) {
-            a.inv[z] = c.inv[b0 + z];
+            a.inv[z] = c.invs[b0 + z];
             a.bc64[z] = c.bc64[b0 + z];
             rmax = std::max(rmax, std::max(c.s64[1][b0 + z].rx, c.s64[1][b0 + z].rz));
         }
@@ -308,27 +311,61 @@ struct MG {
             bytes += 14.5 * vs * npl * nb + 3.0 * coef_bytes(c, l, b0, nb) + ccs * npl * nb;
         }
         const double npc = (double)c.ln1[c.L - 1] * c.ln2[c.L - 1];
-        bytes += nb * (npc * npc * 16.0 + 32.0 * npc);
+        bytes += nb * (npc * npc * vs + 32.0 * npc);
         Prof pr(c, BAH_K_COOP, st, bytes);
         launch_coop_cycle<MODE>(a, rmax, c.nsm, st);
     }
 
-    // Result of one cycle with zero initial guess on level l for blocks
-    // [b0, b0+nb) and bt.nr right-hand sides: right-hand sides in vB[l][b]
-    // (stride npl), results written to out[z] with right-hand-side stride ostride.
+    // levels cl_l0..L-1 of a V-cycle in one cluster launch: right-hand sides in
+    // vB[cl_l0], results in vX[cl_l0] (bt.nr right-hand sides at the level's stride)
+    static void cluster_levels(Ctx& c, int b0, int nb, const Batch& bt, cudaStream_t st, bool warm = false) {
+        ClusterArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.lv = c.coop_lv[b0 == 2 ? 0 : (b0 == 1 ? 3 : (nb == 2 ? 1 : 2))];
+        a.l0 = c.cl_l0; a.L = c.L; a.b0 = b0; a.nb = nb;
+        a.wcycle = c.o.cycle == BAH_CYCLE_W; a.warm = warm;
+        a.nu_pre = c.o.nu_pre; a.nu_post = c.o.nu_post; a.intergrid = c.o.intergrid;
+        a.active = bt.active;
+        int rmax = 1;
+        for (int z = 0; z < nb; ++z) {
+            a.inv[z] = c.invs[b0 + z];
+            for (int l = c.cl_l0; l < c.L; ++l)
+                rmax = std::max(rmax, std::max(c.s64[l][b0 + z].rx, c.s64[l][b0 + z].rz));
+        }
+        const double vs = sizeof(V);
+        double bytes = 0, visits = 1;
+        for (int l = c.cl_l0; l < c.L - 1; ++l) {
+            const double npl = (double)c.ln1[l] * c.ln2[l];
+            const int sweeps = c.o.nu_pre + c.o.nu_post + 1;      // smoothing sweeps and the residual
+            bytes += visits * (sweeps * (coef_bytes(c, l, b0, nb) + 3.0 * vs * npl * nb * bt.nr) +
+                               3.5 * vs * npl * nb * bt.nr);
+            if (a.wcycle && l + 1 < c.L - 1) visits *= 2;
+        }
+        const int npc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
+        bytes += visits * nb * ((double)npc * npc * vs + 2.0 * npc * vs * bt.nr);
+        Prof pr(c, BAH_K_CLUSTER, st, bytes);
+        launch_cluster_cycle<MODE>(a, rmax, bt.nr, c.cl_size, npc, st);
+    }
+
+    // One cycle on level l for blocks [b0, b0+nb) and bt.nr right-hand sides:
+    // right-hand sides in vB[l][b] (stride npl), results written to out[z] with
+    // right-hand-side stride ostride.  The initial guess is zero, or (x0) the
+    // values already in out[z].  A W-cycle visits the coarse problem twice: the
+    // second visit starts from the first one's result (Sec. 2.2, two recursive
+    // calls), except when the coarse level is the coarsest, solved exactly once.
     static void cycle(Ctx& c, int l, int b0, int nb, V* const* out, size_t ostride, const Batch& bt,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool x0 = false) {
         const size_t npl = (size_t)c.ln1[l] * c.ln2[l];
         const double vs = sizeof(V), ccs = sizeof(CC);
         const double nr = bt.nr;
         if (l == c.L - 1) {
-            const double2* inv[3];
+            const V* inv[3];
             const V* bb[3];
             V* xx[3];
-            for (int z = 0; z < nb; ++z) { inv[z] = c.inv[b0 + z]; bb[z] = (const V*)c.vB[l][b0 + z]; xx[z] = out[z]; }
+            for (int z = 0; z < nb; ++z) { inv[z] = (const V*)c.invs[b0 + z]; bb[z] = (const V*)c.vB[l][b0 + z]; xx[z] = out[z]; }
             RhsStride rs;
             rs.s0 = npl; rs.s1 = ostride; rs.active = bt.active;
-            Prof pr(c, BAH_K_COARSE, st, nr * nb * ((double)npl * npl * 16.0 + 2.0 * npl * vs));
+            Prof pr(c, BAH_K_COARSE, st, nb * (double)npl * npl * vs + nr * nb * 2.0 * npl * vs);
             launch_coarse_apply<MODE>(nb, (int)npl, inv, bb, xx, st, bt.nr, rs);
             return;
         }
@@ -349,14 +386,16 @@ struct MG {
         V* cb[3];
         V* cx[3];
         for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
-        if (bt.nr == 1 && c.fused && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
+        const bool wcyc = c.o.cycle == BAH_CYCLE_W;
+        if (bt.nr == 1 && c.fused && !wcyc && !x0 && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
             // pre-smoothing + residual + restriction in one launch
             {
                 Prof pr(c, BAH_K_RESTRICT, st, cb_ + nb * npl * vs * 2.25);
                 launch_smooth_restrict<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), pf5, w, cb,
                                              c.o.intergrid, st);
             }
-            cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
+            if (c.cl_l0 == l + 1) cluster_levels(c, b0, nb, bt, st);
+            else cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
             // prolongation + correction + first post-smoothing sweep
             {
                 Prof pr(c, BAH_K_PROLONG, st, sweep + nb * npl * vs * 0.25);
@@ -370,7 +409,13 @@ struct MG {
             }
         } else {
             // pre-relaxation
-            if (c.o.nu_pre >= 1) {
+            if (x0) {
+                for (int s = 0; s < c.o.nu_pre; ++s) {
+                    Prof pr(c, BAH_K_JACOBI, st, sweep);
+                    launch_jacobi<MODE>(set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt), pf5, w, 0, st);
+                    swap_cur();
+                }
+            } else if (c.o.nu_pre >= 1) {
                 {
                     Prof pr(c, BAH_K_JACOBI, st, nr * nb * npl * (2.0 * vs + ccs));
                     launch_jacobi<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), pf5, w, 1, st);
@@ -396,8 +441,14 @@ struct MG {
                 launch_restrict<MODE>(rs, cb, c.o.intergrid, st, nplc);
             }
             // coarse-grid correction
-            if (l == 0 && c.coop && bt.nr == 1) coop_levels(c, b0, nb, st);
-            else cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
+            if (l == 0 && c.coop && !wcyc && bt.nr == 1) coop_levels(c, b0, nb, st);
+            else if (c.cl_l0 == l + 1) {
+                cluster_levels(c, b0, nb, bt, st);
+                if (wcyc && l + 1 < c.L - 1) cluster_levels(c, b0, nb, bt, st, true);
+            } else {
+                cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
+                if (wcyc && l + 1 < c.L - 1) cycle(c, l + 1, b0, nb, cx, nplc, bt, st, true);
+            }
             {
                 Prof pr(c, BAH_K_PROLONG, st, nr * nb * npl * vs * 2.25);
                 launch_prolong_add<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), cx, st, nplc);
@@ -550,6 +601,13 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
         for (int b = 0; b < 3; ++b) {
             TRY(c.alloc_t(&c.inv[b], (size_t)nc * nc));
             TRY(coarse_invert(b, c.s64[c.L - 1][b], c.inv[b], (double2*)work, flag, st));
+            if (c.mode == BAH_MIXED) {
+                // the FP64 inverse rounded once to FP32 for the mixed cycle's coarse solve
+                TRY(c.alloc(&c.invs[b], (size_t)nc * nc * sizeof(float2)));
+                launch_convert<double2, float2>(c.inv[b], (float2*)c.invs[b], (size_t)nc * nc, st);
+            } else {
+                c.invs[b] = c.inv[b];
+            }
         }
     }
     // multigrid vectors
@@ -598,6 +656,32 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
             }
             TRY(c.alloc_t(&c.coop_lv[set], c.L));
             BAH_CUDA_TRY(cudaMemcpyAsync(c.coop_lv[set], lv.data(), c.L * sizeof(CoopLevel), cudaMemcpyHostToDevice, st));
+        }
+    }
+    // cluster kernel for the small levels: from the first level below the fine
+    // grid with at most BAH_CLUSTER_PTS points (default 16384); BAH_CLUSTER=0
+    // turns it off, BAH_CLUSTER_SIZE sets the CTAs per cluster (default 16,
+    // halved until the device can co-schedule a cluster)
+    {
+        bool on = c.L >= 2 && c.L <= kMaxLevels;
+        if (const char* e = getenv("BAH_CLUSTER")) on = on && e[0] != '0';
+        long long maxpts = 16384;
+        if (const char* e = getenv("BAH_CLUSTER_PTS")) maxpts = atoll(e);
+        int want = 16;
+        if (const char* e = getenv("BAH_CLUSTER_SIZE")) want = std::max(2, std::min(16, atoi(e)));
+        c.cl_l0 = 0;
+        if (on) {
+            for (int l = 1; l < c.L - 1; ++l)
+                if ((long long)c.ln1[l] * c.ln2[l] <= maxpts) { c.cl_l0 = l; break; }
+        }
+        if (c.cl_l0 > 0) {
+            int rmax = 1;
+            for (int l = c.cl_l0; l < c.L; ++l)
+                for (int b = 0; b < 3; ++b) rmax = std::max(rmax, std::max(c.s64[l][b].rx, c.s64[l][b].rz));
+            const int npc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
+            c.cl_size = c.mode == BAH_MIXED ? cluster_size_for<BAH_MIXED>(rmax, want, npc)
+                                            : cluster_size_for<BAH_FP64>(rmax, want, npc);
+            if (c.cl_size < 2) c.cl_l0 = 0;
         }
     }
     // Krylov workspace
@@ -975,8 +1059,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
         set_error("bad intergrid");
         return BAH_ERR_ARG;
     }
-    if (o.cycle == BAH_CYCLE_W) { set_error("W-cycles are not implemented in this build"); return BAH_ERR_UNSUPPORTED; }
-    if (o.cycle != BAH_CYCLE_V) { set_error("bad cycle"); return BAH_ERR_ARG; }
+    if (o.cycle != BAH_CYCLE_V && o.cycle != BAH_CYCLE_W) { set_error("bad cycle"); return BAH_ERR_ARG; }
 
     bah_ctx* h = new (std::nothrow) bah_ctx();
     if (!h) { set_error("host allocation failed"); return BAH_ERR_OOM; }

@@ -388,6 +388,65 @@ def test_cooperative_levels_match_standalone_kernels(prec, monkeypatch):
     assert rel(W.padded_to_compact(out["coop"], p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cluster_levels_match_standalone_kernels(prec, monkeypatch):
+    """By default the levels below the first one with at most 16384 points run
+    in one thread-block-cluster launch per block set; BAH_CLUSTER=0 runs them
+    as separate kernels.  The per-point arithmetic is the same, so the results
+    agree to rounding, for every cluster size, for a single right-hand side
+    and for a batch; and they match the oracle's preconditioner."""
+    p = W.layered(128, 64, 5, seed=29, abc=8)
+    S = elastic.from_problem(p)
+    r = W.random_vector(p.n, 37)
+    out = {}
+    for mode in ("0", "2", "8", "16"):
+        if mode == "0":
+            monkeypatch.setenv("BAH_CLUSTER", "0")
+        else:
+            monkeypatch.setenv("BAH_CLUSTER", "1")
+            monkeypatch.setenv("BAH_CLUSTER_SIZE", mode)
+        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=4)
+        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
+        s.close()
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    for mode in ("2", "8", "16"):
+        assert rel(out[mode], out["0"]) <= tol, (mode, rel(out[mode], out["0"]))
+    pc = precond.multigrid(S, 4, precond.default_alpha(4), precision=prec)
+    ref = pc.apply(W.padded_to_compact(r, p.n))
+    assert rel(W.padded_to_compact(out["16"], p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
+    # batched solves (ragged last batch, 5 sources in batches of 2) with and without the cluster path
+    b = np.stack([W.point_source(p, (12 + 24 * k, 8)) for k in range(5)])
+    xs = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("BAH_CLUSTER", mode)
+        monkeypatch.delenv("BAH_CLUSTER_SIZE", raising=False)
+        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=4,
+                                    rhs_block=2)
+        x, st, stats = s.solve(to_dev(b), rtol=1e-7)
+        assert st == bah.BAH_OK
+        xs[mode] = (to_host(x), [q["iters"] for q in stats])
+        s.close()
+    assert xs["0"][1] == xs["1"][1]
+    assert rel(xs["1"][0], xs["0"][0]) <= (1e-10 if prec == "fp64" else 1e-5)
+
+
+def test_cluster_path_is_taken(systems):
+    """The cluster kernel is launched on the default schedule (one launch per
+    block set per preconditioner application) and no separate kernels run on
+    the levels it covers."""
+    p, S = get("layered_64x32", systems)
+    s = bah.Solver.from_problem(p, levels=3)
+    bah.bah_profile_control(s.ctx, 0, True)
+    s.apply_preconditioner(to_dev(W.random_vector(p.n, 3)))
+    pr = bah.bah_profile_read(s.ctx)
+    cl = pr["classes"]["cluster"]
+    assert cl["calls"] == 2 and cl["launches"] == 2
+    # level 0 only: 3 Jacobi sweeps per block set
+    assert pr["classes"]["jacobi"]["calls"] == 6
+    assert pr["classes"]["coarse"]["calls"] == 0
+    s.close()
+
+
 # ----------------------------------------------------------------------------
 # batched right-hand sides
 # ----------------------------------------------------------------------------
