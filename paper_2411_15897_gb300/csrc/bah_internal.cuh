@@ -33,6 +33,29 @@ __device__ __forceinline__ void pdl_prologue() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// thread-block cluster: hardware barrier over all threads of all CTAs of the
+// cluster (release/acquire at cluster scope: shared and global memory writes
+// before it are visible to every thread of the cluster after it), the CTA's
+// rank, the cluster's CTA count, and the cluster's index in the grid (x)
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_nrank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
     cudaLaunchConfig_t cfg = {};
@@ -167,6 +190,33 @@ struct ClusterArgs {
     const void* inv[3];       // coarsest inverses in the cycle's vector type
     const int* active;        // per-right-hand-side flags, or null
 };
+// shared-memory-resident cluster multigrid (mixed mode): levels l0 .. L-1 of
+// one block set, one cluster per block and right-hand side; lv[k] is level
+// l0 + k, its rows split in slabs of rp rows per CTA, and off_* are byte
+// offsets of its arrays in each CTA's dynamic shared memory
+struct SmLevel {
+    int n1, n2, rp;
+    float w;                  // Jacobi damping
+    unsigned off_c, off_x, off_t, off_b;
+};
+struct SmArgs {
+    SmLevel lv[kMaxLevels];
+    int nlev, b0, nb, nu_pre, nu_post, intergrid, wcycle, warm;
+    int rx[2][kMaxLevels], rz[2][kMaxLevels];
+    const __nv_bfloat162* S[2][kMaxLevels];   // global stencils (levels below the coarsest)
+    const float2* gb[2];      // level-l0 right-hand sides (right-hand side r at r * points)
+    float2* gx[2];            // level-l0 iterates / results
+    const float2* inv[2];     // coarsest inverses, FP32 complex
+    unsigned off_inv, off_g;  // own inverse rows; gathered coarsest right-hand side
+    const int* active;
+};
+// fills the shared-memory layout of a (n1, n2, slot counts per level from l0);
+// returns the bytes of dynamic shared memory per CTA
+size_t smmg_layout(SmArgs& a, const int* n1, const int* n2, const int* nslot_max, int nlev, int cs);
+// sets the kernel attributes; returns how many clusters of cs CTAs fit (0: none)
+int smmg_prepare(int rm, int cs, size_t smem);
+int launch_cluster_mg(const SmArgs& a, int rm, int nrhs, int cs, size_t smem, cudaStream_t st);
+
 template <int MODE>
 int cluster_size_for(int max_radius, int want, int coarse_pts);
 template <int MODE>

@@ -64,4 +64,9 @@ __host__ __device__ __forceinline__ T rw_axis_t(bool nodal, int intergrid, int n
     return T(0.5) * pw_axis_t<T>(nodal, nfine, f, c);
 }
 
+// first fine index of the 4-wide restriction support of coarse index c
+__host__ __device__ __forceinline__ int rbase(bool nodal, int intergrid, int c) {
+    return nodal ? 2 * c - 1 : (intergrid == BAH_INTERGRID_MIXED ? 2 * c : 2 * c - 1);
+}
+
 }  // namespace bah

@@ -1,0 +1,437 @@
+// Shared-memory-resident multigrid on a thread-block cluster (mixed mode).
+//
+// The small levels of a block's hierarchy (here: every level from l0 down to
+// the coarsest) are held entirely in the shared memory of one cluster of up
+// to 16 CTAs, one CTA per SM.  Each level's grid rows are split into equal
+// slabs, one per CTA; a CTA stores, for the points of its slab, the level's
+// Galerkin stencil (bfloat16 complex, slot-major), the iterate, a work
+// vector and the right-hand side, and on the coarsest level its rows of the
+// dense inverse (FP32 complex).  A stencil, restriction or prolongation tap
+// that falls into another CTA's slab is read from that CTA's shared memory
+// through the cluster's distributed shared memory (mapa + ld.shared::cluster).
+//
+// The cycle walks the same phases as the separate kernels -- zero-guess
+// damped Jacobi, Jacobi, residual, restriction, the coarsest solve,
+// prolongation and correction -- with the same per-point arithmetic, and the
+// W-cycle's second coarse visits (Sec. 2.2), separated by the hardware
+// cluster barrier.  Global memory is touched only to load the stencils, the
+// inverse rows and the level-l0 right-hand side (and iterate, on a warm
+// start) at the start, and to store the level-l0 result at the end.
+//
+// Deadlock freedom: the hardware co-schedules all CTAs of a cluster, every
+// thread of every CTA executes the same sequence of barriers (the control
+// flow depends only on kernel arguments; the only early exit is taken by a
+// whole cluster at once), and a final barrier keeps every CTA's shared
+// memory alive until no CTA of the cluster can still read it.
+#include "bah_internal.cuh"
+#include "intergrid.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace bah {
+
+namespace {
+
+__device__ __forceinline__ float2 ld_cluster_f2(uint32_t local_addr, unsigned rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(r));
+    return v;
+}
+
+}  // namespace
+
+template <int RM>
+__global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
+    pdl_prologue();
+    using V = float2;
+    using CC = __nv_bfloat162;
+    const unsigned cid = cluster_index();
+    const int z = (int)(cid % (unsigned)a.nb), rr = (int)(cid / (unsigned)a.nb);
+    if (a.active && !a.active[rr]) return;              // uniform over the cluster
+    const unsigned q = cluster_rank();
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int type = a.b0 + z;
+    const bool nodx = type == 0, nodz = type == 1;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+    const int nlev = a.nlev, kc = nlev - 1;
+
+    auto p0 = [&](const SmLevel& L) { return (int)q * L.rp * L.n1; };
+    auto nown = [&](const SmLevel& L) {
+        const int r0 = (int)q * L.rp, r1 = min(L.n2, r0 + L.rp);
+        return r1 > r0 ? (r1 - r0) * L.n1 : 0;
+    };
+    auto vec = [&](unsigned off) { return reinterpret_cast<V*>(sm + off); };
+    // value of vector `off` of level L at global point g, from whichever CTA owns it
+    auto ldg = [&](const SmLevel& L, unsigned off, int g) -> V {
+        const int owner = (g / L.n1) / L.rp;
+        const int local = g - owner * L.rp * L.n1;
+        return ld_cluster_f2(sbase + off + (uint32_t)local * 8u, (unsigned)owner);
+    };
+    auto coef = [&](int k) { return reinterpret_cast<const CC*>(sm + a.lv[k].off_c); };
+
+    // ---- load: stencils, coarsest inverse rows, level-l0 vectors ----
+    for (int k = 0; k < kc; ++k) {
+        const SmLevel& L = a.lv[k];
+        const int np = L.n1 * L.n2, own = nown(L), g0 = p0(L), cap = L.rp * L.n1;
+        const int nsl = (2 * a.rx[z][k] + 1) * (2 * a.rz[z][k] + 1);
+        const CC* S = a.S[z][k];
+        CC* cs = reinterpret_cast<CC*>(sm + L.off_c);
+        for (int e = tid; e < nsl * own; e += nth) {
+            const int s = e / own, t = e - s * own;
+            cs[s * cap + t] = S[(size_t)s * np + g0 + t];
+        }
+    }
+    {
+        const SmLevel& L = a.lv[kc];
+        const int npc = L.n1 * L.n2, own = nown(L), g0 = p0(L);
+        const V* src = a.inv[z] + (size_t)g0 * npc;
+        V* dst = vec(a.off_inv);
+        for (int e = tid; e < own * npc; e += nth) dst[e] = src[e];
+    }
+    {
+        const SmLevel& L = a.lv[0];
+        const int own = nown(L), g0 = p0(L);
+        const size_t roff = (size_t)rr * L.n1 * L.n2 + g0;
+        V* b = vec(L.off_b);
+        V* x = vec(L.off_x);
+        for (int t = tid; t < own; t += nth) {
+            b[t] = a.gb[z][roff + t];
+            if (a.warm) x[t] = a.gx[z][roff + t];
+        }
+    }
+    cluster_barrier();
+
+    // ---- phases (own points only; neighbours through distributed shared memory) ----
+    auto stencil = [&](int k, unsigned xoff, int lt) -> V {
+        const SmLevel& L = a.lv[k];
+        const int rx = a.rx[z][k], rz = a.rz[z][k], wx = 2 * rx + 1, cap = L.rp * L.n1;
+        const int g = p0(L) + lt, i = g % L.n1, j = g / L.n1;
+        const CC* cs = coef(k);
+        V sv[(2 * RM + 1) * (2 * RM + 1)], xv[(2 * RM + 1) * (2 * RM + 1)];
+        bool in[(2 * RM + 1) * (2 * RM + 1)];
+#pragma unroll
+        for (int dz = -RM; dz <= RM; ++dz) {
+#pragma unroll
+            for (int dx = -RM; dx <= RM; ++dx) {
+                const int qq = (dz + RM) * (2 * RM + 1) + (dx + RM);
+                const int ii = i + dx, jj = j + dz;
+                in[qq] = dx >= -rx && dx <= rx && dz >= -rz && dz <= rz && ii >= 0 && ii < L.n1 && jj >= 0 &&
+                         jj < L.n2;
+                const int slot = in[qq] ? (dz + rz) * wx + (dx + rx) : 0;
+                sv[qq] = ldc(cs[slot * cap + lt]);
+                xv[qq] = ldg(L, xoff, in[qq] ? jj * L.n1 + ii : g);
+            }
+        }
+        V acc = czero<V>();
+#pragma unroll
+        for (int e = 0; e < (2 * RM + 1) * (2 * RM + 1); ++e) {
+            const float m = in[e] ? 1.f : 0.f;
+            acc.x += m * (sv[e].x * xv[e].x - sv[e].y * xv[e].y);
+            acc.y += m * (sv[e].x * xv[e].y + sv[e].y * xv[e].x);
+        }
+        return acc;
+    };
+    auto diag = [&](int k, int lt) -> V {
+        const SmLevel& L = a.lv[k];
+        const int rx = a.rx[z][k], rz = a.rz[z][k];
+        return ldc(coef(k)[(rz * (2 * rx + 1) + rx) * (L.rp * L.n1) + lt]);
+    };
+    auto jacobi = [&](int k, unsigned xin, unsigned xout, bool zero) {
+        const SmLevel& L = a.lv[k];
+        const int own = nown(L), g0 = p0(L);
+        const V* b = vec(L.off_b);
+        const V* xi = vec(xin);
+        V* xo = vec(xout);
+        for (int lt = tid; lt < own; lt += nth) {
+            const int g = g0 + lt;
+            if (!valid_pt(type, g % L.n1, g / L.n1)) { xo[lt] = czero<V>(); continue; }
+            const V dg = diag(k, lt);
+            if (zero) { xo[lt] = cscale(cdiv(b[lt], dg), L.w); continue; }
+            const V ax = stencil(k, xin, lt);
+            const V corr = cdiv(csub(b[lt], ax), dg);
+            const V xv = xi[lt];
+            xo[lt] = cmk<V>(xv.x + L.w * corr.x, xv.y + L.w * corr.y);
+        }
+    };
+    auto residual = [&](int k, unsigned xin, unsigned rout) {
+        const SmLevel& L = a.lv[k];
+        const int own = nown(L), g0 = p0(L);
+        const V* b = vec(L.off_b);
+        V* r = vec(rout);
+        for (int lt = tid; lt < own; lt += nth) {
+            const int g = g0 + lt;
+            if (!valid_pt(type, g % L.n1, g / L.n1)) { r[lt] = czero<V>(); continue; }
+            r[lt] = csub(b[lt], stencil(k, xin, lt));
+        }
+    };
+    auto restrict_ = [&](int k, unsigned rin) {          // b_{k+1} = R r_k on own coarse points
+        const SmLevel& L = a.lv[k];
+        const SmLevel& Lc = a.lv[k + 1];
+        const int own = nown(Lc), g0 = p0(Lc);
+        V* bc = vec(Lc.off_b);
+        for (int lt = tid; lt < own; lt += nth) {
+            const int t = g0 + lt, I = t % Lc.n1, J = t / Lc.n1;
+            V acc = czero<V>();
+            if (valid_pt(type, I, J)) {
+                const int bx = rbase(nodx, a.intergrid, I), bz = rbase(nodz, a.intergrid, J);
+                float wxs[4], wzs[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    wxs[e] = rw_axis_t<float>(nodx, a.intergrid, L.n1, I, bx + e);
+                    wzs[e] = rw_axis_t<float>(nodz, a.intergrid, L.n2, J, bz + e);
+                }
+                V v[16];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        const bool ok = wzs[e] != 0.f && wxs[f] != 0.f;
+                        v[e * 4 + f] = ldg(L, rin, ok ? (bz + e) * L.n1 + (bx + f) : 0);
+                    }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        const float wgt = wzs[e] * wxs[f];
+                        acc.x += wgt * v[e * 4 + f].x;
+                        acc.y += wgt * v[e * 4 + f].y;
+                    }
+            }
+            bc[lt] = acc;
+        }
+    };
+    auto prolong = [&](int k, unsigned xoff) {             // x_k += P x_{k+1} on own fine points
+        const SmLevel& L = a.lv[k];
+        const SmLevel& Lc = a.lv[k + 1];
+        const int own = nown(L), g0 = p0(L), n1c = Lc.n1;
+        V* x = vec(xoff);
+        for (int lt = tid; lt < own; lt += nth) {
+            const int g = g0 + lt, i = g % L.n1, j = g / L.n1;
+            if (!valid_pt(type, i, j)) continue;
+            float px[3], pz[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                px[e] = pw_axis_t<float>(nodx, L.n1, i, (i >> 1) - 1 + e);
+                pz[e] = pw_axis_t<float>(nodz, L.n2, j, (j >> 1) - 1 + e);
+            }
+            V v[9];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const bool ok = pz[e] != 0.f && px[f] != 0.f;
+                    v[e * 3 + f] = ldg(Lc, Lc.off_x, ok ? ((j >> 1) - 1 + e) * n1c + ((i >> 1) - 1 + f) : 0);
+                }
+            V acc = x[lt];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const float wgt = pz[e] * px[f];
+                    acc.x += wgt * v[e * 3 + f].x;
+                    acc.y += wgt * v[e * 3 + f].y;
+                }
+            x[lt] = acc;
+        }
+    };
+    auto coarse = [&]() {                                   // x_c = A_c^{-1} b_c on own rows
+        const SmLevel& L = a.lv[kc];
+        const int npc = L.n1 * L.n2, own = nown(L);
+        V* gath = vec(a.off_g);
+        for (int g = tid; g < npc; g += nth) gath[g] = ldg(L, L.off_b, g);
+        __syncthreads();
+        const V* inv = vec(a.off_inv);
+        V* x = vec(L.off_x);
+        const int lane = tid & 31;
+        for (int row = tid >> 5; row < own; row += nth >> 5) {
+            const V* arow = inv + (size_t)row * npc;
+            float re = 0.f, im = 0.f;
+            for (int c = lane; c < npc; c += 32) {
+                const V m = arow[c];
+                const V v = gath[c];
+                re += m.x * v.x - m.y * v.y;
+                im += m.x * v.y + m.y * v.x;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (lane == 0) x[row] = cmk<V>(re, im);
+        }
+    };
+    auto zero_vec = [&](int k, unsigned off) {
+        V* x = vec(off);
+        for (int lt = tid; lt < nown(a.lv[k]); lt += nth) x[lt] = czero<V>();
+    };
+    auto copy_vec = [&](int k, unsigned from, unsigned to) {
+        const V* s = vec(from);
+        V* d = vec(to);
+        for (int lt = tid; lt < nown(a.lv[k]); lt += nth) d[lt] = s[lt];
+    };
+
+    // ---- the cycle: an explicit walk over the recursion (see k_cluster_cycle) ----
+    unsigned xs[kMaxLevels], ts[kMaxLevels];
+    int stage[kMaxLevels];
+    bool warm[kMaxLevels];
+    int k = 0;
+    stage[0] = 0;
+    warm[0] = a.warm != 0;
+    while (true) {
+        if (k == kc) {
+            coarse();
+            cluster_barrier();
+            --k;
+            continue;
+        }
+        const SmLevel& L = a.lv[k];
+        if (stage[k] == 0) {
+            unsigned x = L.off_x, t = L.off_t;
+            int s0 = 0;
+            if (!warm[k]) {
+                if (a.nu_pre >= 1) {
+                    jacobi(k, 0, x, true);
+                    s0 = 1;
+                } else {
+                    zero_vec(k, x);
+                }
+                cluster_barrier();
+            }
+            for (int s = s0; s < a.nu_pre; ++s) {
+                jacobi(k, x, t, false);
+                cluster_barrier();
+                const unsigned sw = x; x = t; t = sw;
+            }
+            residual(k, x, t);
+            cluster_barrier();
+            restrict_(k, t);
+            cluster_barrier();
+            xs[k] = x;
+            ts[k] = t;
+            stage[k] = 1;
+            ++k;
+            stage[k] = 0;
+            warm[k] = false;
+            continue;
+        }
+        if (stage[k] == 1 && a.wcycle && k + 1 < kc) {
+            stage[k] = 2;
+            ++k;
+            stage[k] = 0;
+            warm[k] = true;
+            continue;
+        }
+        unsigned x = xs[k], t = ts[k];
+        prolong(k, x);
+        cluster_barrier();
+        for (int s = 0; s < a.nu_post; ++s) {
+            jacobi(k, x, t, false);
+            cluster_barrier();
+            const unsigned sw = x; x = t; t = sw;
+        }
+        if (x != L.off_x) {
+            copy_vec(k, x, L.off_x);
+            cluster_barrier();
+        }
+        if (k == 0) break;
+        --k;
+    }
+
+    // ---- store the level-l0 result; keep shared memory alive for remote readers ----
+    {
+        const SmLevel& L = a.lv[0];
+        const int own = nown(L), g0 = p0(L);
+        const size_t roff = (size_t)rr * L.n1 * L.n2 + g0;
+        const V* x = vec(L.off_x);
+        for (int t = tid; t < own; t += nth) a.gx[z][roff + t] = x[t];
+    }
+    cluster_barrier();
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static const void* smmg_fn(int rm) {
+    return rm <= 1 ? (const void*)k_cluster_mg<1> : (const void*)k_cluster_mg<2>;
+}
+
+size_t smmg_layout(SmArgs& a, const int* n1, const int* n2, const int* nslot_max, int nlev, int cs) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 15) & ~size_t(15);
+        return (unsigned)o;
+    };
+    a.nlev = nlev;
+    for (int k = 0; k < nlev; ++k) {
+        SmLevel& L = a.lv[k];
+        L.n1 = n1[k];
+        L.n2 = n2[k];
+        L.rp = (n2[k] + cs - 1) / cs;
+        const size_t cap = (size_t)L.rp * L.n1;
+        if (k < nlev - 1) {
+            L.off_c = take(cap * nslot_max[k] * 4);
+            L.off_t = take(cap * 8);
+        } else {
+            L.off_c = 0;
+            L.off_t = 0;
+        }
+        L.off_x = take(cap * 8);
+        L.off_b = take(cap * 8);
+    }
+    const SmLevel& Lc = a.lv[nlev - 1];
+    const size_t npc = (size_t)Lc.n1 * Lc.n2;
+    a.off_inv = take((size_t)Lc.rp * Lc.n1 * npc * 8);
+    a.off_g = take(npc * 8);
+    return off;
+}
+
+int smmg_prepare(int rm, int cs, size_t smem) {
+    const void* fn = smmg_fn(rm);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int launch_cluster_mg(const SmArgs& a, int rm, int nrhs, int cs, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * a.nb * nrhs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    cudaError_t e = rm <= 1 ? cudaLaunchKernelEx(&cfg, k_cluster_mg<1>, a) : cudaLaunchKernelEx(&cfg, k_cluster_mg<2>, a);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+}  // namespace bah

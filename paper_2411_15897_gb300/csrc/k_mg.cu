@@ -377,9 +377,6 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 template <class V> struct PtrSet { V* p[3]; size_t s = 0; };
 
 // support of a 1-D restriction row for coarse index c: first fine index
-__host__ __device__ __forceinline__ int rbase(bool nodal, int intergrid, int c) {
-    return nodal ? 2 * c - 1 : (intergrid == BAH_INTERGRID_MIXED ? 2 * c : 2 * c - 1);
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> fine,
@@ -847,25 +844,6 @@ template int launch_coop_cycle<BAH_MIXED>(const CoopArgs&, int, int, cudaStream_
 // so the barrier always completes.  Clusters are independent: the grid is
 // (cluster size) x (blocks) x (right-hand sides) CTAs.
 // ===========================================================================
-__device__ __forceinline__ void cluster_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_nrank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_index() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-
 template <int MODE, int RM>
 __global__ void __launch_bounds__(256) k_cluster_cycle(ClusterArgs a) {
     pdl_prologue();

@@ -101,6 +101,9 @@ struct Ctx {
     bool coop = false;                   // opt-in (BAH_COOP=1): measured slower than separate launches
     int cl_l0 = 0;                       // first level run by the cluster kernel (0: off)
     int cl_size = 0;                     // CTAs per cluster
+    int sm_l0 = 0;                       // first level of the shared-memory cluster multigrid (0: off)
+    int sm_cs = 0, sm_rm = 2;            // its CTAs per cluster and stencil radius bound
+    size_t sm_bytes = 0;                 // its dynamic shared memory per CTA
     int nsm = 0;
     CoopLevel* coop_lv[4] = {nullptr, nullptr, nullptr, nullptr};   // device descriptors per block set
     double2* bc64[3] = {nullptr, nullptr, nullptr};
@@ -347,6 +350,44 @@ struct MG {
         launch_cluster_cycle<MODE>(a, rmax, bt.nr, c.cl_size, npc, st);
     }
 
+    // levels sm_l0..L-1 held in one cluster's shared memory per block and
+    // right-hand side (mixed mode): right-hand sides in vB[sm_l0], results in
+    // vX[sm_l0]; warm: start from the values in vX[sm_l0]
+    static void smem_levels(Ctx& c, int b0, int nb, const Batch& bt, cudaStream_t st, bool warm = false) {
+        if constexpr (MODE == BAH_MIXED) {
+            SmArgs a;
+            std::memset(&a, 0, sizeof(a));
+            const int l0 = c.sm_l0, nlev = c.L - l0;
+            int n1s[kMaxLevels], n2s[kMaxLevels], ns[kMaxLevels];
+            for (int k = 0; k < nlev; ++k) {
+                n1s[k] = c.ln1[l0 + k]; n2s[k] = c.ln2[l0 + k];
+                ns[k] = 0;
+                for (int b = 0; b < 3; ++b)
+                    ns[k] = std::max(ns[k], (2 * c.s64[l0 + k][b].rx + 1) * (2 * c.s64[l0 + k][b].rz + 1));
+            }
+            smmg_layout(a, n1s, n2s, ns, nlev, c.sm_cs);
+            for (int k = 0; k < nlev; ++k) a.lv[k].w = (float)weight(c, l0 + k);
+            a.b0 = b0; a.nb = nb; a.nu_pre = c.o.nu_pre; a.nu_post = c.o.nu_post; a.intergrid = c.o.intergrid;
+            a.wcycle = c.o.cycle == BAH_CYCLE_W; a.warm = warm; a.active = bt.active;
+            for (int z = 0; z < nb; ++z) {
+                const int b = b0 + z;
+                for (int k = 0; k < nlev - 1; ++k) {
+                    a.S[z][k] = (const __nv_bfloat162*)c.sst[l0 + k][b];
+                    a.rx[z][k] = c.s64[l0 + k][b].rx; a.rz[z][k] = c.s64[l0 + k][b].rz;
+                }
+                a.gb[z] = (const float2*)c.vB[l0][b];
+                a.gx[z] = (float2*)c.vX[l0][b];
+                a.inv[z] = (const float2*)c.invs[b];
+            }
+            double bytes = 0;
+            for (int k = 0; k < nlev - 1; ++k) bytes += coef_bytes(c, l0 + k, b0, nb) * bt.nr;
+            const double npc = (double)c.ln1[c.L - 1] * c.ln2[c.L - 1];
+            bytes += nb * bt.nr * (npc * npc * 8.0 + (double)c.ln1[l0] * c.ln2[l0] * 8.0 * (warm ? 3 : 2));
+            Prof pr(c, BAH_K_CLUSTER, st, bytes);
+            launch_cluster_mg(a, c.sm_rm, bt.nr, c.sm_cs, c.sm_bytes, st);
+        }
+    }
+
     // One cycle on level l for blocks [b0, b0+nb) and bt.nr right-hand sides:
     // right-hand sides in vB[l][b] (stride npl), results written to out[z] with
     // right-hand-side stride ostride.  The initial guess is zero, or (x0) the
@@ -394,7 +435,8 @@ struct MG {
                 launch_smooth_restrict<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), pf5, w, cb,
                                              c.o.intergrid, st);
             }
-            if (c.cl_l0 == l + 1) cluster_levels(c, b0, nb, bt, st);
+            if (c.sm_l0 == l + 1) smem_levels(c, b0, nb, bt, st);
+            else if (c.cl_l0 == l + 1) cluster_levels(c, b0, nb, bt, st);
             else cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
             // prolongation + correction + first post-smoothing sweep
             {
@@ -442,7 +484,10 @@ struct MG {
             }
             // coarse-grid correction
             if (l == 0 && c.coop && !wcyc && bt.nr == 1) coop_levels(c, b0, nb, st);
-            else if (c.cl_l0 == l + 1) {
+            else if (c.sm_l0 == l + 1) {
+                smem_levels(c, b0, nb, bt, st);
+                if (wcyc && l + 1 < c.L - 1) smem_levels(c, b0, nb, bt, st, true);
+            } else if (c.cl_l0 == l + 1) {
                 cluster_levels(c, b0, nb, bt, st);
                 if (wcyc && l + 1 < c.L - 1) cluster_levels(c, b0, nb, bt, st, true);
             } else {
@@ -658,13 +703,17 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
             BAH_CUDA_TRY(cudaMemcpyAsync(c.coop_lv[set], lv.data(), c.L * sizeof(CoopLevel), cudaMemcpyHostToDevice, st));
         }
     }
-    // cluster kernel for the small levels: from the first level below the fine
-    // grid with at most BAH_CLUSTER_PTS points (default 16384); BAH_CLUSTER=0
-    // turns it off, BAH_CLUSTER_SIZE sets the CTAs per cluster (default 16,
-    // halved until the device can co-schedule a cluster)
+    // cluster kernel for the small levels (opt-in, BAH_CLUSTER=1): from the
+    // first level below the fine grid with at most BAH_CLUSTER_PTS points
+    // (default 16384); BAH_CLUSTER_SIZE sets the CTAs per cluster (default 16,
+    // halved until the device can co-schedule a cluster).  Measured slower than
+    // separate launches on the 512x512 workload: each phase waits on L2
+    // latency, and the coarsest dense product has too few loads in flight on
+    // one cluster's SMs.
     {
-        bool on = c.L >= 2 && c.L <= kMaxLevels;
-        if (const char* e = getenv("BAH_CLUSTER")) on = on && e[0] != '0';
+        bool on = false;
+        if (const char* e = getenv("BAH_CLUSTER")) on = e[0] == '1';
+        on = on && c.L >= 2 && c.L <= kMaxLevels;
         long long maxpts = 16384;
         if (const char* e = getenv("BAH_CLUSTER_PTS")) maxpts = atoll(e);
         int want = 16;
@@ -682,6 +731,37 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
             c.cl_size = c.mode == BAH_MIXED ? cluster_size_for<BAH_MIXED>(rmax, want, npc)
                                             : cluster_size_for<BAH_FP64>(rmax, want, npc);
             if (c.cl_size < 2) c.cl_l0 = 0;
+        }
+    }
+    // shared-memory cluster multigrid (mixed mode; BAH_SMEM_MG=0 turns it off):
+    // from the first level below the fine grid whose levels, down to the
+    // coarsest, fit in the shared memory of one cluster (16 CTAs, else 8)
+    if (c.mode == BAH_MIXED && c.L >= 3 && c.L <= kMaxLevels && c.cl_l0 == 0) {
+        bool on = true;
+        if (const char* e = getenv("BAH_SMEM_MG")) on = e[0] != '0';
+        int dev = 0, optin = 0;
+        BAH_CUDA_TRY(cudaGetDevice(&dev));
+        BAH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        for (int l0 = 1; on && l0 < c.L - 1 && c.sm_l0 == 0; ++l0) {
+            const int nlev = c.L - l0;
+            int n1s[kMaxLevels], n2s[kMaxLevels], ns[kMaxLevels], rm = 1;
+            for (int k = 0; k < nlev; ++k) {
+                n1s[k] = c.ln1[l0 + k]; n2s[k] = c.ln2[l0 + k];
+                ns[k] = 0;
+                for (int b = 0; b < 3; ++b) {
+                    ns[k] = std::max(ns[k], (2 * c.s64[l0 + k][b].rx + 1) * (2 * c.s64[l0 + k][b].rz + 1));
+                    rm = std::max(rm, std::max(c.s64[l0 + k][b].rx, c.s64[l0 + k][b].rz));
+                }
+            }
+            for (int cs = 16; cs >= 8 && c.sm_l0 == 0; cs /= 2) {
+                SmArgs a;
+                std::memset(&a, 0, sizeof(a));
+                const size_t bytes = smmg_layout(a, n1s, n2s, ns, nlev, cs);
+                if (bytes > (size_t)optin) continue;
+                if (smmg_prepare(rm, cs, bytes) >= 1) {
+                    c.sm_l0 = l0; c.sm_cs = cs; c.sm_rm = rm; c.sm_bytes = bytes;
+                }
+            }
         }
     }
     // Krylov workspace

@@ -390,9 +390,10 @@ def test_cooperative_levels_match_standalone_kernels(prec, monkeypatch):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_cluster_levels_match_standalone_kernels(prec, monkeypatch):
-    """By default the levels below the first one with at most 16384 points run
-    in one thread-block-cluster launch per block set; BAH_CLUSTER=0 runs them
-    as separate kernels.  The per-point arithmetic is the same, so the results
+    """With BAH_CLUSTER=1 the levels below the first one with at most 16384
+    points run in one thread-block-cluster launch per block set; by default
+    (BAH_CLUSTER=0) they run as separate kernels.  The per-point arithmetic is
+    the same, so the results
     agree to rounding, for every cluster size, for a single right-hand side
     and for a batch; and they match the oracle's preconditioner."""
     p = W.layered(128, 64, 5, seed=29, abc=8)
@@ -430,10 +431,11 @@ def test_cluster_levels_match_standalone_kernels(prec, monkeypatch):
     assert rel(xs["1"][0], xs["0"][0]) <= (1e-10 if prec == "fp64" else 1e-5)
 
 
-def test_cluster_path_is_taken(systems):
-    """The cluster kernel is launched on the default schedule (one launch per
-    block set per preconditioner application) and no separate kernels run on
-    the levels it covers."""
+def test_cluster_path_is_taken(systems, monkeypatch):
+    """With BAH_CLUSTER=1 the cluster kernel runs once per block set per
+    preconditioner application and no separate kernels run on the levels it
+    covers."""
+    monkeypatch.setenv("BAH_CLUSTER", "1")
     p, S = get("layered_64x32", systems)
     s = bah.Solver.from_problem(p, levels=3)
     bah.bah_profile_control(s.ctx, 0, True)
@@ -445,6 +447,51 @@ def test_cluster_path_is_taken(systems):
     assert pr["classes"]["jacobi"]["calls"] == 6
     assert pr["classes"]["coarse"]["calls"] == 0
     s.close()
+
+
+@pytest.mark.parametrize("cycle", [bah.BAH_CYCLE_V, bah.BAH_CYCLE_W])
+@pytest.mark.parametrize("levels", [4, 5])
+def test_smem_cluster_multigrid_matches_separate_kernels(cycle, levels, monkeypatch):
+    """Mixed mode holds the small levels (from the first one that fits, down
+    to the coarsest) in one cluster's shared memory.  Against the separate
+    kernels (BAH_SMEM_MG=0): the same preconditioner to FP32 rounding, V and
+    W cycles, slabs that leave some CTAs without rows (8x4 and 16x8 levels on
+    a 16-CTA cluster); against the oracle to the mixed-mode tolerance; and
+    batched solves (5 sources in batches of 2) with identical counts."""
+    p = W.layered(128, 64, 5, seed=31, abc=8)
+    S = elastic.from_problem(p)
+    r = W.random_vector(p.n, 41)
+    cyc = "W" if cycle == bah.BAH_CYCLE_W else "V"
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("BAH_SMEM_MG", mode)
+        s = bah.Solver.from_problem(p, levels=levels, cycle=cycle)
+        if mode == "1":
+            bah.bah_profile_control(s.ctx, 0, True)
+        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
+        if mode == "1":
+            pr = bah.bah_profile_read(s.ctx)
+            assert pr["classes"]["cluster"]["calls"] >= 2, pr["classes"]["cluster"]
+            assert pr["classes"]["coarse"]["calls"] == 0
+        s.close()
+    assert rel(out["1"], out["0"]) <= 1e-6, rel(out["1"], out["0"])
+    pc = precond.multigrid(S, levels, precond.default_alpha(levels), precision="mixed", cycle=cyc)
+    assert rel(W.padded_to_compact(out["1"], p.n), pc.apply(W.padded_to_compact(r, p.n))) <= 2e-4
+    b = np.stack([W.point_source(p, (12 + 24 * k, 8)) for k in range(5)])
+    xs = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("BAH_SMEM_MG", mode)
+        s = bah.Solver.from_problem(p, levels=levels, cycle=cycle, rhs_block=2)
+        x, st, stats = s.solve(to_dev(b), rtol=1e-7)
+        assert st == bah.BAH_OK
+        xs[mode] = (to_host(x), [q["iters"] for q in stats])
+        s.close()
+    assert xs["0"][1] == xs["1"][1]
+    assert rel(xs["1"][0], xs["0"][0]) <= 1e-5
+    xh = xs["1"][0]
+    for k in range(5):
+        bc = W.padded_to_compact(b[k], p.n)
+        assert np.linalg.norm(bc - S.H @ W.padded_to_compact(xh[k], p.n)) / np.linalg.norm(bc) <= 1e-7
 
 
 # ----------------------------------------------------------------------------

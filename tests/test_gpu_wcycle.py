@@ -65,11 +65,15 @@ def layered():
     return p, elastic.from_problem(p)
 
 
+@pytest.mark.parametrize("cluster", ["0", "1"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("levels,nu", [(3, (1, 2)), (4, (1, 2)), (4, (2, 2)), (4, (0, 2)), (2, (1, 2))])
-def test_w_block_cycle_matches_oracle(prec, levels, nu, layered):
+def test_w_block_cycle_matches_oracle(prec, levels, nu, cluster, layered, monkeypatch):
     """One W(nu1,nu2) cycle per block with zero initial guess; 2 levels (where a
-    W-cycle equals a V-cycle) up to 4 (a 4-deep recursion: 1, 2, 4 visits)."""
+    W-cycle equals a V-cycle) up to 4 (a 4-deep recursion: 1, 2, 4 visits),
+    with the levels below the fine one as separate kernels or (cluster=1) in
+    the cluster kernel's walk of the recursion."""
+    monkeypatch.setenv("BAH_CLUSTER", cluster)
     p, S = layered
     s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=levels,
                                 cycle=bah.BAH_CYCLE_W, nu_pre=nu[0], nu_post=nu[1])
@@ -111,10 +115,12 @@ def test_w_preconditioner_matches_oracle(prec, layered):
     s.close()
 
 
+@pytest.mark.parametrize("cluster", ["0", "1"])
 @pytest.mark.parametrize("prec", [bah.BAH_MIXED, bah.BAH_FP64])
-def test_w_batched_solve_equals_sequential(prec, layered):
+def test_w_batched_solve_equals_sequential(prec, cluster, layered, monkeypatch):
     """W-cycles inside the batched solve (5 sources in batches of 3, ragged
     last batch): identical counts and iterates to the one-at-a-time solve."""
+    monkeypatch.setenv("BAH_CLUSTER", cluster)
     p, S = layered
     b = np.stack([W.point_source(p, (8 + 12 * k, 6)) for k in range(5)])
     s1 = bah.Solver.from_problem(p, precision=prec, levels=4, cycle=bah.BAH_CYCLE_W)
