@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per batch (default: all sources)")
     ap.add_argument("--gradient", action="store_true", help="also time the adjoint gradient of a receiver misfit")
     ap.add_argument("--maxit", type=int, default=20000)
+    ap.add_argument("--alpha", type=float, default=-1.0, help="shift alpha (default: the library's choice)")
+    ap.add_argument("--cycle", default="V", choices=["V", "W"])
+    ap.add_argument("--nu", default="1,2", help="pre- and post-smoothing sweeps")
     ap.add_argument("--krylov-fp64-steps", type=int, default=2,
                     help="also time the same solve with the Krylov basis in IEEE FP64")
     return ap.parse_args()
@@ -227,7 +230,9 @@ def run_bah(args):
     rhs_block = args.rhs_block if args.rhs_block > 0 else nsrc
     opts = dict(precision=bah.BAH_MIXED, levels=args.levels, max_coarse_cells=args.max_coarse, restart=args.restart,
                 krylov_arith=bah.BAH_KRYLOV_DF if args.krylov == "df" else bah.BAH_KRYLOV_FP64,
-                rhs_block=rhs_block, maxit=args.maxit)
+                rhs_block=rhs_block, maxit=args.maxit, shift_alpha=args.alpha,
+                cycle=bah.BAH_CYCLE_W if args.cycle == "W" else bah.BAH_CYCLE_V,
+                nu_pre=int(args.nu.split(",")[0]), nu_post=int(args.nu.split(",")[1]))
     solver = bah.Solver.from_problem(prob, **opts)
     levels = solver.levels
     b_host = W.all_sources(prob) if nsrc > 1 else W.point_source(prob)
@@ -442,7 +447,8 @@ def run_bah(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.config, args.config), "grid": list(prob.n),
                    "unknowns": int(sum(W.compact_sizes(prob.n))), "sources": nsrc, "rhs_block": rhs_block,
-                   "levels": levels, "cycle": "V(1,2)", "restart": args.restart, "iters": iters[-1],
+                   "levels": levels, "cycle": f"{args.cycle}({args.nu})", "alpha": solver.alpha,
+                   "cluster_levels_from": solver.info["cluster_level"], "restart": args.restart, "iters": iters[-1],
                    "relres_true": relres, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"independent solves per GPU x{world}"},
         "fp64": fp64,

@@ -140,6 +140,21 @@ void bah_destroy(bah_ctx* ctx);
  * levels in use.  Either output pointer may be NULL. */
 int bah_sizes(const bah_ctx* ctx, long long* vector_len, int* levels);
 
+/* What the context chose (after defaults were applied): level count, the
+ * shift alpha of Eq. 2.8, the coarsest grid's point count, and the first
+ * level held in a thread-block cluster's shared memory (0: none) with the
+ * CTAs per cluster and the bytes of shared memory per CTA.  The paper has no
+ * counterpart; this is for reporting and tests. */
+typedef struct {
+    int       levels;
+    double    shift_alpha;
+    int       coarse_points;
+    int       cluster_level;
+    int       cluster_ctas;
+    long long cluster_smem_bytes;
+} bah_info;
+int bah_get_info(const bah_ctx* ctx, bah_info* out);
+
 /* y = H x (conj_transpose = 0) or y = H^H x (conj_transpose = 1) in FP64 for
  * nrhs vectors (Eq. 2.6; H is complex symmetric, so H^H = conj(H)).  x and y
  * are device vectors and must not overlap. */

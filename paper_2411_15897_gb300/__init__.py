@@ -36,7 +36,7 @@ BAH_KRYLOV_FP64 = 0
 BAH_KRYLOV_DF = 1
 
 # every symbol include/bah.h declares
-EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_apply_operator",
+EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_get_info", "bah_apply_operator",
            "bah_apply_preconditioner", "bah_solve", "bah_block_cycle", "bah_level_stencil",
            "bah_status_string", "bah_last_error", "bah_profile_control", "bah_profile_read",
            "bah_residual_norm_static", "bah_solve_adjoint", "bah_misfit", "bah_gradient")
@@ -57,6 +57,14 @@ class bah_opts(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("jacobi_w", C.c_double * 8), ("n_jacobi_w", C.c_int),
                 ("shift_alpha", C.c_double), ("intergrid", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
                 ("rhs_block", C.c_int), ("krylov_arith", C.c_int)]
+
+
+class bah_info(C.Structure):
+    _fields_ = [("levels", C.c_int), ("shift_alpha", C.c_double), ("coarse_points", C.c_int),
+                ("cluster_level", C.c_int), ("cluster_ctas", C.c_int), ("cluster_smem_bytes", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class bah_stats(C.Structure):
@@ -93,6 +101,8 @@ def lib():
         L.bah_destroy.restype = None
         L.bah_sizes.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
         L.bah_sizes.restype = C.c_int
+        L.bah_get_info.argtypes = [vp, C.POINTER(bah_info)]
+        L.bah_get_info.restype = C.c_int
         L.bah_apply_operator.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bah_apply_operator.restype = C.c_int
         L.bah_apply_preconditioner.argtypes = [vp, vp, vp, C.c_int, vp]
@@ -173,6 +183,12 @@ def bah_create(n, h, lam, mu, rho, gamma, omega, opts: bah_opts | None = None):
 
 def bah_destroy(ctx):
     lib().bah_destroy(ctx)
+
+
+def bah_get_info(ctx):
+    out = bah_info()
+    _check(lib().bah_get_info(ctx, C.byref(out)), "bah_get_info")
+    return out.as_dict()
 
 
 def bah_sizes(ctx):
@@ -290,6 +306,8 @@ class Solver:
         self.opts = bah_default_opts(**opts)
         self.ctx = bah_create(self.n, h, lam, mu, rho, gamma, omega, self.opts)
         self.vector_len, self.levels = bah_sizes(self.ctx)
+        self.info = bah_get_info(self.ctx)
+        self.alpha = self.info["shift_alpha"]
 
     @classmethod
     def from_problem(cls, prob, **opts):

@@ -196,6 +196,7 @@ struct ClusterArgs {
 // offsets of its arrays in each CTA's dynamic shared memory
 struct SmLevel {
     int n1, n2, rp;
+    float inv_rp, inv_n1;     // 1/rp and 1/n1 (row and column from a flat or row index)
     float w;                  // Jacobi damping
     unsigned off_c, off_x, off_t, off_b;
 };

@@ -31,6 +31,8 @@
 
 namespace bah {
 
+constexpr int kSmThreads = 384;   // threads per CTA (one CTA per SM)
+
 namespace {
 
 __device__ __forceinline__ float2 ld_cluster_f2(uint32_t local_addr, unsigned rank) {
@@ -41,10 +43,17 @@ __device__ __forceinline__ float2 ld_cluster_f2(uint32_t local_addr, unsigned ra
     return v;
 }
 
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
 }  // namespace
 
 template <int RM>
-__global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
+__global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
     pdl_prologue();
     using V = float2;
     using CC = __nv_bfloat162;
@@ -65,51 +74,57 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
         return r1 > r0 ? (r1 - r0) * L.n1 : 0;
     };
     auto vec = [&](unsigned off) { return reinterpret_cast<V*>(sm + off); };
-    // value of vector `off` of level L at global point g, from whichever CTA owns it
-    auto ldg = [&](const SmLevel& L, unsigned off, int g) -> V {
-        const int owner = (g / L.n1) / L.rp;
-        const int local = g - owner * L.rp * L.n1;
+    // value of vector `off` of level L at grid point (row, col), from whichever
+    // CTA owns the row (rows below 2^22: the float quotient floors exactly)
+    auto ldrc = [&](const SmLevel& L, unsigned off, int row, int col) -> V {
+        const int owner = (int)(((float)row + 0.5f) * L.inv_rp);
+        const int local = (row - owner * L.rp) * L.n1 + col;
         return ld_cluster_f2(sbase + off + (uint32_t)local * 8u, (unsigned)owner);
+    };
+    // row and column of own point lt of level L
+    auto own_rc = [&](const SmLevel& L, int lt, int& row, int& col) {
+        const int r = (int)(((float)lt + 0.5f) * L.inv_n1);
+        row = (int)q * L.rp + r;
+        col = lt - r * L.n1;
     };
     auto coef = [&](int k) { return reinterpret_cast<const CC*>(sm + a.lv[k].off_c); };
 
     // ---- load: stencils, coarsest inverse rows, level-l0 vectors ----
+    // asynchronous copies (cp.async), so that every thread keeps many loads in
+    // flight; one wait for all of them before the first barrier
     for (int k = 0; k < kc; ++k) {
         const SmLevel& L = a.lv[k];
         const int np = L.n1 * L.n2, own = nown(L), g0 = p0(L), cap = L.rp * L.n1;
         const int nsl = (2 * a.rx[z][k] + 1) * (2 * a.rz[z][k] + 1);
         const CC* S = a.S[z][k];
-        CC* cs = reinterpret_cast<CC*>(sm + L.off_c);
-        for (int e = tid; e < nsl * own; e += nth) {
-            const int s = e / own, t = e - s * own;
-            cs[s * cap + t] = S[(size_t)s * np + g0 + t];
-        }
+        for (int s = 0; s < nsl; ++s)
+            for (int t = tid; t < own; t += nth)
+                cp_async4(sbase + L.off_c + (uint32_t)(s * cap + t) * 4u, S + (size_t)s * np + g0 + t);
     }
     {
         const SmLevel& L = a.lv[kc];
         const int npc = L.n1 * L.n2, own = nown(L), g0 = p0(L);
         const V* src = a.inv[z] + (size_t)g0 * npc;
-        V* dst = vec(a.off_inv);
-        for (int e = tid; e < own * npc; e += nth) dst[e] = src[e];
+        for (int e = tid; e < own * npc; e += nth) cp_async8(sbase + a.off_inv + (uint32_t)e * 8u, src + e);
     }
     {
         const SmLevel& L = a.lv[0];
         const int own = nown(L), g0 = p0(L);
         const size_t roff = (size_t)rr * L.n1 * L.n2 + g0;
-        V* b = vec(L.off_b);
-        V* x = vec(L.off_x);
         for (int t = tid; t < own; t += nth) {
-            b[t] = a.gb[z][roff + t];
-            if (a.warm) x[t] = a.gx[z][roff + t];
+            cp_async8(sbase + L.off_b + (uint32_t)t * 8u, a.gb[z] + roff + t);
+            if (a.warm) cp_async8(sbase + L.off_x + (uint32_t)t * 8u, a.gx[z] + roff + t);
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     cluster_barrier();
 
     // ---- phases (own points only; neighbours through distributed shared memory) ----
     auto stencil = [&](int k, unsigned xoff, int lt) -> V {
         const SmLevel& L = a.lv[k];
         const int rx = a.rx[z][k], rz = a.rz[z][k], wx = 2 * rx + 1, cap = L.rp * L.n1;
-        const int g = p0(L) + lt, i = g % L.n1, j = g / L.n1;
+        int j, i;
+        own_rc(L, lt, j, i);
         const CC* cs = coef(k);
         V sv[(2 * RM + 1) * (2 * RM + 1)], xv[(2 * RM + 1) * (2 * RM + 1)];
         bool in[(2 * RM + 1) * (2 * RM + 1)];
@@ -123,7 +138,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
                          jj < L.n2;
                 const int slot = in[qq] ? (dz + rz) * wx + (dx + rx) : 0;
                 sv[qq] = ldc(cs[slot * cap + lt]);
-                xv[qq] = ldg(L, xoff, in[qq] ? jj * L.n1 + ii : g);
+                xv[qq] = ldrc(L, xoff, in[qq] ? jj : j, in[qq] ? ii : i);
             }
         }
         V acc = czero<V>();
@@ -142,13 +157,14 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
     };
     auto jacobi = [&](int k, unsigned xin, unsigned xout, bool zero) {
         const SmLevel& L = a.lv[k];
-        const int own = nown(L), g0 = p0(L);
+        const int own = nown(L);
         const V* b = vec(L.off_b);
         const V* xi = vec(xin);
         V* xo = vec(xout);
         for (int lt = tid; lt < own; lt += nth) {
-            const int g = g0 + lt;
-            if (!valid_pt(type, g % L.n1, g / L.n1)) { xo[lt] = czero<V>(); continue; }
+            int j, i;
+            own_rc(L, lt, j, i);
+            if (!valid_pt(type, i, j)) { xo[lt] = czero<V>(); continue; }
             const V dg = diag(k, lt);
             if (zero) { xo[lt] = cscale(cdiv(b[lt], dg), L.w); continue; }
             const V ax = stencil(k, xin, lt);
@@ -159,22 +175,24 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
     };
     auto residual = [&](int k, unsigned xin, unsigned rout) {
         const SmLevel& L = a.lv[k];
-        const int own = nown(L), g0 = p0(L);
+        const int own = nown(L);
         const V* b = vec(L.off_b);
         V* r = vec(rout);
         for (int lt = tid; lt < own; lt += nth) {
-            const int g = g0 + lt;
-            if (!valid_pt(type, g % L.n1, g / L.n1)) { r[lt] = czero<V>(); continue; }
+            int j, i;
+            own_rc(L, lt, j, i);
+            if (!valid_pt(type, i, j)) { r[lt] = czero<V>(); continue; }
             r[lt] = csub(b[lt], stencil(k, xin, lt));
         }
     };
     auto restrict_ = [&](int k, unsigned rin) {          // b_{k+1} = R r_k on own coarse points
         const SmLevel& L = a.lv[k];
         const SmLevel& Lc = a.lv[k + 1];
-        const int own = nown(Lc), g0 = p0(Lc);
+        const int own = nown(Lc);
         V* bc = vec(Lc.off_b);
         for (int lt = tid; lt < own; lt += nth) {
-            const int t = g0 + lt, I = t % Lc.n1, J = t / Lc.n1;
+            int J, I;
+            own_rc(Lc, lt, J, I);
             V acc = czero<V>();
             if (valid_pt(type, I, J)) {
                 const int bx = rbase(nodx, a.intergrid, I), bz = rbase(nodz, a.intergrid, J);
@@ -190,7 +208,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
 #pragma unroll
                     for (int f = 0; f < 4; ++f) {
                         const bool ok = wzs[e] != 0.f && wxs[f] != 0.f;
-                        v[e * 4 + f] = ldg(L, rin, ok ? (bz + e) * L.n1 + (bx + f) : 0);
+                        v[e * 4 + f] = ldrc(L, rin, ok ? bz + e : 0, ok ? bx + f : 0);
                     }
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -207,10 +225,11 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
     auto prolong = [&](int k, unsigned xoff) {             // x_k += P x_{k+1} on own fine points
         const SmLevel& L = a.lv[k];
         const SmLevel& Lc = a.lv[k + 1];
-        const int own = nown(L), g0 = p0(L), n1c = Lc.n1;
+        const int own = nown(L);
         V* x = vec(xoff);
         for (int lt = tid; lt < own; lt += nth) {
-            const int g = g0 + lt, i = g % L.n1, j = g / L.n1;
+            int j, i;
+            own_rc(L, lt, j, i);
             if (!valid_pt(type, i, j)) continue;
             float px[3], pz[3];
 #pragma unroll
@@ -224,7 +243,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
                     const bool ok = pz[e] != 0.f && px[f] != 0.f;
-                    v[e * 3 + f] = ldg(Lc, Lc.off_x, ok ? ((j >> 1) - 1 + e) * n1c + ((i >> 1) - 1 + f) : 0);
+                    v[e * 3 + f] = ldrc(Lc, Lc.off_x, ok ? (j >> 1) - 1 + e : 0, ok ? (i >> 1) - 1 + f : 0);
                 }
             V acc = x[lt];
 #pragma unroll
@@ -242,7 +261,7 @@ __global__ void __launch_bounds__(256, 1) k_cluster_mg(SmArgs a) {
         const SmLevel& L = a.lv[kc];
         const int npc = L.n1 * L.n2, own = nown(L);
         V* gath = vec(a.off_g);
-        for (int g = tid; g < npc; g += nth) gath[g] = ldg(L, L.off_b, g);
+        for (int g = tid; g < npc; g += nth) gath[g] = ldrc(L, L.off_b, g / L.n1, g % L.n1);
         __syncthreads();
         const V* inv = vec(a.off_inv);
         V* x = vec(L.off_x);
@@ -371,6 +390,8 @@ size_t smmg_layout(SmArgs& a, const int* n1, const int* n2, const int* nslot_max
         L.n1 = n1[k];
         L.n2 = n2[k];
         L.rp = (n2[k] + cs - 1) / cs;
+        L.inv_rp = 1.0f / (float)L.rp;
+        L.inv_n1 = 1.0f / (float)L.n1;
         const size_t cap = (size_t)L.rp * L.n1;
         if (k < nlev - 1) {
             L.off_c = take(cap * nslot_max[k] * 4);
@@ -398,7 +419,7 @@ int smmg_prepare(int rm, int cs, size_t smem) {
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kSmThreads);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -418,7 +439,7 @@ int smmg_prepare(int rm, int cs, size_t smem) {
 int launch_cluster_mg(const SmArgs& a, int rm, int nrhs, int cs, size_t smem, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * a.nb * nrhs);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kSmThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[2];

@@ -1205,6 +1205,18 @@ int bah_sizes(const bah_ctx* h, long long* vector_len, int* levels) {
     return BAH_OK;
 }
 
+int bah_get_info(const bah_ctx* h, bah_info* out) {
+    if (!h || !out) { set_error("bad argument"); return BAH_ERR_ARG; }
+    const Ctx& c = h->c;
+    out->levels = c.L;
+    out->shift_alpha = c.alpha;
+    out->coarse_points = c.ln1[c.L - 1] * c.ln2[c.L - 1];
+    out->cluster_level = c.sm_l0;
+    out->cluster_ctas = c.sm_cs;
+    out->cluster_smem_bytes = (long long)c.sm_bytes;
+    return BAH_OK;
+}
+
 int bah_apply_operator(bah_ctx* h, const void* x, void* y, int nrhs, int conj, void* stream) {
     if (!h || !x || !y || nrhs < 0) { set_error("bad argument"); return BAH_ERR_ARG; }
     Ctx& c = h->c;
