@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle FGMRES iterations per baseline sample")
     ap.add_argument("--profile-json", default="", help="write the per-kernel-class profile here")
     ap.add_argument("--levels", type=int, default=0)
-    ap.add_argument("--max-coarse", type=int, default=1024)
+    ap.add_argument("--max-coarse", type=int, default=256)
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--krylov", default="df", choices=["fp64", "df"])
     ap.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per batch (default: all sources)")
@@ -133,8 +133,9 @@ def run_reference(args):
         return
     prob = W.config(args.config)
     counts = oracle_counts().get(args.config)
+    from oracle import precond
     levels = counts["levels"] if counts else 6
-    alpha = counts["alpha"] if counts else 0.5
+    alpha = counts["alpha"] if counts else precond.default_alpha(levels)
     its = counts["iters"] if counts else None
     per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=args.warmup + args.steps)
     per = per[args.warmup:]
@@ -431,10 +432,11 @@ def run_bah(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         counts = oracle_counts().get(args.config)
-        alpha = 0.5 if levels >= 5 else {1: 0.0, 2: 0.1, 3: 0.2, 4: 0.4}[levels]
+        alpha = solver.alpha
         per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=1)
-        its = counts["iters"] if counts and counts.get("levels") == levels else statistics.median(iters)
-        src = "oracle's own count" if counts and counts.get("levels") == levels else "the GPU run's count"
+        same = bool(counts) and counts.get("levels") == levels and abs(counts.get("alpha", -1.0) - alpha) < 1e-12
+        its = counts["iters"] if same else statistics.median(iters)
+        src = "oracle's own count" if same else "the GPU run's count"
         cpu = {"value": 1.0 / (its * per[0]), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_iters} oracle FGMRES iterations of the same workload after a {setup:.1f} s setup, "
                          f"extrapolated to {its} iterations per solve ({src})"}

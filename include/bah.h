@@ -114,11 +114,11 @@ typedef struct {
     int    status;           /* BAH_OK, BAH_ERR_NOT_CONVERGED or BAH_ERR_NONFINITE */
 } bah_stats;
 
-/* Fill *opts with the defaults: BAH_MIXED, automatic levels with at most 1024
+/* Fill *opts with the defaults: BAH_MIXED, automatic levels with at most 256
  * coarsest cells, V(1,2), Jacobi weights 0.8, 0.8, 0.3 (Sec. 4.4.1), shift by
- * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels, 0.5 deeper; Sec. 4.4.3,
- * Table 4), bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1,
- * BAH_KRYLOV_FP64. */
+ * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels as in Sec. 4.4.3,
+ * Table 4; 1.0 for deeper hierarchies, found by the same kind of search),
+ * bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1, BAH_KRYLOV_FP64. */
 void bah_default_opts(bah_opts* opts);
 
 /* Build a solver for one grid, medium and frequency.  Copies the host medium

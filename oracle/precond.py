@@ -34,10 +34,16 @@ from . import multigrid as mg
 ALPHA_BY_LEVELS = {1: 0.0, 2: 0.1, 3: 0.2, 4: 0.4}
 
 
+ALPHA_DEEP = 1.0
+
+
 def default_alpha(levels):
     """Shift by level count following the 2D linear-media table (Sec. 4.4.3):
-    2 levels 0.1, 3 levels 0.2, 4 levels 0.4; deeper hierarchies 0.5."""
-    return ALPHA_BY_LEVELS.get(levels, 0.5)
+    2 levels 0.1, 3 levels 0.2, 4 levels 0.4.  The paper's tables stop at 4
+    levels and pick each shift by a search at resolution 0.1; deeper
+    hierarchies use 1.0, the value such a search gives on the layered and
+    random-field workloads with 5-7 levels."""
+    return ALPHA_BY_LEVELS.get(levels, ALPHA_DEEP)
 
 
 @dataclass

@@ -29,6 +29,10 @@ void set_error(const std::string& m) { g_err = m; }
     } while (0)
 
 static const double kAlphaByLevels[5] = {0.0, 0.0, 0.1, 0.2, 0.4};
+// deeper hierarchies than the paper's tables: the shift minimising the
+// iteration count on the layered and random-field workloads (5-7 levels),
+// searched at a resolution of 0.1 as the paper searches its shifts
+static const double kAlphaDeep = 1.0;
 static const int kIntSlots = 8;
 
 struct Ctx {
@@ -1084,7 +1088,7 @@ void bah_default_opts(bah_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->precision = BAH_MIXED;
     o->levels = 0;
-    o->max_coarse_cells = 1024;
+    o->max_coarse_cells = 256;
     o->cycle = BAH_CYCLE_V;
     o->nu_pre = 1;
     o->nu_post = 2;
@@ -1166,7 +1170,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
                 a /= 2; b /= 2; ++L;
             }
         } else {
-            const int maxc = o.max_coarse_cells > 0 ? o.max_coarse_cells : 1024;
+            const int maxc = o.max_coarse_cells > 0 ? o.max_coarse_cells : 256;
             while ((long long)a * b > maxc && a % 2 == 0 && b % 2 == 0 && a / 2 >= 2 && b / 2 >= 2) {
                 a /= 2; b /= 2; ++L;
             }
@@ -1178,7 +1182,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
         }
     }
     c.L = L;
-    c.alpha = o.shift_alpha >= 0.0 ? o.shift_alpha : (L < 5 ? kAlphaByLevels[L] : 0.5);
+    c.alpha = o.shift_alpha >= 0.0 ? o.shift_alpha : (L < 5 ? kAlphaByLevels[L] : kAlphaDeep);
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;

@@ -19,7 +19,7 @@ from oracle import elastic, fgmres, precond  # noqa: E402
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_counts.json")
 
 
-def auto_levels(n, max_coarse=1024):
+def auto_levels(n, max_coarse=256):
     L, a, b = 1, n[0], n[1]
     while a * b > max_coarse and a % 2 == 0 and b % 2 == 0 and a // 2 >= 2 and b // 2 >= 2:
         a //= 2
