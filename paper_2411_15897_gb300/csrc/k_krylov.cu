@@ -54,16 +54,30 @@ __global__ void __launch_bounds__(256) k_dot_norm_partial(const double2* __restr
     partial += r * ks.sp;
     const int y = blockIdx.y;
     double2 acc = make_double2(0.0, 0.0);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    // accumulated in element order; the loads of kU elements go out together
+    constexpr int kU = 4;
+    auto mac = [&](const double2& a, const double2& b) {
+        acc.x += a.x * b.x + a.y * b.y;
+        acc.y += a.x * b.y - a.y * b.x;
+    };
     if (y < k) {
         const double2* v = V + (size_t)y * n;
-        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-            const double2 a = v[e], b = w[e];
-            acc.x += a.x * b.x + a.y * b.y;
-            acc.y += a.x * b.y - a.y * b.x;
+        for (; e + (kU - 1) * stride < n; e += kU * stride) {
+            double2 a[kU], b[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                a[u] = __ldg(v + e + u * stride);
+                b[u] = __ldg(w + e + u * stride);
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) mac(a[u], b[u]);
         }
+        for (; e < n; e += stride) mac(__ldg(v + e), __ldg(w + e));
     } else {
-        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-            const double2 b = w[e];
+        for (; e < n; e += stride) {
+            const double2 b = __ldg(w + e);
             acc.x += b.x * b.x + b.y * b.y;
         }
     }
@@ -111,13 +125,22 @@ __global__ void __launch_bounds__(256) k_axpy_norm(const double2* __restrict__ V
     if (threadIdx.x < k) c[threadIdx.x] = coef[threadIdx.x];
     __syncthreads();
     double nn = 0.0;
+    constexpr int kU = 8;   // rows whose loads go out together
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double2 acc = w[e];
-        for (int i = 0; i < k; ++i) {
-            const double2 v = V[(size_t)i * n + e];
-            acc.x -= c[i].x * v.x - c[i].y * v.y;
-            acc.y -= c[i].x * v.y + c[i].y * v.x;
+        auto sub = [&](const double2& v, const double2& cc) {
+            acc.x -= cc.x * v.x - cc.y * v.y;
+            acc.y -= cc.x * v.y + cc.y * v.x;
+        };
+        int i = 0;
+        for (; i + kU <= k; i += kU) {
+            double2 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) v[u] = __ldg(V + (size_t)(i + u) * n + e);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) sub(v[u], c[i + u]);
         }
+        for (; i < k; ++i) sub(__ldg(V + (size_t)i * n + e), c[i]);
         w[e] = acc;
         nn += acc.x * acc.x + acc.y * acc.y;
     }

@@ -44,24 +44,45 @@ __global__ void __launch_bounds__(256) k_dot_norm_partial_df(const float4* __res
     partial += r * ks.sp;
     const int y = blockIdx.y;
     dfacc are, aim;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    // conj(a) b = (ar br + ai bi) + i (ar bi - ai br), accumulated in element
+    // order; the loads of kU elements go out together before any arithmetic
+    auto mac = [&](const float4& a, const float4& b) {
+        const dfl ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
+        are.add_prod(ar, br);
+        are.add_prod(ai, bi);
+        aim.add_prod(ar, bi);
+        aim.add_prod(df_neg(ai), br);
+    };
+    auto sq = [&](const float4& b) {
+        const dfl br = re_of(b), bi = im_of(b);
+        are.add_prod(br, br);
+        are.add_prod(bi, bi);
+    };
+    constexpr int kU = 4;
     if (y < k) {
         const float4* v = V + (size_t)y * n;
-        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-            const float4 a = v[e], b = w[e];
-            const dfl ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
-            // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
-            are.add_prod(ar, br);
-            are.add_prod(ai, bi);
-            aim.add_prod(ar, bi);
-            aim.add_prod(df_neg(ai), br);
+        for (; e + (kU - 1) * stride < n; e += kU * stride) {
+            float4 a[kU], b[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                a[u] = __ldg(v + e + u * stride);
+                b[u] = __ldg(w + e + u * stride);
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) mac(a[u], b[u]);
         }
+        for (; e < n; e += stride) mac(__ldg(v + e), __ldg(w + e));
     } else {
-        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-            const float4 b = w[e];
-            const dfl br = re_of(b), bi = im_of(b);
-            are.add_prod(br, br);
-            are.add_prod(bi, bi);
+        for (; e + (kU - 1) * stride < n; e += kU * stride) {
+            float4 b[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) b[u] = __ldg(w + e + u * stride);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) sq(b[u]);
         }
+        for (; e < n; e += stride) sq(__ldg(w + e));
     }
     double2 acc = block_sum2_df(make_double2(are.value(), aim.value()));
     if (threadIdx.x == 0) partial[(size_t)y * gridDim.x + blockIdx.x] = acc;
@@ -107,20 +128,29 @@ __global__ void __launch_bounds__(256) k_axpy_norm_df(const float4* __restrict__
     if (threadIdx.x < k) c[threadIdx.x] = cdf_from_double2(coef[threadIdx.x]);
     __syncthreads();
     dfacc nn;
+    constexpr int kU = 8;   // rows whose loads go out together
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const float4 w0 = w[e];
         dfacc xr, xi;
         xr.hi = w0.x; xr.lo = w0.y;
         xi.hi = w0.z; xi.lo = w0.w;
-        for (int i = 0; i < k; ++i) {
-            const float4 v = V[(size_t)i * n + e];
-            const dfl vr = re_of(v), vi = im_of(v), cr = re_of(c[i]), ci = im_of(c[i]);
-            // w -= c v = (cr vr - ci vi) + i (cr vi + ci vr)
+        // w -= c v = (cr vr - ci vi) + i (cr vi + ci vr), rows in order
+        auto sub = [&](const float4& v, const float4& cc) {
+            const dfl vr = re_of(v), vi = im_of(v), cr = re_of(cc), ci = im_of(cc);
             xr.add_prod(df_neg(cr), vr);
             xr.add_prod(ci, vi);
             xi.add_prod(df_neg(cr), vi);
             xi.add_prod(df_neg(ci), vr);
+        };
+        int i = 0;
+        for (; i + kU <= k; i += kU) {
+            float4 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) v[u] = __ldg(V + (size_t)(i + u) * n + e);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) sub(v[u], c[i + u]);
         }
+        for (; i < k; ++i) sub(__ldg(V + (size_t)i * n + e), c[i]);
         w[e] = make_float4(xr.hi, xr.lo, xi.hi, xi.lo);
         nn.add_prod(dfl{xr.hi, xr.lo}, dfl{xr.hi, xr.lo});
         nn.add_prod(dfl{xi.hi, xi.lo}, dfl{xi.hi, xi.lo});
