@@ -408,7 +408,10 @@ def run_bah(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
-    roof = {"kernel": KERNEL_NAMES.get(dom_id, dom), "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
+    kname = KERNEL_NAMES.get(dom_id, dom)
+    if dom == "cluster" and solver.info["cluster_level"] > 0:
+        kname = "k_cluster_mg"
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
             "unit": "GB/s", "frac": (achieved_gbs / hbm_peak) if achieved_gbs else None, "traffic": None,
             "peak_source": peak_src, "avg_launch_us": dom_ms * 1e3, "algorithmic_bytes_per_launch": dom_bytes,
             "launches_timed": dc["calls"],
@@ -423,6 +426,15 @@ def run_bah(args):
     wc = prof_all["classes"]
     tot_ms = sum(v["ms"] for v in wc.values()) or 1.0
     shares = {k: round(v["ms"] / tot_ms, 4) for k, v in sorted(wc.items(), key=lambda kv: -kv[1]["ms"])[:6]}
+    # every class in the warm-up solve: launches and device time per FGMRES step, and the
+    # achieved algorithmic bandwidth as a fraction of the measured HBM peak
+    nsteps = max(1, stats0["iters"] if isinstance(stats0, dict) else 1)
+    classes = {k: {"launches_per_step": round(v["launches"] / nsteps, 2),
+                   "us_per_step": round(1e3 * v["ms"] / nsteps, 2),
+                   "us_per_launch": round(1e3 * v["ms"] / max(v["launches"], 1), 2),
+                   "gbs": round(v["bytes"] / (v["ms"] * 1e6), 1) if v["ms"] > 0 else None,
+                   "frac_hbm": round(v["bytes"] / (v["ms"] * 1e6) / peaks.get("hbm_gbs", 6800.0), 4) if v["ms"] > 0 else None}
+               for k, v in sorted(wc.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"] > 0}
     prof_path = args.profile_json
     if rank == 0 and prof_path:
         json.dump({"warmup_all_classes": prof_all, "dominant_instrumented": prof, "timed": prof_timed,
@@ -459,6 +471,7 @@ def run_bah(args):
         "e2e": e2e,
         "gpu_launches": prof_timed["launches"],
         "kernel_shares": shares,
+        "classes_warmup_instrumented": classes,
         "roofline": roof,
         "clocks": clk,
         "cpu_baseline": cpu,
