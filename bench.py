@@ -59,7 +59,7 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA/clk/SM at the 2070 MHz max
 KERNEL_NAMES = {0: "k_elastic_apply", 1: "k_distributor", 2: "k_u_rhs", 3: "k_jacobi", 4: "k_residual",
                 5: "k_restrict", 6: "k_prolong_add", 7: "k_coarse_apply", 8: "k_dot_norm_partial",
                 9: "k_axpy_norm", 10: "k_norm2_partial", 11: "k_update_x", 12: "small kernels",
-                13: "k_coop_cycle", 14: "k_cluster_cycle"}
+                13: "k_coop_cycle", 14: "k_cluster_cycle", 15: "k_down_tiled + k_up_tiled"}
 # FP64 flops per algorithmic byte of the FP64 classes (2 flops per real FMA):
 #   dot/axpy: 8 flops per complex MAC on 16 streamed bytes; operator: ~84 flops per cell on ~200 bytes
 FP64_FLOP_PER_BYTE = {"dot": 0.5, "axpy": 0.5, "update": 8.0 / 8.0, "operator": 84.0 / 200.0}
@@ -254,7 +254,7 @@ def run_bah(args):
         return st, agg
 
     # warm-up, with every kernel class timed once to find the dominant one
-    bah.bah_profile_control(solver.ctx, (1 << 15) - 1, True)
+    bah.bah_profile_control(solver.ctx, (1 << 16) - 1, True)
     st0, stats0 = solve_once(solver, b, x)
     prof_all = bah.bah_profile_read(solver.ctx)
     for _ in range(max(0, args.warmup - 1)):

@@ -243,8 +243,9 @@ int bah_level_stencil(const bah_ctx* ctx, int block, int level, double* out, int
 #define BAH_K_UPDATE   11   /* x += Z y */
 #define BAH_K_SMALL    12   /* Givens update, triangular solve, scaling, copies, conversions */
 #define BAH_K_COOP     13   /* cooperative launch running all levels below the fine grid */
-#define BAH_K_CLUSTER  14   /* thread-block-cluster launch running the small levels of a V-cycle */
-#define BAH_NKCLASS    15
+#define BAH_K_CLUSTER  14   /* thread-block-cluster launch running the small levels of a cycle */
+#define BAH_K_TILED    15   /* tiled fused level visit: sweep + residual + restriction, prolongation + 2 sweeps */
+#define BAH_NKCLASS    16
 
 typedef struct {
     long long launches;             /* kernels launched since the last reset */

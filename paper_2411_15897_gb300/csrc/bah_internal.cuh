@@ -274,6 +274,17 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 template <int MODE>
 void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                      typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride = 0);
+// tiled fused level visit (zero initial guess, one pre- and two post-sweeps):
+// the smoothed iterate into s.blk[z].xout and R r into coarse_b; then
+// x_out = two sweeps on (x_in + P e)
+template <int MODE>
+void launch_down_tiled(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                       const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                       typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride);
+template <int MODE>
+void launch_up_tiled(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                     const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride);
 template <int MODE>
 void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                         const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride = 0);

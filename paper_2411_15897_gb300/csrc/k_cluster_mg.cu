@@ -35,14 +35,16 @@ constexpr int kSmThreads = 384;   // threads per CTA (one CTA per SM)
 
 namespace {
 
-__device__ __forceinline__ float2 ld_cluster_f2(uint32_t local_addr, unsigned rank) {
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t local_addr, unsigned rank) {
     uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float2 ld_cluster_at(uint32_t cluster_addr) {
     float2 v;
-    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(r));
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(cluster_addr));
     return v;
 }
-
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -74,12 +76,11 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
         return r1 > r0 ? (r1 - r0) * L.n1 : 0;
     };
     auto vec = [&](unsigned off) { return reinterpret_cast<V*>(sm + off); };
-    // value of vector `off` of level L at grid point (row, col), from whichever
-    // CTA owns the row (rows below 2^22: the float quotient floors exactly)
-    auto ldrc = [&](const SmLevel& L, unsigned off, int row, int col) -> V {
+    // cluster address of column 0 of grid row `row` of vector `off` of level L
+    // (one owner lookup and one mapa per row; the columns follow at 8 bytes)
+    auto row_addr = [&](const SmLevel& L, unsigned off, int row) -> uint32_t {
         const int owner = (int)(((float)row + 0.5f) * L.inv_rp);
-        const int local = (row - owner * L.rp) * L.n1 + col;
-        return ld_cluster_f2(sbase + off + (uint32_t)local * 8u, (unsigned)owner);
+        return mapa_rank(sbase + off + (uint32_t)((row - owner * L.rp) * L.n1) * 8u, (unsigned)owner);
     };
     // row and column of own point lt of level L
     auto own_rc = [&](const SmLevel& L, int lt, int& row, int& col) {
@@ -130,15 +131,17 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
         bool in[(2 * RM + 1) * (2 * RM + 1)];
 #pragma unroll
         for (int dz = -RM; dz <= RM; ++dz) {
+            const int jj = j + dz;
+            const bool rok = dz >= -rz && dz <= rz && jj >= 0 && jj < L.n2;
+            const uint32_t ra = row_addr(L, xoff, rok ? jj : j);
 #pragma unroll
             for (int dx = -RM; dx <= RM; ++dx) {
                 const int qq = (dz + RM) * (2 * RM + 1) + (dx + RM);
-                const int ii = i + dx, jj = j + dz;
-                in[qq] = dx >= -rx && dx <= rx && dz >= -rz && dz <= rz && ii >= 0 && ii < L.n1 && jj >= 0 &&
-                         jj < L.n2;
+                const int ii = i + dx;
+                in[qq] = rok && dx >= -rx && dx <= rx && ii >= 0 && ii < L.n1;
                 const int slot = in[qq] ? (dz + rz) * wx + (dx + rx) : 0;
                 sv[qq] = ldc(cs[slot * cap + lt]);
-                xv[qq] = ldrc(L, xoff, in[qq] ? jj : j, in[qq] ? ii : i);
+                xv[qq] = ld_cluster_at(ra + (uint32_t)(in[qq] ? ii : i) * 8u);
             }
         }
         V acc = czero<V>();
@@ -204,12 +207,15 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
                 }
                 V v[16];
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
+                for (int e = 0; e < 4; ++e) {
+                    const bool rok = wzs[e] != 0.f;
+                    const uint32_t ra = row_addr(L, rin, rok ? bz + e : 0);
 #pragma unroll
                     for (int f = 0; f < 4; ++f) {
-                        const bool ok = wzs[e] != 0.f && wxs[f] != 0.f;
-                        v[e * 4 + f] = ldrc(L, rin, ok ? bz + e : 0, ok ? bx + f : 0);
+                        const bool ok = rok && wxs[f] != 0.f;
+                        v[e * 4 + f] = ld_cluster_at(ra + (uint32_t)(ok ? bx + f : 0) * 8u);
                     }
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
 #pragma unroll
@@ -239,12 +245,15 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
             }
             V v[9];
 #pragma unroll
-            for (int e = 0; e < 3; ++e)
+            for (int e = 0; e < 3; ++e) {
+                const bool rok = pz[e] != 0.f;
+                const uint32_t ra = row_addr(Lc, Lc.off_x, rok ? (j >> 1) - 1 + e : 0);
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
-                    const bool ok = pz[e] != 0.f && px[f] != 0.f;
-                    v[e * 3 + f] = ldrc(Lc, Lc.off_x, ok ? (j >> 1) - 1 + e : 0, ok ? (i >> 1) - 1 + f : 0);
+                    const bool ok = rok && px[f] != 0.f;
+                    v[e * 3 + f] = ld_cluster_at(ra + (uint32_t)(ok ? (i >> 1) - 1 + f : 0) * 8u);
                 }
+            }
             V acc = x[lt];
 #pragma unroll
             for (int e = 0; e < 3; ++e)
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
         const SmLevel& L = a.lv[kc];
         const int npc = L.n1 * L.n2, own = nown(L);
         V* gath = vec(a.off_g);
-        for (int g = tid; g < npc; g += nth) gath[g] = ldrc(L, L.off_b, g / L.n1, g % L.n1);
+        for (int g = tid; g < npc; g += nth) gath[g] = ld_cluster_at(row_addr(L, L.off_b, g / L.n1) + (uint32_t)(g % L.n1) * 8u);
         __syncthreads();
         const V* inv = vec(a.off_inv);
         V* x = vec(L.off_x);

@@ -17,9 +17,9 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
     return v;
 }
 
-// block-wide sum of a double2 (blockDim.x = 256); result valid in thread 0
+// block-wide sum of a double2 (blockDim.x a multiple of 32, at most 1024); result valid in thread 0
 __device__ __forceinline__ double2 block_sum2(double2 v) {
-    __shared__ double2 sh[8];
+    __shared__ double2 sh[32];   // one per warp, up to 1024 threads
     v = warp_sum2(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) sh[w] = v;
@@ -111,7 +111,7 @@ void launch_dot_norm(const double2* V, int k, const double2* w, size_t n, double
 }
 
 // w -= sum_i coef[i] V_i, and per-CTA partial sums of |w_new|^2
-__global__ void __launch_bounds__(256) k_axpy_norm(const double2* __restrict__ V, int k,
+__global__ void __launch_bounds__(512) k_axpy_norm(const double2* __restrict__ V, int k,
                                                    const double2* __restrict__ coef, double2* __restrict__ w, size_t n,
                                                    double* __restrict__ npart, const int* flag, KS ks) {
     pdl_prologue();
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_axpy_norm(const double2* __restrict__ V
 }
 void launch_axpy_norm(const double2* V, int k, const double2* coef, double2* w, size_t n, double* npart,
                       const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    launch_pdl(k_axpy_norm, dim3(dim3(RED_CTAS, 1, nrhs)), dim3(256), 0, st, V, k, coef, w, n, npart, flag, ks);
+    launch_pdl(k_axpy_norm, dim3(dim3(RED_CTAS, 1, nrhs)), dim3(512), 0, st, V, k, coef, w, n, npart, flag, ks);
 }
 
 // reduce the pass-1 norm, decide on the second pass, set ||w|| for the Givens

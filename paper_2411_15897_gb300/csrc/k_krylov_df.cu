@@ -17,7 +17,7 @@ __device__ __forceinline__ double2 warp_sum2_df(double2 v) {
     return v;
 }
 __device__ __forceinline__ double2 block_sum2_df(double2 v) {
-    __shared__ double2 sh[8];
+    __shared__ double2 sh[32];   // one per warp, up to 1024 threads
     v = warp_sum2_df(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) sh[w] = v;
@@ -114,7 +114,7 @@ void launch_dot_norm_df(const float4* V, int k, const float4* w, size_t n, doubl
 }
 
 // w -= sum_i coef[i] V_i (coef FP64, split once per CTA), per-CTA |w_new|^2
-__global__ void __launch_bounds__(256) k_axpy_norm_df(const float4* __restrict__ V, int k,
+__global__ void __launch_bounds__(512) k_axpy_norm_df(const float4* __restrict__ V, int k,
                                                       const double2* __restrict__ coef, float4* __restrict__ w,
                                                       size_t n, double* __restrict__ npart, const int* flag, KS ks) {
     pdl_prologue();
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_axpy_norm_df(const float4* __restrict__
 }
 void launch_axpy_norm_df(const float4* V, int k, const double2* coef, float4* w, size_t n, double* npart,
                          const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    launch_pdl(k_axpy_norm_df, dim3(dim3(RED_CTAS, 1, nrhs)), dim3(256), 0, st, V, k, coef, w, n, npart, flag, ks);
+    launch_pdl(k_axpy_norm_df, dim3(dim3(RED_CTAS, 1, nrhs)), dim3(512), 0, st, V, k, coef, w, n, npart, flag, ks);
 }
 
 // v = w / sc[slot]: from a double-float w, or (from64) from an FP64 vector

@@ -101,6 +101,7 @@ struct Ctx {
     std::vector<cudaEvent_t> itev;
     bool use_graphs = true;
     bool fused = false;                  // fused multigrid kernels (BAH_FUSED=1) when nu_pre == 1 and nu_post >= 1
+    bool tiled = true;                   // tiled fused level visits (BAH_TILED=0 turns them off)
     // cooperative cycle over levels 1..L-1 (one launch per block set)
     bool coop = false;                   // opt-in (BAH_COOP=1): measured slower than separate launches
     int cl_l0 = 0;                       // first level run by the cluster kernel (0: off)
@@ -432,7 +433,31 @@ struct MG {
         V* cx[3];
         for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
         const bool wcyc = c.o.cycle == BAH_CYCLE_W;
-        if (bt.nr == 1 && c.fused && !wcyc && !x0 && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
+        const bool tiled = c.tiled && !x0 && c.o.nu_pre == 1 && c.o.nu_post == 2 && c.ln1[l] >= 8 && c.ln2[l] >= 8;
+        if (tiled && !(bt.nr == 1 && c.fused)) {
+            // one launch for the zero-guess sweep, the residual and the
+            // restriction (smoothed iterate into oth), one for the prolongation
+            // and the two post-sweeps (oth + P e -> cur)
+            {
+                Prof pr(c, BAH_K_TILED, st, nr * nb * npl * (vs * 2.25 + (double)ccs) + cb_);
+                launch_down_tiled<MODE>(set(c, l, b0, nb, nullptr, 0, oth, oth_s, bt), pf5, w, cb, c.o.intergrid, st,
+                                        nplc);
+            }
+            if (c.sm_l0 == l + 1) {
+                smem_levels(c, b0, nb, bt, st);
+                if (wcyc && l + 1 < c.L - 1) smem_levels(c, b0, nb, bt, st, true);
+            } else if (c.cl_l0 == l + 1) {
+                cluster_levels(c, b0, nb, bt, st);
+                if (wcyc && l + 1 < c.L - 1) cluster_levels(c, b0, nb, bt, st, true);
+            } else {
+                cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
+                if (wcyc && l + 1 < c.L - 1) cycle(c, l + 1, b0, nb, cx, nplc, bt, st, true);
+            }
+            {
+                Prof pr(c, BAH_K_TILED, st, nr * nb * npl * vs * 3.25 + 2.0 * cb_);
+                launch_up_tiled<MODE>(set(c, l, b0, nb, oth, oth_s, cur, cur_s, bt), pf5, w, cx, st, nplc);
+            }
+        } else if (bt.nr == 1 && c.fused && !wcyc && !x0 && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
             // pre-smoothing + residual + restriction in one launch
             {
                 Prof pr(c, BAH_K_RESTRICT, st, cb_ + nb * npl * vs * 2.25);
@@ -800,6 +825,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     for (int j = 0; j < m; ++j) BAH_CUDA_TRY(cudaEventCreateWithFlags(&c.itev[j], cudaEventDisableTiming));
     if (const char* e = getenv("BAH_NO_GRAPHS")) c.use_graphs = (e[0] == '0');
     if (const char* e = getenv("BAH_FUSED")) c.fused = (e[0] == '1');
+    if (const char* e = getenv("BAH_TILED")) c.tiled = (e[0] != '0');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
     return BAH_OK;

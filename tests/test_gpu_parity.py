@@ -342,11 +342,12 @@ def test_profile_counters(systems):
     """Launch and byte counters advance and timed classes report device time."""
     p, S = get("c1", systems)
     s = bah.Solver.from_problem(p, maxit=5)
-    bah.bah_profile_control(s.ctx, 1 << 3, True)
+    tiled = bah.BAH_K_NAMES.index("tiled")
+    bah.bah_profile_control(s.ctx, 1 << tiled, True)
     s.solve(to_dev(W.point_source(p)))
     pr = bah.bah_profile_read(s.ctx)
-    assert pr["launches"] > 5 * 20
-    assert pr["classes"]["jacobi"]["ms"] > 0 and pr["classes"]["jacobi"]["bytes"] > 0
+    assert pr["launches"] > 5 * 10
+    assert pr["classes"]["tiled"]["ms"] > 0 and pr["classes"]["tiled"]["bytes"] > 0
     assert pr["classes"]["dot"]["ms"] == 0
     s.close()
 
@@ -436,6 +437,7 @@ def test_cluster_path_is_taken(systems, monkeypatch):
     preconditioner application and no separate kernels run on the levels it
     covers."""
     monkeypatch.setenv("BAH_CLUSTER", "1")
+    monkeypatch.setenv("BAH_TILED", "0")
     p, S = get("layered_64x32", systems)
     s = bah.Solver.from_problem(p, levels=3)
     bah.bah_profile_control(s.ctx, 0, True)
@@ -492,6 +494,34 @@ def test_smem_cluster_multigrid_matches_separate_kernels(cycle, levels, monkeypa
     for k in range(5):
         bc = W.padded_to_compact(b[k], p.n)
         assert np.linalg.norm(bc - S.H @ W.padded_to_compact(xh[k], p.n)) / np.linalg.norm(bc) <= 1e-7
+
+
+@pytest.mark.parametrize("prec", [bah.BAH_FP64, bah.BAH_MIXED])
+@pytest.mark.parametrize("cycle", [bah.BAH_CYCLE_V, bah.BAH_CYCLE_W])
+@pytest.mark.parametrize("name", ["random_48x40", "layered_64x32"])
+def test_tiled_level_visits_match_separate_kernels(prec, cycle, name, systems, monkeypatch):
+    """A zero-guess V(1,2)/W(1,2) level visit runs as two tiled launches (sweep +
+    residual + restriction; prolongation + two sweeps) by default, and as six
+    separate launches with BAH_TILED=0.  Same per-point arithmetic: the
+    preconditioner agrees to rounding, including tiles cut by the grid edge
+    (48x40, 24x20 fine grids on 32x16 tiles), and matches the oracle."""
+    p, S = get(name, systems)
+    r = W.random_vector(p.n, 43)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("BAH_TILED", mode)
+        s = bah.Solver.from_problem(p, precision=prec, levels=3, cycle=cycle)
+        bah.bah_profile_control(s.ctx, 0, True)
+        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
+        pr = bah.bah_profile_read(s.ctx)
+        assert (pr["classes"]["tiled"]["calls"] > 0) == (mode == "1")
+        s.close()
+    tol = 1e-12 if prec == bah.BAH_FP64 else 1e-6
+    assert rel(out["1"], out["0"]) <= tol, rel(out["1"], out["0"])
+    pc = precond.multigrid(S, 3, precond.default_alpha(3), precision="fp64" if prec == bah.BAH_FP64 else "mixed",
+                           cycle="W" if cycle == bah.BAH_CYCLE_W else "V")
+    ref = pc.apply(W.padded_to_compact(r, p.n))
+    assert rel(W.padded_to_compact(out["1"], p.n), ref) <= (1e-10 if prec == bah.BAH_FP64 else 2e-4)
 
 
 # ----------------------------------------------------------------------------
