@@ -32,10 +32,7 @@ __device__ __forceinline__ double2 block_sum2_df(double2 v) {
 }
 __device__ __forceinline__ bool inactive_df(const KS& ks, int r) { return ks.active && !ks.active[r]; }
 
-// rows 0..k-1: conj(V_y) w; row k: |w|^2.  Each CTA serves kDotRows rows
-// of one element chunk, so w is read once per kDotRows rows; every row is
-// accumulated in element order.
-constexpr int kDotRows = 4;
+// rows 0..k-1: conj(V_y) w; row k: |w|^2
 __global__ void __launch_bounds__(256) k_dot_norm_partial_df(const float4* __restrict__ V, int k,
                                                              const float4* __restrict__ w, size_t n,
                                                              double2* __restrict__ partial, const int* flag, KS ks) {
@@ -45,48 +42,50 @@ __global__ void __launch_bounds__(256) k_dot_norm_partial_df(const float4* __res
     V += r * ks.sv;
     w += r * ks.sw;
     partial += r * ks.sp;
-    const int y0 = blockIdx.y * kDotRows;
-    dfacc are[kDotRows], aim[kDotRows];
-    const float4* v[kDotRows];
-    bool isv[kDotRows], isn[kDotRows];
-#pragma unroll
-    for (int u = 0; u < kDotRows; ++u) {
-        const int y = y0 + u;
-        isv[u] = y < k;
-        isn[u] = y == k;
-        v[u] = V + (size_t)(isv[u] ? y : 0) * n;
-    }
-    // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
-    auto mac = [&](int u, const float4& a, const float4& b) {
-        const dfl ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
-        are[u].add_prod(ar, br);
-        are[u].add_prod(ai, bi);
-        aim[u].add_prod(ar, bi);
-        aim[u].add_prod(df_neg(ai), br);
-    };
-    auto sq = [&](int u, const float4& b) {
-        const dfl br = re_of(b), bi = im_of(b);
-        are[u].add_prod(br, br);
-        are[u].add_prod(bi, bi);
-    };
+    const int y = blockIdx.y;
+    dfacc are, aim;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-        const float4 b = __ldg(w + e);
-        float4 a[kDotRows];
+    size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    // conj(a) b = (ar br + ai bi) + i (ar bi - ai br), accumulated in element
+    // order; the loads of kU elements go out together before any arithmetic
+    auto mac = [&](const float4& a, const float4& b) {
+        const dfl ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
+        are.add_prod(ar, br);
+        are.add_prod(ai, bi);
+        aim.add_prod(ar, bi);
+        aim.add_prod(df_neg(ai), br);
+    };
+    auto sq = [&](const float4& b) {
+        const dfl br = re_of(b), bi = im_of(b);
+        are.add_prod(br, br);
+        are.add_prod(bi, bi);
+    };
+    constexpr int kU = 4;
+    if (y < k) {
+        const float4* v = V + (size_t)y * n;
+        for (; e + (kU - 1) * stride < n; e += kU * stride) {
+            float4 a[kU], b[kU];
 #pragma unroll
-        for (int u = 0; u < kDotRows; ++u) a[u] = isv[u] ? __ldg(v[u] + e) : b;
+            for (int u = 0; u < kU; ++u) {
+                a[u] = __ldg(v + e + u * stride);
+                b[u] = __ldg(w + e + u * stride);
+            }
 #pragma unroll
-        for (int u = 0; u < kDotRows; ++u) {
-            if (isv[u]) mac(u, a[u], b);
-            else if (isn[u]) sq(u, b);
+            for (int u = 0; u < kU; ++u) mac(a[u], b[u]);
         }
-    }
+        for (; e < n; e += stride) mac(__ldg(v + e), __ldg(w + e));
+    } else {
+        for (; e + (kU - 1) * stride < n; e += kU * stride) {
+            float4 b[kU];
 #pragma unroll
-    for (int u = 0; u < kDotRows; ++u) {
-        if (y0 + u > k) break;                        // uniform over the CTA
-        const double2 acc = block_sum2_df(make_double2(are[u].value(), aim[u].value()));
-        if (threadIdx.x == 0) partial[(size_t)(y0 + u) * gridDim.x + blockIdx.x] = acc;
+            for (int u = 0; u < kU; ++u) b[u] = __ldg(w + e + u * stride);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) sq(b[u]);
+        }
+        for (; e < n; e += stride) sq(__ldg(w + e));
     }
+    double2 acc = block_sum2_df(make_double2(are.value(), aim.value()));
+    if (threadIdx.x == 0) partial[(size_t)y * gridDim.x + blockIdx.x] = acc;
 }
 __global__ void __launch_bounds__(256) k_reduce_rows_df(const double2* __restrict__ partial, int np, double2* out,
                                                         const int* flag, KS ks) {
@@ -110,8 +109,7 @@ __global__ void __launch_bounds__(256) k_reduce_rows_df(const double2* __restric
 }
 void launch_dot_norm_df(const float4* V, int k, const float4* w, size_t n, double2* partial, double2* out,
                         const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    launch_pdl(k_dot_norm_partial_df, dim3(dim3(RED_CTAS, (k + kDotRows) / kDotRows, nrhs)), dim3(256), 0, st, V, k, w, n,
-               partial, flag, ks);
+    launch_pdl(k_dot_norm_partial_df, dim3(dim3(RED_CTAS, k + 1, nrhs)), dim3(256), 0, st, V, k, w, n, partial, flag, ks);
     launch_pdl(k_reduce_rows_df, dim3(dim3(1, k + 1, nrhs)), dim3(256), 0, st, partial, RED_CTAS, out, flag, ks);
 }
 
