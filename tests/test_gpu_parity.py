@@ -338,16 +338,18 @@ def test_graph_and_direct_launch_paths_agree(systems, monkeypatch):
     s2.close()
 
 
-def test_profile_counters(systems):
-    """Launch and byte counters advance and timed classes report device time."""
+@pytest.mark.parametrize("cls,env", [("jacobi", "0"), ("tiled", "1")])
+def test_profile_counters(cls, env, systems, monkeypatch):
+    """Launch and byte counters advance and timed classes report device time
+    (separate level kernels by default; tiled level visits with BAH_TILED=1)."""
+    monkeypatch.setenv("BAH_TILED", env)
     p, S = get("c1", systems)
     s = bah.Solver.from_problem(p, maxit=5)
-    tiled = bah.BAH_K_NAMES.index("tiled")
-    bah.bah_profile_control(s.ctx, 1 << tiled, True)
+    bah.bah_profile_control(s.ctx, 1 << bah.BAH_K_NAMES.index(cls), True)
     s.solve(to_dev(W.point_source(p)))
     pr = bah.bah_profile_read(s.ctx)
     assert pr["launches"] > 5 * 10
-    assert pr["classes"]["tiled"]["ms"] > 0 and pr["classes"]["tiled"]["bytes"] > 0
+    assert pr["classes"][cls]["ms"] > 0 and pr["classes"][cls]["bytes"] > 0
     assert pr["classes"]["dot"]["ms"] == 0
     s.close()
 
@@ -501,8 +503,8 @@ def test_smem_cluster_multigrid_matches_separate_kernels(cycle, levels, monkeypa
 @pytest.mark.parametrize("name", ["random_48x40", "layered_64x32"])
 def test_tiled_level_visits_match_separate_kernels(prec, cycle, name, systems, monkeypatch):
     """A zero-guess V(1,2)/W(1,2) level visit runs as two tiled launches (sweep +
-    residual + restriction; prolongation + two sweeps) by default, and as six
-    separate launches with BAH_TILED=0.  Same per-point arithmetic: the
+    residual + restriction; prolongation + two sweeps) with BAH_TILED=1, and as
+    six separate launches by default.  Same per-point arithmetic: the
     preconditioner agrees to rounding, including tiles cut by the grid edge
     (48x40, 24x20 fine grids on 32x16 tiles), and matches the oracle."""
     p, S = get(name, systems)
