@@ -128,6 +128,15 @@ struct OpCoef {
     double ihx, ihz;     // 1/h1, 1/h2
 };
 
+// the same coefficients as double-float pairs (hi, lo), for the operator
+// applied to FP32 vectors in double-float arithmetic
+struct OpCoefDF {
+    int n1, n2;
+    const float2 *cx, *cz, *nx, *nz, *cinv;
+    const float4 *d1, *d2;
+    float2 ihx, ihz;
+};
+
 // ---------------------------------------------------------------------------
 // multigrid level-0 (fine) operators: 5-point stencils from per-point arrays
 // (Eq. 2.6 blocks with the shift of Eq. 2.8; H_p,s of Eq. 3.4; A_p of Eq. 3.2)
@@ -262,6 +271,11 @@ void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const doubl
 // y = H x written as double-float (float4) for the double-float Krylov basis
 template <class Vin>
 void launch_elastic_apply_df(const OpCoef& c, const Vin* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs);
+// y = H x for FP32 x in double-float arithmetic (no FP64 instructions), y as double-float
+void launch_elastic_apply_dfa(const OpCoefDF& c, const float2* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs);
+// FP64 arrays to double-float pairs
+void launch_to_df(const double* src, float2* dst, size_t n, cudaStream_t st);
+void launch_to_df_c(const double2* src, float4* dst, size_t n, cudaStream_t st);
 
 // multigrid (k_mg.cu)
 template <int MODE>

@@ -67,6 +67,21 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
     return df_renorm(p, e);
 }
 
+// a (double-float) times a float, to about 2^-47 relative
+__device__ __forceinline__ dfl df_mul_f(dfl a, float x) {
+    const float p = a.hi * x;
+    float e = fmaf(a.hi, x, -p);
+    e = fmaf(a.lo, x, e);
+    return df_renorm(p, e);
+}
+// a - b for two floats, exactly, as a double-float
+__device__ __forceinline__ dfl df_diff_f(float a, float b) {
+    dfl r;
+    two_sum(a, -b, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ dfl df_of(const float2& v) { dfl r; r.hi = v.x; r.lo = v.y; return r; }
+
 // accumulator for long sums: acc += a*b, renormalised on every step
 struct dfacc {
     float hi = 0.f, lo = 0.f;

@@ -103,6 +103,111 @@ __global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __re
     st_out(y, 2 * np + t, yp);
 }
 
+// ---------------------------------------------------------------------------
+// y = H x for an FP32 x (the flexible basis in mixed mode), in double-float
+// arithmetic: every coefficient is a double-float pair, every product an
+// error-free FP32 product (FMA) and every sum a two-sum, so the result matches
+// the FP64 kernel to about 2^-47 relative without FP64 instructions.  Same
+// stencil as k_elastic_apply (Eq. 2.6), y = H x only.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_elastic_apply_dfa(OpCoefDF c, const float2* __restrict__ x,
+                                                           float4* __restrict__ y, RhsStride rs) {
+    pdl_prologue();
+    const int n1 = c.n1, n2 = c.n2, np = n1 * n2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rr = blockIdx.y;
+    if (t >= np || (rs.active && !rs.active[rr])) return;
+    x += rr * rs.s0;
+    y += rr * rs.s1;
+    const int i = t % n1, j = t / n1;
+    const float2* x1 = x;
+    const float2* x2 = x + np;
+    const float2* xp = x + 2 * np;
+    const float2 z = make_float2(0.f, 0.f);
+    auto U1 = [&](int ii, int jj) { return (ii >= 1 && ii < n1 && jj >= 0 && jj < n2) ? x1[jj * n1 + ii] : z; };
+    auto U2 = [&](int ii, int jj) { return (ii >= 0 && ii < n1 && jj >= 1 && jj < n2) ? x2[jj * n1 + ii] : z; };
+    const float2 p = xp[t];
+    const dfl ihx = df_of(c.ihx), ihz = df_of(c.ihz);
+    const dfl zero = {0.f, 0.f};
+    // acc -= k v (k real double-float, v complex float)
+    auto sub_kv = [&](dfacc& ar, dfacc& ai, dfl k, float2 v) {
+        ar.add(df_neg(df_mul_f(k, v.x)));
+        ai.add(df_neg(df_mul_f(k, v.y)));
+    };
+    float4 y1 = make_float4(0.f, 0.f, 0.f, 0.f), y2 = y1;
+    if (i >= 1) {
+        // u1 row: (diagonal) u - neighbours + (grad_h p)_1
+        const float2 u = U1(i, j);
+        const float4 d = c.d1[t];
+        const dfl dr = re_of(d), di = im_of(d);
+        dfacc ar, ai;
+        ar.add(df_mul_f(dr, u.x));
+        ar.add(df_neg(df_mul_f(di, u.y)));
+        ai.add(df_mul_f(dr, u.y));
+        ai.add(df_mul_f(di, u.x));
+        sub_kv(ar, ai, df_of(c.cx[t - 1]), U1(i - 1, j));
+        sub_kv(ar, ai, df_of(c.cx[t]), U1(i + 1, j));
+        sub_kv(ar, ai, df_of(c.nz[t]), U1(i, j - 1));
+        sub_kv(ar, ai, (j + 1 < n2) ? df_of(c.nz[t + n1]) : zero, U1(i, j + 1));
+        const float2 pw = xp[t - 1];
+        ar.add(df_mul(ihx, df_diff_f(p.x, pw.x)));
+        ai.add(df_mul(ihx, df_diff_f(p.y, pw.y)));
+        y1 = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+    }
+    if (j >= 1) {
+        const float2 u = U2(i, j);
+        const float4 d = c.d2[t];
+        const dfl dr = re_of(d), di = im_of(d);
+        dfacc ar, ai;
+        ar.add(df_mul_f(dr, u.x));
+        ar.add(df_neg(df_mul_f(di, u.y)));
+        ai.add(df_mul_f(dr, u.y));
+        ai.add(df_mul_f(di, u.x));
+        sub_kv(ar, ai, df_of(c.cz[t - n1]), U2(i, j - 1));
+        sub_kv(ar, ai, df_of(c.cz[t]), U2(i, j + 1));
+        sub_kv(ar, ai, df_of(c.nx[t]), U2(i - 1, j));
+        sub_kv(ar, ai, (i + 1 < n1) ? df_of(c.nx[t + 1]) : zero, U2(i + 1, j));
+        const float2 ps = xp[t - n1];
+        ar.add(df_mul(ihz, df_diff_f(p.x, ps.x)));
+        ai.add(df_mul(ihz, df_diff_f(p.y, ps.y)));
+        y2 = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+    }
+    // p row: B u - C p
+    const float2 u1c = U1(i, j), u1e = U1(i + 1, j), u2c = U2(i, j), u2n = U2(i, j + 1);
+    const dfl ci = df_of(c.cinv[t]);
+    dfacc pr, pi;
+    pr.add(df_mul(ihx, df_diff_f(u1c.x, u1e.x)));
+    pr.add(df_mul(ihz, df_diff_f(u2c.x, u2n.x)));
+    pr.add(df_neg(df_mul_f(ci, p.x)));
+    pi.add(df_mul(ihx, df_diff_f(u1c.y, u1e.y)));
+    pi.add(df_mul(ihz, df_diff_f(u2c.y, u2n.y)));
+    pi.add(df_neg(df_mul_f(ci, p.y)));
+    y[t] = y1;
+    y[np + t] = y2;
+    y[2 * np + t] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+}
+void launch_elastic_apply_dfa(const OpCoefDF& c, const float2* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs) {
+    const int np = c.n1 * c.n2;
+    launch_pdl(k_elastic_apply_dfa, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, c, x, y, rs);
+}
+__global__ void k_to_df(const double* __restrict__ s, float2* __restrict__ d, size_t n) {
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (e < n) {
+        const dfl v = df_from_double(s[e]);
+        d[e] = make_float2(v.hi, v.lo);
+    }
+}
+__global__ void k_to_df_c(const double2* __restrict__ s, float4* __restrict__ d, size_t n) {
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (e < n) d[e] = cdf_from_double2(s[e]);
+}
+void launch_to_df(const double* src, float2* dst, size_t n, cudaStream_t st) {
+    k_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+}
+void launch_to_df_c(const double2* src, float4* dst, size_t n, cudaStream_t st) {
+    k_to_df_c<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+}
+
 template <class Vin>
 void launch_elastic_apply(const OpCoef& c, const Vin* x, double2* y, const double2* b, int conj, cudaStream_t st,
                           int nrhs, RhsStride rs) {

@@ -49,6 +49,8 @@ struct Ctx {
     double2 *d1 = nullptr, *d2 = nullptr, *dg[3] = {nullptr, nullptr, nullptr}, *dAp = nullptr;
     double* gam = nullptr;               // attenuation at cells (device), for the gradient
     OpCoef op{};
+    OpCoefDF opdf{};                     // double-float copies (mixed mode with the double-float basis)
+    bool opdf_ok = false;
     // level-0 arrays in storage precision
     void *s_cx = nullptr, *s_cz = nullptr, *s_nx = nullptr, *s_nz = nullptr, *s_wx = nullptr, *s_wz = nullptr;
     void *s_dg[3] = {nullptr, nullptr, nullptr}, *s_dAp = nullptr;
@@ -589,7 +591,8 @@ static void op_apply_z(Ctx& c, const void* z, size_t zstride, void* y, size_t ys
     RhsStride rs;
     rs.s0 = zstride; rs.s1 = ystride; rs.active = bt.active;
     if (c.kdf) {
-        if (c.mode == BAH_MIXED) launch_elastic_apply_df<float2>(c.op, (const float2*)z, (float4*)y, st, bt.nr, rs);
+        if (c.mode == BAH_MIXED && c.opdf_ok) launch_elastic_apply_dfa(c.opdf, (const float2*)z, (float4*)y, st, bt.nr, rs);
+        else if (c.mode == BAH_MIXED) launch_elastic_apply_df<float2>(c.op, (const float2*)z, (float4*)y, st, bt.nr, rs);
         else launch_elastic_apply_df<double2>(c.op, (const double2*)z, (float4*)y, st, bt.nr, rs);
     } else {
         if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
@@ -619,6 +622,45 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
                        c.wz, c.d1, c.d2, c.cinv, c.dg[0], c.dg[1], c.dg[2], c.dAp, st);
     BAH_CUDA_TRY(cudaGetLastError());
     c.op = OpCoef{c.n1, c.n2, c.cx, c.cz, c.nx, c.nz, c.d1, c.d2, c.cinv, 1.0 / c.h1, 1.0 / c.h2};
+    // double-float copies of the operator coefficients for w = H z in mixed mode
+    // with the double-float Krylov basis (BAH_OP_F64=1 keeps the FP64 kernel)
+    {
+        bool on = c.mode == BAH_MIXED && c.kdf;
+        if (const char* e = getenv("BAH_OP_F64")) on = on && e[0] != '1';
+        if (on) {
+            const size_t np = c.np;
+            auto conv = [&](const double* src, const float2** dst, const double* alias_of, const float2* alias_dst) {
+                if (src == alias_of && alias_dst) { *dst = alias_dst; return BAH_OK; }
+                float2* d = nullptr;
+                TRY(c.alloc_t(&d, np));
+                launch_to_df(src, d, np, st);
+                *dst = d;
+                return BAH_OK;
+            };
+            OpCoefDF& o = c.opdf;
+            o.n1 = c.n1; o.n2 = c.n2;
+            TRY(conv(c.cx, &o.cx, nullptr, nullptr));
+            TRY(conv(c.nx, &o.nx, nullptr, nullptr));
+            TRY(conv(c.cz, &o.cz, c.cx, o.cx));
+            TRY(conv(c.nz, &o.nz, c.nx, o.nx));
+            TRY(conv(c.cinv, &o.cinv, nullptr, nullptr));
+            float4* d1 = nullptr;
+            float4* d2 = nullptr;
+            TRY(c.alloc_t(&d1, np));
+            TRY(c.alloc_t(&d2, np));
+            launch_to_df_c(c.d1, d1, np, st);
+            launch_to_df_c(c.d2, d2, np, st);
+            o.d1 = d1; o.d2 = d2;
+            auto dfh = [](double v) {
+                const float hi = (float)v;
+                return make_float2(hi, (float)(v - (double)hi));
+            };
+            o.ihx = dfh(1.0 / c.h1);
+            o.ihz = dfh(1.0 / c.h2);
+            BAH_CUDA_TRY(cudaGetLastError());
+            c.opdf_ok = true;
+        }
+    }
 
     // level-0 coefficients in storage precision
     const bool iso = c.h1 == c.h2;

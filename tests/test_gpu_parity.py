@@ -526,6 +526,34 @@ def test_tiled_level_visits_match_separate_kernels(prec, cycle, name, systems, m
     assert rel(W.padded_to_compact(out["1"], p.n), ref) <= (1e-10 if prec == bah.BAH_FP64 else 2e-4)
 
 
+def test_double_float_operator_in_fgmres(monkeypatch):
+    """In mixed mode with the double-float basis, w = H z is formed in
+    double-float arithmetic (about 2^-47 relative).  An operator that is only
+    FP32-accurate would make the Arnoldi residual estimate drift from the true
+    residual by ~1e-7 relative to ||b||, i.e. ~10% at convergence; here the two
+    agree to 1e-3 relative, the iteration count equals the FP64-operator
+    run's to within 2, and the true residual (recomputed by the oracle's
+    assembled operator) meets the tolerance."""
+    p = W.layered(128, 64, 5, seed=29, abc=8)
+    S = elastic.from_problem(p)
+    b = W.point_source(p)
+    bc = W.padded_to_compact(b, p.n)
+    res = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("BAH_OP_F64", mode)
+        s = bah.Solver.from_problem(p, krylov_arith=bah.BAH_KRYLOV_DF, maxit=20000)
+        x, status, st = s.solve(to_dev(b), rtol=1e-7)
+        assert status == bah.BAH_OK, st
+        xc = W.padded_to_compact(to_host(x), p.n)
+        rr = np.linalg.norm(bc - S.H @ xc) / np.linalg.norm(bc)
+        assert rr <= 1e-7
+        res[mode] = st[0]
+        s.close()
+    q = res["0"]
+    assert abs(q["relres_est"] - q["relres_true"]) <= 1e-3 * q["relres_true"], q
+    assert abs(res["0"]["iters"] - res["1"]["iters"]) <= 2, res
+
+
 # ----------------------------------------------------------------------------
 # batched right-hand sides
 # ----------------------------------------------------------------------------
