@@ -6,6 +6,7 @@
 // problem, the triangular solve and the solution update x += Z y.
 // A right-hand side whose active flag is 0 is skipped by every kernel.
 #include "bah_internal.cuh"
+#include "df.cuh"
 
 namespace bah {
 
@@ -244,6 +245,50 @@ __global__ void __launch_bounds__(256) k_update_x(const Vz* __restrict__ Z, cons
             acc.x += c[i].x * zx - c[i].y * zy;
             acc.y += c[i].x * zy + c[i].y * zx;
         }
+        x[e] = acc;
+    }
+}
+// FP32 Z (mixed mode): the k products in double-float arithmetic (y split
+// once per CTA into double-float pairs, every product an error-free FP32
+// product, every sum a two-sum), added to the FP64 x once per element; the
+// loads of kU rows go out together
+template <>
+__global__ void __launch_bounds__(256) k_update_x<float2>(const float2* __restrict__ Z, const int* kk,
+                                                          const double2* __restrict__ y, double2* __restrict__ x,
+                                                          size_t n, KS ks) {
+    pdl_prologue();
+    const int r = blockIdx.y;
+    const int k = kk[r];
+    if (k <= 0) return;
+    Z += r * ks.sz;
+    y += r * ks.so;
+    x += r * ks.sx;
+    __shared__ float4 c[64];
+    if (threadIdx.x < k) c[threadIdx.x] = cdf_from_double2(y[threadIdx.x]);
+    __syncthreads();
+    constexpr int kU = 8;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        dfacc ar, ai;
+        auto mac = [&](const float2& zv, const float4& cc) {
+            // (cr + i ci)(zx + i zy) = (cr zx - ci zy) + i (cr zy + ci zx)
+            const dfl cr = re_of(cc), ci = im_of(cc);
+            ar.add(df_mul_f(cr, zv.x));
+            ar.add(df_neg(df_mul_f(ci, zv.y)));
+            ai.add(df_mul_f(cr, zv.y));
+            ai.add(df_mul_f(ci, zv.x));
+        };
+        int i = 0;
+        for (; i + kU <= k; i += kU) {
+            float2 zv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) zv[u] = __ldg(Z + (size_t)(i + u) * n + e);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) mac(zv[u], c[i + u]);
+        }
+        for (; i < k; ++i) mac(__ldg(Z + (size_t)i * n + e), c[i]);
+        double2 acc = x[e];
+        acc.x += ar.value();
+        acc.y += ai.value();
         x[e] = acc;
     }
 }
