@@ -165,6 +165,7 @@ template <class V, class CC> struct LvlSet {
     LvlBlk<V, CC> blk[3];
     int nrhs;          // right-hand sides in the launch (blockIdx.z)
     const int* active; // per right-hand side, or nullptr
+    int staged;        // Galerkin-level sweeps may stage their inputs in shared memory
 };
 
 // device-resident descriptor of one multigrid level for the cooperative cycle

@@ -247,6 +247,91 @@ void launch_prolong_smooth(const LvlSet<typename Prec<MODE>::V, typename Prec<MO
     else k_prolong_smooth<MODE, false, 2><<<g, 256, 0, st>>>(s, nof, (R)w, ce);
 }
 
+// ---------------------------------------------------------------------------
+// Jacobi sweep (RES = false) or residual (RES = true) on a Galerkin level with
+// the CTA's inputs staged in shared memory first: every stencil coefficient of
+// its 256 points and the iterate over the points' rows plus RM rows on each
+// side are requested with asynchronous copies (cp.async) before any is used,
+// so the number of loads in flight no longer depends on how many registers
+// the compiler keeps for them.  Arithmetic as in k_jacobi / k_residual.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+template <class T>
+__device__ __forceinline__ void cpa(T* dst, const T* src) {
+    if constexpr (sizeof(T) == 4) cpa4(dst, src);
+    else if constexpr (sizeof(T) == 8) cpa8(dst, src);
+    else cpa16(dst, src);
+}
+
+template <int MODE, int RM, bool RES>
+__global__ void __launch_bounds__(256) k_stencil_staged(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
+                                                        typename MGT<MODE>::R w) {
+    pdl_prologue();
+    using V = typename MGT<MODE>::V;
+    using CC = typename MGT<MODE>::CC;
+    const auto& B = s.blk[blockIdx.y];
+    const int n1 = s.n1, n2 = s.n2, np = n1 * n2;
+    const int rr = blockIdx.z;
+    if (s.active && !s.active[rr]) return;              // uniform over the CTA
+    const int t0 = blockIdx.x * 256;
+    const int nsl = (2 * B.rx + 1) * (2 * B.rz + 1);
+    const int halo = RM * n1 + RM;
+    const int xbase = t0 - halo, xlen = 256 + 2 * halo;
+    extern __shared__ __align__(16) unsigned char stage_raw[];
+    V* xs = reinterpret_cast<V*>(stage_raw);
+    CC* cs = reinterpret_cast<CC*>(stage_raw + (size_t)xlen * sizeof(V));
+    const V* __restrict__ xin = B.xin + rr * B.sxi;
+    for (int e = threadIdx.x; e < xlen; e += 256) {
+        const int g = xbase + e;
+        if (g >= 0 && g < np) cpa(xs + e, xin + g);
+    }
+    for (int e = threadIdx.x; e < nsl * 256; e += 256) {
+        const int g = t0 + (e & 255);
+        if (g < np) cpa(cs + e, B.S + (size_t)(e >> 8) * np + g);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int t = t0 + threadIdx.x;
+    if (t >= np) return;
+    V* __restrict__ xout = B.xout + rr * B.sxo;
+    const int i = t % n1, j = t / n1;
+    if (!valid_pt(B.type, i, j)) { xout[t] = czero<V>(); return; }
+    auto X = [&](int g) { return xs[g - xbase]; };
+    auto S = [&](int slot) { return cs[slot * 256 + threadIdx.x]; };
+    const V ax = apply_stencil_acc<MODE, RM>(S, B.rx, B.rz, n1, n2, i, j, t, X);
+    const V b = B.b[rr * B.sb + t];
+    if (RES) {
+        xout[t] = csub(b, ax);
+    } else {
+        const V dg = ldc(S(B.rz * (2 * B.rx + 1) + B.rx));
+        const V corr = cdiv(csub(b, ax), dg);
+        const V x = X(t);
+        xout[t] = cmk<V>(x.x + w * corr.x, x.y + w * corr.y);
+    }
+}
+
+// bytes of shared memory the staged kernel needs on this set (0: use the plain kernel)
+template <int MODE>
+static size_t staged_smem(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s, int rm) {
+    if (!s.staged || MODE != BAH_MIXED) return 0;
+    int nsl = 0;
+    for (int z = 0; z < s.nb; ++z) nsl = std::max(nsl, (2 * s.blk[z].rx + 1) * (2 * s.blk[z].rz + 1));
+    const size_t xlen = 256 + 2 * ((size_t)rm * s.n1 + rm);
+    const size_t bytes = xlen * sizeof(typename Prec<MODE>::V) + (size_t)nsl * 256 * sizeof(typename Prec<MODE>::CC);
+    return bytes <= 48 * 1024 ? bytes : 0;
+}
+
 template <int MODE>
 void launch_jacobi(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
                    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w, int zero_init,
@@ -255,8 +340,12 @@ void launch_jacobi(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>
     dim3 g((np + 255) / 256, s.nb, s.nrhs);
     using R = typename Prec<MODE>::R;
     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
+    const int rm = f5 ? 1 : max_radius(s);
+    const size_t sm = (f5 || zero_init) ? 0 : staged_smem<MODE>(s, rm);
     if (f5) launch_pdl(k_jacobi<MODE, true, 1>, dim3(g), dim3(256), 0, st, s, *f5, (R)w, zero_init);
-    else if (max_radius(s) <= 1) launch_pdl(k_jacobi<MODE, false, 1>, dim3(g), dim3(256), 0, st, s, nof, (R)w, zero_init);
+    else if (sm && rm <= 1) launch_pdl(k_stencil_staged<MODE, 1, false>, dim3(g), dim3(256), sm, st, s, (R)w);
+    else if (sm) launch_pdl(k_stencil_staged<MODE, 2, false>, dim3(g), dim3(256), sm, st, s, (R)w);
+    else if (rm <= 1) launch_pdl(k_jacobi<MODE, false, 1>, dim3(g), dim3(256), 0, st, s, nof, (R)w, zero_init);
     else launch_pdl(k_jacobi<MODE, false, 2>, dim3(g), dim3(256), 0, st, s, nof, (R)w, zero_init);
 }
 template <int MODE>
@@ -265,8 +354,13 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
     const int np = s.n1 * s.n2;
     dim3 g((np + 255) / 256, s.nb, s.nrhs);
     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
+    using R = typename Prec<MODE>::R;
+    const int rm = f5 ? 1 : max_radius(s);
+    const size_t sm = f5 ? 0 : staged_smem<MODE>(s, rm);
     if (f5) launch_pdl(k_residual<MODE, true, 1>, dim3(g), dim3(256), 0, st, s, *f5);
-    else if (max_radius(s) <= 1) launch_pdl(k_residual<MODE, false, 1>, dim3(g), dim3(256), 0, st, s, nof);
+    else if (sm && rm <= 1) launch_pdl(k_stencil_staged<MODE, 1, true>, dim3(g), dim3(256), sm, st, s, (R)0);
+    else if (sm) launch_pdl(k_stencil_staged<MODE, 2, true>, dim3(g), dim3(256), sm, st, s, (R)0);
+    else if (rm <= 1) launch_pdl(k_residual<MODE, false, 1>, dim3(g), dim3(256), 0, st, s, nof);
     else launch_pdl(k_residual<MODE, false, 2>, dim3(g), dim3(256), 0, st, s, nof);
 }
 

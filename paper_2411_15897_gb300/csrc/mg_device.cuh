@@ -104,6 +104,38 @@ __device__ __forceinline__ typename MGT<MODE>::V apply_stencil_fn(const typename
     return acc;
 }
 
+// the same stencil product with the coefficients read through an accessor
+// S(slot) (e.g. from shared memory); same loads, masks and order as above
+template <int MODE, int RM, class SF, class XF>
+__device__ __forceinline__ typename MGT<MODE>::V apply_stencil_acc(SF S, int rx, int rz, int n1, int n2, int i, int j,
+                                                                  int t, XF X) {
+    using V = typename MGT<MODE>::V;
+    using R = typename MGT<MODE>::R;
+    const int wx = 2 * rx + 1;
+    V sv[(2 * RM + 1) * (2 * RM + 1)], xv[(2 * RM + 1) * (2 * RM + 1)];
+    bool in[(2 * RM + 1) * (2 * RM + 1)];
+#pragma unroll
+    for (int dz = -RM; dz <= RM; ++dz) {
+#pragma unroll
+        for (int dx = -RM; dx <= RM; ++dx) {
+            const int q = (dz + RM) * (2 * RM + 1) + (dx + RM);
+            const int ii = i + dx, jj = j + dz;
+            in[q] = dx >= -rx && dx <= rx && dz >= -rz && dz <= rz && ii >= 0 && ii < n1 && jj >= 0 && jj < n2;
+            const int slot = in[q] ? (dz + rz) * wx + (dx + rx) : 0;
+            sv[q] = ldc(S(slot));
+            xv[q] = X(in[q] ? jj * n1 + ii : t);
+        }
+    }
+    V acc = czero<V>();
+#pragma unroll
+    for (int q = 0; q < (2 * RM + 1) * (2 * RM + 1); ++q) {
+        const R m = in[q] ? R(1) : R(0);
+        acc.x += m * (sv[q].x * xv[q].x - sv[q].y * xv[q].y);
+        acc.y += m * (sv[q].x * xv[q].y + sv[q].y * xv[q].x);
+    }
+    return acc;
+}
+
 template <int MODE>
 __device__ __forceinline__ typename MGT<MODE>::V diag_only(const Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC>* f5,
                                                           const LvlBlk<typename MGT<MODE>::V, typename MGT<MODE>::CC>& B,

@@ -103,6 +103,7 @@ struct Ctx {
     std::vector<cudaEvent_t> itev;
     bool use_graphs = true;
     bool fused = false;                  // fused multigrid kernels (BAH_FUSED=1) when nu_pre == 1 and nu_post >= 1
+    bool staged = true;                  // shared-memory staging of Galerkin-level sweeps (BAH_STAGED=0: off)
     bool tiled = false;                  // tiled fused level visits (opt-in, BAH_TILED=1): measured 3% slower
                                          // than the separate launches on the 512x512 workload
     // cooperative cycle over levels 1..L-1 (one launch per block set)
@@ -271,6 +272,7 @@ struct MG {
         s.nb = nb; s.n1 = c.ln1[l]; s.n2 = c.ln2[l];
         s.nrhs = bt.nr;
         s.active = bt.active;
+        s.staged = c.staged ? 1 : 0;
         const size_t npl = (size_t)c.ln1[l] * c.ln2[l];
         for (int z = 0; z < nb; ++z) {
             const int b = b0 + z;
@@ -869,6 +871,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     if (const char* e = getenv("BAH_NO_GRAPHS")) c.use_graphs = (e[0] == '0');
     if (const char* e = getenv("BAH_FUSED")) c.fused = (e[0] == '1');
     if (const char* e = getenv("BAH_TILED")) c.tiled = (e[0] == '1');
+    if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
     return BAH_OK;

@@ -526,6 +526,26 @@ def test_tiled_level_visits_match_separate_kernels(prec, cycle, name, systems, m
     assert rel(W.padded_to_compact(out["1"], p.n), ref) <= (1e-10 if prec == bah.BAH_FP64 else 2e-4)
 
 
+@pytest.mark.parametrize("name", ["random_48x40", "layered_64x32"])
+def test_staged_level_kernels_match_plain(name, systems, monkeypatch):
+    """Mixed mode stages each CTA's stencil coefficients and iterate rows in
+    shared memory before a Jacobi sweep or residual on a Galerkin level; with
+    BAH_STAGED=0 the plain kernels read them directly.  Same arithmetic:
+    identical preconditioner (to rounding), and equal to the oracle's."""
+    p, S = get(name, systems)
+    r = W.random_vector(p.n, 45)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("BAH_STAGED", mode)
+        monkeypatch.setenv("BAH_SMEM_MG", "0")     # keep every level on the separate kernels
+        s = bah.Solver.from_problem(p, levels=3)
+        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
+        s.close()
+    assert rel(out["1"], out["0"]) <= 1e-6, rel(out["1"], out["0"])
+    pc = precond.multigrid(S, 3, precond.default_alpha(3), precision="mixed")
+    assert rel(W.padded_to_compact(out["1"], p.n), pc.apply(W.padded_to_compact(r, p.n))) <= 2e-4
+
+
 def test_double_float_operator_in_fgmres(monkeypatch):
     """In mixed mode with the double-float basis, w = H z is formed in
     double-float arithmetic (about 2^-47 relative).  An operator that is only
