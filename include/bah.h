@@ -54,7 +54,7 @@ extern "C" {
 #define BAH_ERR_CUDA          -3   /* a CUDA runtime call failed */
 #define BAH_ERR_NOT_CONVERGED -4   /* maxit reached; x holds the last iterate */
 #define BAH_ERR_NONFINITE     -5   /* NaN/Inf met in a reduction; x holds the last finite iterate */
-#define BAH_ERR_UNSUPPORTED   -6   /* a valid request this build does not implement */
+#define BAH_ERR_UNSUPPORTED   -6   /* a valid request the library does not implement (3-D grids) */
 
 /* precision of the preconditioner (the outer FGMRES, the operator apply and
  * the coarsest-level solve are FP64 in both modes) */

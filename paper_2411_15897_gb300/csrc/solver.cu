@@ -1194,7 +1194,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     *out = nullptr;
     g_err.clear();
     if (!grid || !med) { set_error("grid or medium is NULL"); return BAH_ERR_ARG; }
-    if (grid->dim == 3) { set_error("3-D grids are not implemented in this build"); return BAH_ERR_UNSUPPORTED; }
+    if (grid->dim == 3) { set_error("3-D grids are not implemented (2-D only)"); return BAH_ERR_UNSUPPORTED; }
     if (grid->dim != 2) { set_error("dim must be 2"); return BAH_ERR_ARG; }
     if (!med->lambda || !med->mu || !med->rho || !med->gamma) { set_error("medium array is NULL"); return BAH_ERR_ARG; }
     if (!(med->omega > 0.0)) { set_error("omega must be > 0"); return BAH_ERR_ARG; }

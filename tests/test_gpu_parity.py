@@ -2,8 +2,8 @@
 the FP64 CPU oracle on the same seeded inputs.
 
 Tolerances (relative 2-norm errors):
-  * operator apply H x (FP64 kernels vs FP64 sparse matrix): 1e-12, the bar
-    the specification sets for the operator;
+  * operator apply H x (FP64 kernels vs FP64 sparse matrix): 1e-12, FP64
+    rounding over a 19-entry row;
   * Galerkin stencils (FP64 setup kernels vs sparse R A P): 1e-12;
   * FP64-mode multigrid cycle / preconditioner: 1e-10 (same arithmetic, only
     the summation order differs; the coarse inverse can amplify rounding by
@@ -15,9 +15,9 @@ Tolerances (relative 2-norm errors):
     rounding of its right-hand side: 6e-8 * 20 * 1e3 ~ 1e-3 worst case, 2e-4
     with the observed cancellation margin of the random-phase inputs used;
   * solves: the true relative residual ||b - H x|| / ||b|| recomputed with the
-    oracle's assembled H must be <= 1e-6 (the specification's acceptance
-    criterion); FP64-mode iterates after a fixed number of steps agree with
-    the oracle's FGMRES iterates to 1e-8.
+    oracle's assembled H must be <= 1e-6 (the stopping rule of Sec. 4);
+    FP64-mode iterates after a fixed number of steps agree with the oracle's
+    FGMRES iterates to 1e-8.
 """
 import math
 
