@@ -207,6 +207,19 @@ int bah_misfit(bah_ctx* ctx, const void* x, const void* d, const int* rec, int n
 int bah_gradient(bah_ctx* ctx, const void* x_fwd, const void* y_adj, int nrhs, double* g_lambda, double* g_mu,
                  double* g_rho, void* stream);
 
+/* Spectral radius of the preconditioned fixed-point iteration's error
+ * operator T = I - P^{-1} D H (Sec. 3: with exact blocks, Theorem 1 gives
+ * rho(T) = rho(Z), Z = Xi A^{-1} B^T H_p^{-1}; the paper estimates it by the
+ * power method on a matrix-free product).  Power method from the device
+ * vector x0 (FP64 complex, the vector layout above, not modified):
+ * x_{k+1} = T x_k / ||T x_k||, with x_0 = x0 / ||x0||, for iters >= 1 steps,
+ * using the context's preconditioner (exact blocks with levels = 1, else its
+ * multigrid cycles).  history (host, iters doubles, may be NULL) receives
+ * ||T x_k||; *rho the geometric mean of the last quarter of the history.
+ * Uses the context's Krylov workspace (no solve may run on the context at the
+ * same time).  Synchronous on the given stream. */
+int bah_spectral_radius(bah_ctx* ctx, const void* x0, int iters, double* history, double* rho, void* stream);
+
 /* Test hook: one multigrid cycle (the context's cycle type) on acoustic block
  * `block` (0..dim-1 = A_{block+1},s; dim = H_p,s) with zero initial guess.
  * b and x are device arrays of cells complex FP64 values in the padded

@@ -36,7 +36,8 @@ BAH_KRYLOV_FP64 = 0
 BAH_KRYLOV_DF = 1
 
 # every symbol include/bah.h declares
-EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_get_info", "bah_apply_operator",
+EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_get_info", "bah_spectral_radius",
+           "bah_apply_operator",
            "bah_apply_preconditioner", "bah_solve", "bah_block_cycle", "bah_level_stencil",
            "bah_status_string", "bah_last_error", "bah_profile_control", "bah_profile_read",
            "bah_residual_norm_static", "bah_solve_adjoint", "bah_misfit", "bah_gradient")
@@ -103,6 +104,8 @@ def lib():
         L.bah_sizes.restype = C.c_int
         L.bah_get_info.argtypes = [vp, C.POINTER(bah_info)]
         L.bah_get_info.restype = C.c_int
+        L.bah_spectral_radius.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+        L.bah_spectral_radius.restype = C.c_int
         L.bah_apply_operator.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bah_apply_operator.restype = C.c_int
         L.bah_apply_preconditioner.argtypes = [vp, vp, vp, C.c_int, vp]
@@ -189,6 +192,15 @@ def bah_get_info(ctx):
     out = bah_info()
     _check(lib().bah_get_info(ctx, C.byref(out)), "bah_get_info")
     return out.as_dict()
+
+
+def bah_spectral_radius(ctx, x0, iters, stream=None):
+    """(rho, history) of the power method on T = I - P^{-1} D H from device vector x0."""
+    hist = (C.c_double * int(iters))()
+    rho = C.c_double()
+    _check(lib().bah_spectral_radius(ctx, _ptr(x0), int(iters), hist, C.byref(rho), _stream(stream)),
+           "bah_spectral_radius")
+    return rho.value, np.array(hist[:])
 
 
 def bah_sizes(ctx):

@@ -353,6 +353,7 @@ void launch_norm2(const double2* w, size_t n, double* partial, double* sc, int s
 template <class Vz>
 void launch_update_x(const Vz* Z, const int* kk, const double2* y, double2* x, size_t n, int nrhs, const KS& ks,
                      cudaStream_t st);
+void launch_sub(const double2* a, const double2* b, double2* c, size_t n, cudaStream_t st);
 void launch_scale_copy(const double2* w, const double* sc, int slot, double2* v, size_t n, size_t sw, size_t sv,
                        int nrhs, const KS& ks, cudaStream_t st);
 void launch_arnoldi_givens(double2* Hm, int ldh, const double2* h1, const double2* h2, const double* sc, int j,

@@ -316,6 +316,16 @@ __global__ void k_scale_copy(const double2* __restrict__ w, const double* sc, in
         v[e] = make_double2(a.x * s, a.y * s);
     }
 }
+// c = a - b
+__global__ void k_sub(const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ c, size_t n) {
+    pdl_prologue();
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        c[e] = csub(a[e], b[e]);
+}
+void launch_sub(const double2* a, const double2* b, double2* c, size_t n, cudaStream_t st) {
+    launch_pdl(k_sub, dim3(RED_CTAS * 2), dim3(256), 0, st, a, b, c, n);
+}
+
 void launch_scale_copy(const double2* w, const double* sc, int slot, double2* v, size_t n, size_t sw, size_t sv,
                        int nrhs, const KS& ks, cudaStream_t st) {
     launch_pdl(k_scale_copy, dim3(dim3(RED_CTAS * 2, nrhs)), dim3(256), 0, st, w, sc, slot, v, n, sw, sv, ks);

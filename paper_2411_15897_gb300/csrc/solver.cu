@@ -1324,6 +1324,46 @@ int bah_apply_preconditioner(bah_ctx* h, const void* r, void* z, int nrhs, void*
     return BAH_OK;
 }
 
+int bah_spectral_radius(bah_ctx* h, const void* x0, int iters, double* history, double* rho, void* stream) {
+    if (!h || !x0 || iters < 1 || !rho) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = c.vec_len();
+    double2* x = c.X;
+    double2* y = c.R;
+    double2* z = c.W;
+    double2* t = c.Bs;
+    KS ks;
+    Batch one;
+    launch_norm2((const double2*)x0, n, c.dpart, c.nrm, 0, 1, ks, st);
+    launch_scale_copy((const double2*)x0, c.nrm, 0, x, n, 0, 0, 1, ks, st);
+    std::vector<double> hist(iters);
+    for (int k = 0; k < iters; ++k) {
+        launch_elastic_apply<double2>(c.op, x, y, nullptr, 0, st);
+        if (c.mode == BAH_MIXED) {
+            precond_any(c, (const double2*)y, n, c.ztmp, n, one, st);
+            launch_convert<float2, double2>((const float2*)c.ztmp, z, n, st);
+        } else {
+            precond_any(c, (const double2*)y, n, z, n, one, st);
+        }
+        launch_sub(x, z, t, n, st);
+        launch_norm2(t, n, c.dpart, c.nrm, 0, 1, ks, st);
+        launch_scale_copy(t, c.nrm, 0, x, n, 0, 0, 1, ks, st);
+        BAH_CUDA_TRY(cudaGetLastError());
+        BAH_CUDA_TRY(cudaMemcpyAsync(&hist[k], c.nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+        BAH_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!std::isfinite(hist[k])) { set_error("non-finite value in the power method"); return BAH_ERR_NONFINITE; }
+        if (hist[k] == 0.0) { iters = k + 1; break; }
+    }
+    const int q = std::max(1, iters / 4);
+    double acc = 0.0;
+    for (int k = iters - q; k < iters; ++k) acc += std::log(std::max(hist[k], 1e-300));
+    *rho = std::exp(acc / q);
+    if (history)
+        for (int k = 0; k < iters; ++k) history[k] = hist[k];
+    return BAH_OK;
+}
+
 int bah_block_cycle(bah_ctx* h, int block, const void* b, void* x, void* stream) {
     if (!h || !b || !x || block < 0 || block > h->c.dim) { set_error("bad argument"); return BAH_ERR_ARG; }
     Ctx& c = h->c;

@@ -76,3 +76,28 @@ def test_exact_block_gmres_count(prec, linear_small):
     xc = W.padded_to_compact(to_host(x), p.n)
     assert np.linalg.norm(bc - H @ xc) / np.linalg.norm(bc) <= 1e-6
     s.close()
+
+
+# ----------------------------------------------------------------------------
+# spectral radius of T = I - P^{-1} D H (Sec. 3, Theorem 1) by the power method
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("levels,prec", [(1, bah.BAH_FP64), (3, bah.BAH_FP64), (3, bah.BAH_MIXED)])
+def test_spectral_radius_matches_oracle_power_method(levels, prec, linear_small):
+    """The same power method from the same start vector, on the GPU
+    (bah_spectral_radius) and in the oracle (theorem1.power_T): with exact
+    blocks (levels = 1) it estimates rho(T) = rho(Z) of Theorem 1; with
+    multigrid blocks the fixed-point iteration's rate.  FP64 histories agree
+    step by step; mixed precision to its rounding."""
+    from oracle import theorem1
+    p, S = linear_small
+    x0 = W.random_vector(p.n, 53)
+    s = bah.Solver.from_problem(p, precision=prec, levels=levels)
+    rho, hist = bah.bah_spectral_radius(s.ctx, to_dev(x0), 60)
+    pc = (precond.exact(S, 0.0) if levels == 1
+          else precond.multigrid(S, levels, precond.default_alpha(levels),
+                                 precision="fp64" if prec == bah.BAH_FP64 else "mixed"))
+    ref, ref_hist = theorem1.power_T(S, pc.apply, W.padded_to_compact(x0, p.n), 60)
+    tol = 1e-8 if prec == bah.BAH_FP64 else 1e-3
+    np.testing.assert_allclose(hist, ref_hist, rtol=tol)
+    assert abs(rho - ref) <= tol * ref
+    s.close()

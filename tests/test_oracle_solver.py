@@ -299,3 +299,44 @@ def test_linear_media_block_acoustic_multigrid_counts(idx):
     r = fgmres.fgmres(lambda v: H @ v, b, pc.apply, restart=5, rtol=1e-6, maxit=3000)
     assert r.converged
     assert abs(r.iters - row["iters"]) <= 0.2 * row["iters"], r.iters
+
+
+# ----------------------------------------------------------------------------
+# spectral radius of the error iteration (Sec. 3, Theorem 1; the power method
+# on a matrix-free product, as the paper measures rho(Z))
+# ----------------------------------------------------------------------------
+def test_power_method_rho_matches_dense_eigenvalues():
+    """On a tiny grid the power method on T = I - P^{-1} K (exact blocks) and on
+    Z = Xi A^{-1} B^T H_p^{-1} both converge to the largest |eigenvalue| of the
+    dense matrices, and the two agree (rho(T) = rho(Z), Theorem 1)."""
+    from oracle import theorem1
+    p = W.random_medium((6, 5), 9, omega=4.0, abc=1)
+    S = elastic.from_problem(p)
+    Pm, D, K = precond.dense_matrices(S, 0.0)
+    T = np.eye(Pm.shape[0]) - np.linalg.solve(Pm, K)
+    rho_dense = np.abs(np.linalg.eigvals(T)).max()
+    rng = np.random.default_rng(5)
+    x0 = rng.standard_normal(S.H.shape[0]) + 1j * rng.standard_normal(S.H.shape[0])
+    rT, _ = theorem1.power_T(S, precond.exact(S, 0.0).apply, x0, 400)
+    np.testing.assert_allclose(rT, rho_dense, rtol=2e-2)
+    z0 = rng.standard_normal(S.sizes[2]) + 1j * rng.standard_normal(S.sizes[2])
+    rZ, _ = theorem1.rho_Z(S, 0.0, z0, 400)
+    np.testing.assert_allclose(rZ, rho_dense, rtol=2e-2)
+
+
+@pytest.mark.slow
+def test_linear_medium_rho_below_one_without_shift():
+    """Sec. 3 (spectral radius of Z against the shift): for the linear medium
+    the shift needed for rho(Z) < 1 is zero or negligible.  Here, 200x64 at
+    omega = 1.75 pi: rho(Z) < 1 at alpha = 0, estimated by the power method on
+    Z with sparse LU block solves, and equal to rho(T) (Theorem 1)."""
+    from oracle import theorem1
+    p = W.linear_medium(200, 64, 1.75 * math.pi)
+    S = elastic.from_problem(p)
+    rng = np.random.default_rng(1)
+    z0 = rng.standard_normal(S.sizes[2]) + 1j * rng.standard_normal(S.sizes[2])
+    rZ, _ = theorem1.rho_Z(S, 0.0, z0, 150)
+    x0 = rng.standard_normal(S.H.shape[0]) + 1j * rng.standard_normal(S.H.shape[0])
+    rT, _ = theorem1.power_T(S, precond.exact(S, 0.0).apply, x0, 150)
+    assert rZ < 1.0
+    assert abs(rZ - rT) <= 0.02 * rT
