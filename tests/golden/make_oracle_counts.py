@@ -3,7 +3,7 @@ count and true relative residual for the named workloads, with the solver
 options the benchmark uses (mixed-precision coefficient set, V(1,2), FGMRES(20),
 rel-res 1e-6).  Calls only oracle/ and workloads/.
 
-    python tests/golden/make_oracle_counts.py c1 c2 [--levels L]
+    python tests/golden/make_oracle_counts.py c1 c2 [--levels L] [--alpha A] [--nu PRE,POST]
 """
 import json
 import os
@@ -33,18 +33,25 @@ def main():
     lv = None
     if "--levels" in sys.argv:
         lv = int(sys.argv[sys.argv.index("--levels") + 1])
+    al = None
+    if "--alpha" in sys.argv:
+        al = float(sys.argv[sys.argv.index("--alpha") + 1])
+    nu = (1, 2)
+    if "--nu" in sys.argv:
+        nu = tuple(int(v) for v in sys.argv[sys.argv.index("--nu") + 1].split(","))
+    names = [a for a in names if a not in (str(lv), str(al), ",".join(map(str, nu)))]
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in names:
         p = W.config(name)
         L = lv or auto_levels(p.n)
-        alpha = precond.default_alpha(L)
+        alpha = al if al is not None else precond.default_alpha(L)
         t0 = time.perf_counter()
         S = elastic.from_problem(p)
         H = S.H
-        pc = precond.multigrid(S, L, alpha, precision="mixed")
+        pc = precond.multigrid(S, L, alpha, precision="mixed", nu_pre=nu[0], nu_post=nu[1])
         b = W.padded_to_compact(W.point_source(p), p.n)
         r = fgmres.fgmres(lambda v: H @ v, b, pc.apply, restart=20, rtol=1e-6, maxit=20000)
-        data[name] = {"levels": L, "alpha": alpha, "restart": 20, "precision": "mixed", "iters": r.iters,
+        data[name] = {"levels": L, "alpha": alpha, "nu": list(nu), "restart": 20, "precision": "mixed", "iters": r.iters,
                       "relres_true": r.relres_true, "converged": bool(r.converged),
                       "cpu_seconds": time.perf_counter() - t0}
         print(name, data[name], flush=True)
