@@ -484,6 +484,11 @@ struct MG {
                 swap_cur();
             }
         } else {
+            // With a zero initial guess the caller's buffer holds nothing yet: if the
+            // sweeps below swap the two buffers an odd number of times, start in the
+            // other one, so that the last sweep lands in the caller's buffer and no
+            // copy is needed.
+            if (!x0 && ((std::max(c.o.nu_pre - 1, 0) + c.o.nu_post) & 1)) swap_cur();
             // pre-relaxation
             if (x0) {
                 for (int s = 0; s < c.o.nu_pre; ++s) {

@@ -211,6 +211,26 @@ def test_preconditioner_matches_oracle(prec, name, systems):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nu", [(1, 3), (2, 3), (0, 3), (2, 2)])
+def test_preconditioner_smoothing_counts_match_oracle(prec, nu, systems, monkeypatch):
+    """V(nu1,nu2) cycles with other sweep counts (the benchmark runs V(1,3)):
+    odd and even numbers of buffer swaps, a zero pre-smoothing count, on the
+    separate kernels and with the small levels in the cluster kernel."""
+    p, S = get("layered_64x32", systems)
+    r = W.random_vector(p.n, 49)
+    pc = precond.multigrid(S, 4, precond.default_alpha(4), precision=prec, nu_pre=nu[0], nu_post=nu[1])
+    ref = pc.apply(W.padded_to_compact(r, p.n))
+    tol = 1e-10 if prec == "fp64" else 2e-4
+    for smem in ("0", "1"):
+        monkeypatch.setenv("BAH_SMEM_MG", smem)
+        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=4,
+                                    nu_pre=nu[0], nu_post=nu[1])
+        z = to_host(s.apply_preconditioner(to_dev(r)))
+        assert rel(W.padded_to_compact(z, p.n), ref) <= tol, (smem, rel(W.padded_to_compact(z, p.n), ref))
+        s.close()
+
+
 # ----------------------------------------------------------------------------
 # solves
 # ----------------------------------------------------------------------------
