@@ -284,11 +284,12 @@ def test_scalability_table_exact_blocks():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("idx", [0, 1, 2])
+@pytest.mark.parametrize("idx", [0, 1, 2, 3])
 def test_linear_media_block_acoustic_multigrid_counts(idx):
     """Table 4 (Sec. 4.4.3), block-acoustic column: GMRES(5) with one W(1,2)
     cycle per block on the 400x128 linear medium needs 31/49/90 iterations for
-    2/3/4 levels.  Soft pin: within +-20%."""
+    2/3/4 levels, and 49 with 2 levels on 800x256 at twice the frequency (the
+    oracle gives 30/51/93 and 50).  Soft pin: within +-20%."""
     row = GOLD["linear_2d_block_acoustic"]["rows"][idx]
     n1, n2 = row["grid"]
     p = W.linear_medium(n1, n2, row["omega_over_pi"] * math.pi)
