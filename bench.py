@@ -236,6 +236,8 @@ def run_bah(args):
     nsrc_all = len(prob.sources)
     # many sources: each rank solves its own share (no exchange during the
     # solves); one source: every rank solves it (replicas)
+    if 1 < nsrc_all < world:
+        raise SystemExit(f"{world} ranks for {nsrc_all} sources: every rank needs at least one source")
     mine = shard.shard(nsrc_all, rank, world) if nsrc_all > 1 else np.array([0])
     nsrc = len(mine)
     job_units = nsrc_all if nsrc_all > 1 else world      # solves completed by the whole job per step
