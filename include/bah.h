@@ -56,13 +56,17 @@ extern "C" {
 #define BAH_ERR_NONFINITE     -5   /* NaN/Inf met in a reduction; x holds the last finite iterate */
 #define BAH_ERR_UNSUPPORTED   -6   /* a valid request the library does not implement (3-D grids) */
 
-/* precision of the preconditioner (the outer FGMRES, the operator apply and
- * the coarsest-level solve are FP64 in both modes) */
+/* precision of the preconditioner.  The coarsest-level inverse is computed in
+ * FP64 in both modes and applied in the multigrid's precision; the outer
+ * FGMRES keeps its Hessenberg update, Givens rotations, true residual and
+ * solution in FP64 in both modes (see krylov_arith for the basis) */
 #define BAH_FP64   0   /* multigrid in complex FP64 with FP64 coefficients */
 #define BAH_MIXED  1   /* multigrid in complex FP32, coefficients stored in bfloat16 */
 
-/* arithmetic of the Krylov basis (Gram-Schmidt dots and updates); the
- * Hessenberg least-squares update, the true residual and x are FP64 always */
+/* arithmetic of the Krylov basis (Gram-Schmidt dots and updates, and, in
+ * BAH_MIXED mode, the operator w = H z and the update x += Z y on the FP32
+ * flexible basis); the Hessenberg least-squares update, the true residual and
+ * x are FP64 always */
 #define BAH_KRYLOV_FP64 0  /* IEEE FP64 */
 #define BAH_KRYLOV_DF   1  /* double-FP32: each real is an FP32 pair hi + lo (48-bit significand),
                               products and sums by error-free FP32 transformations */
