@@ -52,6 +52,16 @@ WORKLOADS = {
           "FGMRES(20) to rel-res 1e-6",
     "c4": "2D 1024x512 layered medium (6 layers, seed 5), 64 point sources along row 20 solved as one batch, "
           "FGMRES(20) to rel-res 1e-6 per source",
+    "c5": "3D 128x128x128 smooth random medium (log Vp Gaussian random field, correlation 16 cells, std 0.2, mean "
+          "log 3; nu in [0.3,0.49]), 8 points per shear wavelength, 10-cell absorbing layer, top-face point source, "
+          "FGMRES(20) to rel-res 1e-6",
+}
+# per-workload cycle settings where they differ from the 2-D benchmark's: the 3-D
+# workload runs the paper's 3-D multigrid (Sec. 4.5: mixed intergrid, W(2,2),
+# Jacobi 0.8, 0.8, 0.2) on 5 levels (coarsest 8^3) with the FP64 Krylov basis
+PRESETS = {
+    "2d": dict(levels=0, alpha=0.8, cycle="V", nu="1,3", jacobi="0.8,0.8,0.3", intergrid="bilinear", krylov="df"),
+    "c5": dict(levels=5, alpha=0.4, cycle="W", nu="2,2", jacobi="0.8,0.8,0.2", intergrid="mixed", krylov="fp64"),
 }
 WORKLOAD = WORKLOADS["c2"]
 L2_FLUSH_BYTES = 512 << 20
@@ -60,6 +70,9 @@ KERNEL_NAMES = {0: "k_elastic_apply", 1: "k_distributor", 2: "k_u_rhs", 3: "k_ja
                 5: "k_restrict", 6: "k_prolong_add", 7: "k_coarse_apply", 8: "k_dot_norm_partial",
                 9: "k_axpy_norm", 10: "k_norm2_partial", 11: "k_update_x", 12: "small kernels",
                 13: "k_coop_cycle", 14: "k_cluster_cycle", 15: "k_down_tiled + k_up_tiled"}
+KERNEL_NAMES_3D = {0: "k_apply3", 1: "k_distrib3", 2: "k_urhs3", 3: "k_jacobi3", 4: "k_jacobi3 (residual)",
+                   5: "k_restrict3", 6: "k_prolong3", 7: "k_coarse_apply", 8: "k_dot_norm_partial",
+                   9: "k_axpy_norm", 10: "k_norm2_partial", 11: "k_update_x", 12: "small kernels"}
 # FP64 flops per algorithmic byte of the FP64 classes (2 flops per real FMA):
 #   dot/axpy: 8 flops per complex MAC on 16 streamed bytes; operator: ~84 flops per cell on ~200 bytes
 FP64_FLOP_PER_BYTE = {"dot": 0.5, "axpy": 0.5, "update": 8.0 / 8.0, "operator": 84.0 / 200.0}
@@ -77,21 +90,27 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle FGMRES iterations per baseline sample")
     ap.add_argument("--profile-json", default="", help="write the per-kernel-class profile here")
-    ap.add_argument("--levels", type=int, default=0)
+    ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--max-coarse", type=int, default=256)
     ap.add_argument("--restart", type=int, default=20)
-    ap.add_argument("--krylov", default="df", choices=["fp64", "df"])
+    ap.add_argument("--krylov", default=None, choices=["fp64", "df"])
     ap.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per batch (default: all sources)")
     ap.add_argument("--gradient", action="store_true", help="also time the adjoint gradient of a receiver misfit")
     ap.add_argument("--maxit", type=int, default=20000)
     # the benchmark's tuned cycle: V(1,3) with alpha 0.8 (searched at a resolution of 0.1 on this
     # workload, as the paper searches its shifts); --alpha -1 --nu 1,2 gives the library defaults
-    ap.add_argument("--alpha", type=float, default=0.8, help="shift alpha (-1: the library's choice)")
-    ap.add_argument("--cycle", default="V", choices=["V", "W"])
-    ap.add_argument("--nu", default="1,3", help="pre- and post-smoothing sweeps")
+    ap.add_argument("--alpha", type=float, default=None, help="shift alpha (-1: the library's choice)")
+    ap.add_argument("--cycle", default=None, choices=["V", "W"])
+    ap.add_argument("--nu", default=None, help="pre- and post-smoothing sweeps")
+    ap.add_argument("--jacobi", default=None, help="Jacobi damping per level, comma separated")
+    ap.add_argument("--intergrid", default=None, choices=["bilinear", "mixed"])
     ap.add_argument("--krylov-fp64-steps", type=int, default=2,
                     help="also time the same solve with the Krylov basis in IEEE FP64")
-    return ap.parse_args()
+    args = ap.parse_args()
+    for k, v in PRESETS.get(args.config, PRESETS["2d"]).items():
+        if getattr(args, k) is None:
+            setattr(args, k, v)
+    return args
 
 
 def dist_env():
@@ -111,14 +130,16 @@ def oracle_counts():
 # ----------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------
-def oracle_sample(prob, levels, alpha, restart, iters, reps=1, nu=(1, 2)):
+def oracle_sample(prob, levels, alpha, restart, iters, reps=1, nu=(1, 2), cycle="V", weights=(0.8, 0.8, 0.3),
+                  intergrid="bilinear"):
     """Oracle setup once, then ``reps`` samples of ``iters`` FGMRES iterations;
     returns (seconds per iteration list, setup seconds)."""
     from oracle import elastic, fgmres, precond
     t0 = time.perf_counter()
     S = elastic.from_problem(prob)
     H = S.H
-    pc = precond.multigrid(S, levels, alpha, precision="mixed", nu_pre=nu[0], nu_post=nu[1])
+    pc = precond.multigrid(S, levels, alpha, precision="mixed", nu_pre=nu[0], nu_post=nu[1], cycle=cycle,
+                           weights=weights, intergrid=intergrid)
     setup = time.perf_counter() - t0
     b = W.padded_to_compact(W.point_source(prob), prob.n)
     per = []
@@ -246,8 +267,15 @@ def run_bah(args):
                 krylov_arith=bah.BAH_KRYLOV_DF if args.krylov == "df" else bah.BAH_KRYLOV_FP64,
                 rhs_block=rhs_block, maxit=args.maxit, shift_alpha=args.alpha,
                 cycle=bah.BAH_CYCLE_W if args.cycle == "W" else bah.BAH_CYCLE_V,
-                nu_pre=int(args.nu.split(",")[0]), nu_post=int(args.nu.split(",")[1]))
+                nu_pre=int(args.nu.split(",")[0]), nu_post=int(args.nu.split(",")[1]),
+                jacobi_w=tuple(float(v) for v in args.jacobi.split(",")),
+                intergrid=bah.BAH_INTERGRID_MIXED if args.intergrid == "mixed" else bah.BAH_INTERGRID_BILINEAR)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
     solver = bah.Solver.from_problem(prob, **opts)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    context_bytes = int(free0 - free1)
     levels = solver.levels
     b_host = np.ascontiguousarray(W.all_sources(prob)[mine]) if nsrc_all > 1 else W.point_source(prob)
     b = torch.from_numpy(b_host).cuda()
@@ -424,7 +452,7 @@ def run_bah(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
-    kname = KERNEL_NAMES.get(dom_id, dom)
+    kname = (KERNEL_NAMES_3D if prob.dim == 3 else KERNEL_NAMES).get(dom_id, dom)
     if dom == "cluster" and solver.info["cluster_level"] > 0:
         kname = "k_cluster_mg"
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
@@ -462,7 +490,8 @@ def run_bah(args):
         counts = oracle_counts().get(args.config)
         alpha = solver.alpha
         nu = (int(args.nu.split(",")[0]), int(args.nu.split(",")[1]))
-        per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=1, nu=nu)
+        per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=1, nu=nu, cycle=args.cycle,
+                                   weights=tuple(float(v) for v in args.jacobi.split(",")), intergrid=args.intergrid)
         same = (bool(counts) and counts.get("levels") == levels and abs(counts.get("alpha", -1.0) - alpha) < 1e-12
                 and tuple(counts.get("nu", (1, 2))) == nu)
         its = counts["iters"] if same else statistics.median(iters)
@@ -474,7 +503,9 @@ def run_bah(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "strong" if nsrc_all > 1 else "weak", "vs_baseline": None,
-        "dtype": ("mixed: bf16 coefficients, f32 multigrid (coarsest inverse computed in f64, applied in f32), "
+        "dtype": (("mixed: f32 stencils, f32 multigrid (coarsest inverse computed in f64, applied in f32), "
+                   if prob.dim == 3 else
+                   "mixed: bf16 coefficients, f32 multigrid (coarsest inverse computed in f64, applied in f32), ")
                   + ("double-f32 (48-bit) Krylov basis, Gram-Schmidt and operator" if args.krylov == "df"
                      else "f64 Krylov basis, Gram-Schmidt and operator")
                   + ", f64 Hessenberg / Givens / true residual"),
@@ -483,6 +514,7 @@ def run_bah(args):
                    "unknowns": int(sum(W.compact_sizes(prob.n))), "sources": nsrc_all, "sources_per_rank": nsrc,
                    "rhs_block": rhs_block,
                    "levels": levels, "cycle": f"{args.cycle}({args.nu})", "alpha": solver.alpha,
+                   "jacobi": args.jacobi, "intergrid": args.intergrid, "context_bytes": context_bytes,
                    "cluster_levels_from": solver.info["cluster_level"], "restart": args.restart, "iters": iters[-1],
                    "relres_true": relres, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": (f"sources split over {world} GPUs, no exchange during the solves" if nsrc_all > 1

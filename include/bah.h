@@ -54,14 +54,16 @@ extern "C" {
 #define BAH_ERR_CUDA          -3   /* a CUDA runtime call failed */
 #define BAH_ERR_NOT_CONVERGED -4   /* maxit reached; x holds the last iterate */
 #define BAH_ERR_NONFINITE     -5   /* NaN/Inf met in a reduction; x holds the last finite iterate */
-#define BAH_ERR_UNSUPPORTED   -6   /* a valid request the library does not implement (3-D grids) */
+#define BAH_ERR_UNSUPPORTED   -6   /* a valid request the library does not implement (3-D options and
+                                      calls listed at bah_create) */
 
 /* precision of the preconditioner.  The coarsest-level inverse is computed in
  * FP64 in both modes and applied in the multigrid's precision; the outer
  * FGMRES keeps its Hessenberg update, Givens rotations, true residual and
  * solution in FP64 in both modes (see krylov_arith for the basis) */
 #define BAH_FP64   0   /* multigrid in complex FP64 with FP64 coefficients */
-#define BAH_MIXED  1   /* multigrid in complex FP32, coefficients stored in bfloat16 */
+#define BAH_MIXED  1   /* multigrid in complex FP32, coefficients stored in bfloat16 (2-D) or
+                          FP32 stencils (3-D) */
 
 /* arithmetic of the Krylov basis (Gram-Schmidt dots and updates, and, in
  * BAH_MIXED mode, the operator w = H z and the update x += Z y on the FP32
@@ -131,9 +133,17 @@ void bah_default_opts(bah_opts* opts);
  * Galerkin hierarchies R A P (Eq. 4.3) and the FP64 inverse of every coarsest
  * block, and allocates all solve workspace.  Synchronous.  *out receives the
  * context; on failure *out is NULL and nothing is leaked.
- * Errors: BAH_ERR_ARG (dim not 2, odd or too small sizes for the requested
- * levels, non-positive h or omega, NULL arrays), BAH_ERR_UNSUPPORTED (dim 3),
- * BAH_ERR_OOM, BAH_ERR_CUDA. */
+ * 3-D grids (dim 3) follow the paper's 3-D multigrid (Sec. 4.5): they need
+ * intergrid = BAH_INTERGRID_MIXED (Eq. 4.4; with it every Galerkin level is a
+ * 27-point stencil), krylov_arith = BAH_KRYLOV_FP64 and at least 2 levels; the
+ * paper's W(2,2) cycle with Jacobi weights 0.8, 0.8, 0.2 is set through
+ * cycle, nu_pre, nu_post and jacobi_w.  On a 3-D context bah_gradient,
+ * bah_level_stencil and bah_residual_norm_static return BAH_ERR_UNSUPPORTED.
+ * Errors: BAH_ERR_ARG (dim not 2 or 3, odd or too small sizes for the
+ * requested levels, a coarsest level above 4096 cells, non-positive h or
+ * omega, NULL arrays, a 3-D grid with one level), BAH_ERR_UNSUPPORTED (3-D with
+ * the bilinear intergrid or the double-FP32 basis), BAH_ERR_OOM,
+ * BAH_ERR_CUDA. */
 int bah_create(const bah_grid* grid, const bah_medium* medium, const bah_opts* opts, bah_ctx** out);
 
 /* Release the context and all device memory it owns.  NULL is ignored.  The

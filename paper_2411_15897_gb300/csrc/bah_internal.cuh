@@ -379,6 +379,42 @@ void launch_gradient(int n1, int n2, double h1, double h2, double omega, const d
                      size_t vlen, int nrhs, const double2* X, const double2* Y, double* gl, double* gm, double* gr,
                      cudaStream_t st);
 
+// three-dimensional grids (k_3d.cu).  FP64 operator coefficients of H on
+// n[0] x n[1] x n[2] cells; mue[e] is the edge mean of mu for the pair of axes
+// other than e, zero on boundary edges.
+struct Op3 {
+    int n[3];
+    double ih[3], ih2[3];     // 1/h_a, 1/h_a^2
+    const double* muc;        // mu at cells
+    const double* mue[3];
+    const double2* dg[3];     // diagonal of A_a (unshifted, with -omega^2 A_f(rho~))
+    const double* cinv;       // 1/(lambda+mu)
+    const double2* mrt;       // omega^2 rho~ at cells
+};
+void launch_prep3(const Op3& op, double omega, double alpha, const double* lam, const double* mu, const double* rho,
+                  const double* gam, double* cinv, double2* mrt, double* const* mue, double2* const* dg,
+                  double2* const* S, cudaStream_t st);
+template <class Vin>
+void launch_apply3(const Op3& op, const Vin* x, double2* y, const double2* b, int conj, int nrhs, size_t sx, size_t sy,
+                   size_t sb, cudaStream_t st);
+void launch_sanitize3(double2* v, int n1, int n2, int n3, int nvec, cudaStream_t st);
+template <class V>
+void launch_distrib3(const Op3& op, const double2* r, V* tp, cudaStream_t st);
+template <class V>
+void launch_urhs3(const Op3& op, const double2* r, const V* ep, V* const* su, cudaStream_t st);
+template <class V>
+void launch_jacobi3(int type, const int* n, int ns, const V* S, const V* b, const V* xin, V* xout, double w, int zero,
+                    int res, cudaStream_t st);
+template <class V>
+void launch_restrict3(int type, const int* nf, const V* r, V* bc, cudaStream_t st);
+template <class V>
+void launch_prolong3(int type, const int* nf, const V* ec, V* x, cudaStream_t st);
+void launch_galerkin3(int type, const int* nf, int nsf, const double2* Sf, double2* Sc, int* err, cudaStream_t st);
+int coarse_invert3(int type, const int* n, const double2* S, double2* inv, double2* work, int* flag, cudaStream_t st);
+// dense FP64 inverse X = A^{-1} of an n x n matrix by Gauss-Jordan elimination
+// (A is overwritten; X enters as the identity; f holds n scratch entries)
+int gauss_jordan(int n, double2* A, double2* X, double2* f, int* flag, cudaStream_t st);
+
 // error handling
 void set_error(const std::string& msg);
 }  // namespace bah

@@ -305,10 +305,15 @@ int coarse_invert(int type, const StencilF64& S, double2* inv, double2* work, in
     double2* f = work + (size_t)n * n;       // n
     dim3 g((n + 127) / 128, n);
     k_dense_assemble<<<g, 128, 0, st>>>(type, S.S, S.rx, S.rz, S.n1, S.n2, A, inv);
+    return gauss_jordan(n, A, inv, f, flag, st);
+}
+
+int gauss_jordan(int n, double2* A, double2* X, double2* f, int* flag, cudaStream_t st) {
+    dim3 g((n + 127) / 128, n);
     BAH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
     for (int k = 0; k < n; ++k) {
-        k_gj_pivot<<<1, 256, 0, st>>>(n, k, A, inv, f, flag);
-        k_gj_eliminate<<<g, 128, 0, st>>>(n, k, A, inv, f);
+        k_gj_pivot<<<1, 256, 0, st>>>(n, k, A, X, f, flag);
+        k_gj_eliminate<<<g, 128, 0, st>>>(n, k, A, X, f);
     }
     BAH_CUDA_TRY(cudaGetLastError());
     int h = 0;

@@ -15,6 +15,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <utility>
 
 namespace bah {
@@ -119,6 +120,17 @@ struct Ctx {
     unsigned* bar = nullptr;                      // [0] count, [1] generation
     int* coop_err = nullptr;
 
+    // three-dimensional grids (dim == 3): n1 x n2 x n3 cells
+    int n3 = 1;
+    double h3 = 0;
+    Op3 op3{};
+    std::vector<std::array<int, 3>> d3;            // level grids
+    std::vector<std::array<double2*, 4>> s3;       // FP64 stencils (level 0: 7-point, coarser: 27-point)
+    std::vector<std::array<void*, 4>> s3s;         // the same in the cycle's vector type (levels below the coarsest)
+    std::vector<std::array<void*, 4>> v3B, v3X, v3T;
+    double2* inv3[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* inv3s[4] = {nullptr, nullptr, nullptr, nullptr};
+
     static void clear_graph(IterGraph& G) {
         if (G.exec) cudaGraphExecDestroy(G.exec);
         for (auto& e : G.ev) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
@@ -152,7 +164,7 @@ struct Ctx {
         *p = (T*)q;
         return s;
     }
-    size_t vec_len() const { return (size_t)3 * np; }
+    size_t vec_len() const { return (size_t)(dim + 1) * np; }
 };
 
 // ---------------------------------------------------------------------------
@@ -580,9 +592,101 @@ struct MG {
     }
 };
 
+// ---------------------------------------------------------------------------
+// three-dimensional multigrid: one block's cycle (Algorithm 1 applied
+// recursively; a W-cycle visits every level below the first twice, the second
+// visit starting from the first's result) and the block-acoustic
+// preconditioner e = P^{-1} D r (Eq. 3.3 - 3.5) with its four blocks
+// ---------------------------------------------------------------------------
+template <int MODE>
+struct MG3 {
+    using V = typename Prec<MODE>::V;
+    static size_t pts(const Ctx& c, int l) { return (size_t)c.d3[l][0] * c.d3[l][1] * c.d3[l][2]; }
+    static double jw(const Ctx& c, int l) { return c.o.jacobi_w[std::min(l, c.o.n_jacobi_w - 1)]; }
+    // x_out = Jacobi sweep from x_in (zero: from x_in = 0), or x_out = b - A x_in (res)
+    static void sweep(Ctx& c, int l, int q, const V* b, const V* xin, V* xout, int zero, int res, cudaStream_t st) {
+        const int ns = l == 0 ? 7 : 27;
+        const double vb = sizeof(V);
+        Prof pr(c, res ? BAH_K_RESIDUAL : BAH_K_JACOBI, st, (double)pts(c, l) * (ns * vb + (zero ? 2.0 : 3.0) * vb));
+        launch_jacobi3<V>(q, c.d3[l].data(), ns, (const V*)c.s3s[l][q], b, xin, xout, jw(c, l), zero, res, st);
+    }
+    // x = approximately A_q^{-1} b_q on level l (b_q in v3B[l][q]); zero: zero initial guess, else start from x
+    static void cycle(Ctx& c, int l, int q, V* x, bool zero, cudaStream_t st) {
+        const V* b = (const V*)c.v3B[l][q];
+        const size_t np = pts(c, l);
+        if (l == c.L - 1) {
+            const double vb = sizeof(V);
+            Prof pr(c, BAH_K_COARSE, st, (double)np * np * vb + 2.0 * np * vb);
+            const V* inv[1] = {(const V*)c.inv3s[q]};
+            const V* bb[1] = {b};
+            V* xx[1] = {x};
+            launch_coarse_apply<MODE>(1, (int)np, inv, bb, xx, st);
+            return;
+        }
+        V* cur = x;
+        V* spare = (V*)c.v3T[l][q];
+        int s0 = 0;
+        if (zero) {
+            s0 = c.o.nu_pre >= 1 ? 1 : 0;
+            // start the ping-pong so that the last sweep writes x
+            if (((c.o.nu_pre - s0) + c.o.nu_post) % 2) std::swap(cur, spare);
+            if (s0) sweep(c, l, q, b, cur, cur, 1, 0, st);
+            else cudaMemsetAsync(cur, 0, np * sizeof(V), st);
+        }
+        for (int s = s0; s < c.o.nu_pre; ++s) {
+            sweep(c, l, q, b, cur, spare, 0, 0, st);
+            std::swap(cur, spare);
+        }
+        sweep(c, l, q, b, cur, spare, 0, 1, st);
+        {
+            Prof pr(c, BAH_K_RESTRICT, st, (double)np * sizeof(V) * 1.125);
+            launch_restrict3<V>(q, c.d3[l].data(), spare, (V*)c.v3B[l + 1][q], st);
+        }
+        V* xc = (V*)c.v3X[l + 1][q];
+        cycle(c, l + 1, q, xc, true, st);
+        if (c.o.cycle == BAH_CYCLE_W && l + 1 < c.L - 1) cycle(c, l + 1, q, xc, false, st);
+        {
+            Prof pr(c, BAH_K_PROLONG, st, (double)np * sizeof(V) * 2.125);
+            launch_prolong3<V>(q, c.d3[l].data(), xc, cur, st);
+        }
+        for (int s = 0; s < c.o.nu_post; ++s) {
+            sweep(c, l, q, b, cur, spare, 0, 0, st);
+            std::swap(cur, spare);
+        }
+        if (cur != x) cudaMemcpyAsync(x, cur, np * sizeof(V), cudaMemcpyDeviceToDevice, st);
+    }
+    // z = P^{-1} D r for one right-hand side (r FP64, z in the cycle's type)
+    static void precond(Ctx& c, const double2* r, V* z, cudaStream_t st) {
+        const size_t np = c.np;
+        const double vb = sizeof(V);
+        {
+            Prof pr(c, BAH_K_DISTRIB, st, (double)np * (64.0 + 56.0 + vb));
+            launch_distrib3<V>(c.op3, r, (V*)c.v3B[0][3], st);
+        }
+        cycle(c, 0, 3, z + 3 * np, true, st);
+        {
+            V* su[3] = {(V*)c.v3B[0][0], (V*)c.v3B[0][1], (V*)c.v3B[0][2]};
+            Prof pr(c, BAH_K_URHS, st, (double)np * (48.0 + 4.0 * vb));
+            launch_urhs3<V>(c.op3, r, z + 3 * np, su, st);
+        }
+        for (int q = 0; q < 3; ++q) cycle(c, 0, q, z + q * np, true, st);
+    }
+};
+
 template <class RIN>
 static void precond_any(Ctx& c, const RIN* r, size_t rstride, void* z, size_t zstride, const Batch& bt,
                         cudaStream_t st) {
+    if constexpr (std::is_same<RIN, double2>::value) {
+        if (c.dim == 3) {
+            for (int k = 0; k < bt.nr; ++k) {
+                if (c.mode == BAH_MIXED)
+                    MG3<BAH_MIXED>::precond(c, r + k * rstride, (float2*)z + k * zstride, st);
+                else
+                    MG3<BAH_FP64>::precond(c, r + k * rstride, (double2*)z + k * zstride, st);
+            }
+            return;
+        }
+    }
     if (c.mode == BAH_MIXED) MG<BAH_MIXED>::template precond<RIN>(c, r, rstride, (float2*)z, zstride, bt, st);
     else MG<BAH_FP64>::template precond<RIN>(c, r, rstride, (double2*)z, zstride, bt, st);
 }
@@ -592,8 +696,32 @@ static double op_bytes(const Ctx& c, double in_bytes, bool residual) {
     const double coef = (c.h1 == c.h2 ? 16.0 : 32.0) + 32.0 + 8.0;
     return (double)c.np * (3.0 * in_bytes + 48.0 + coef + (residual ? 48.0 : 0.0));
 }
+// 3-D: input (4 components), FP64 output, mu, three edge means, three complex
+// diagonals, 1/(lambda+mu)
+static double op_bytes3(const Ctx& c, double in_bytes, bool residual) {
+    return (double)c.np * (4.0 * in_bytes + 64.0 + 88.0 + (residual ? 64.0 : 0.0));
+}
+// y = H x (b null) or y = b - H x on nr right-hand sides at the given element strides
+static void apply_h(Ctx& c, const double2* x, size_t sx, double2* y, size_t sy, const double2* b, size_t sb, int conj,
+                    int nr, cudaStream_t st, const int* active = nullptr) {
+    if (c.dim == 3) {
+        launch_apply3<double2>(c.op3, x, y, b, conj, nr, sx, sy, sb, st);
+        return;
+    }
+    RhsStride rs;
+    rs.s0 = sx; rs.s1 = sy; rs.s2 = sb; rs.active = active;
+    launch_elastic_apply<double2>(c.op, x, y, b, conj, st, nr, rs);
+}
 static void op_apply_z(Ctx& c, const void* z, size_t zstride, void* y, size_t ystride, const Batch& bt,
                        cudaStream_t st) {
+    if (c.dim == 3) {
+        Prof pr(c, BAH_K_OPERATOR, st, bt.nr * op_bytes3(c, (double)c.vsz, false));
+        if (c.mode == BAH_MIXED)
+            launch_apply3<float2>(c.op3, (const float2*)z, (double2*)y, nullptr, 0, bt.nr, zstride, ystride, 0, st);
+        else
+            launch_apply3<double2>(c.op3, (const double2*)z, (double2*)y, nullptr, 0, bt.nr, zstride, ystride, 0, st);
+        return;
+    }
     Prof pr(c, BAH_K_OPERATOR, st, bt.nr * op_bytes(c, (double)c.vsz, false));
     RhsStride rs;
     rs.s0 = zstride; rs.s1 = ystride; rs.active = bt.active;
@@ -605,6 +733,43 @@ static void op_apply_z(Ctx& c, const void* z, size_t zstride, void* y, size_t ys
         if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
         else launch_elastic_apply<double2>(c.op, (const double2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
     }
+}
+
+// FGMRES workspace for nbatch right-hand sides: bases V (FP64 or
+// double-float) and Z (the preconditioner's precision), Hessenberg matrices,
+// rotations, reduction partials, status slots and the per-step graphs
+static int alloc_krylov(Ctx& c, cudaStream_t st) {
+    const size_t n = c.vec_len();
+    const int m = c.m;
+    const size_t nbt = c.nbatch;
+    const size_t so = m + 2;
+    TRY(c.alloc_t(&c.V, n * (m + 1) * nbt));
+    TRY(c.alloc(&c.Z, n * m * c.vsz * nbt));
+    TRY(c.alloc_t(&c.W, n * nbt)); TRY(c.alloc_t(&c.R, n * nbt)); TRY(c.alloc_t(&c.Bs, n * nbt));
+    TRY(c.alloc_t(&c.X, n * nbt));
+    TRY(c.alloc(&c.ztmp, n * c.vsz));
+    TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m * nbt));
+    TRY(c.alloc_t(&c.h1v, so * nbt)); TRY(c.alloc_t(&c.h2v, so * nbt));
+    TRY(c.alloc_t(&c.gsflag, nbt));
+    TRY(c.alloc_t(&c.cs, so * nbt)); TRY(c.alloc_t(&c.sn, so * nbt)); TRY(c.alloc_t(&c.g, so * nbt));
+    TRY(c.alloc_t(&c.y, so * nbt));
+    TRY(c.alloc_t(&c.partial, so * RED_CTAS * nbt));
+    TRY(c.alloc_t(&c.dpart, (size_t)RED_CTAS * nbt));
+    TRY(c.alloc_t(&c.nrm, 8 * nbt));
+    TRY(c.alloc_t(&c.status, 4 * nbt));
+    TRY(c.alloc_t(&c.active, nbt));
+    TRY(c.alloc_t(&c.jk, nbt));
+    BAH_CUDA_TRY(cudaMemsetAsync(c.nrm, 0, 8 * nbt * sizeof(double), st));
+    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hstatus, (4 * (size_t)(m + 1) * nbt + 8 * nbt) * sizeof(double)));
+    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hint, kIntSlots * nbt * sizeof(int)));
+    c.ks.sv = (size_t)(m + 1) * n; c.ks.sw = n; c.ks.sp = so * RED_CTAS; c.ks.so = so;
+    c.ks.sh = (size_t)(m + 1) * m; c.ks.sz = (size_t)m * n; c.ks.sx = n; c.ks.active = c.active;
+    BAH_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    c.ig.assign(m, Ctx::IterGraph());
+    c.itev.assign(m, nullptr);
+    for (int j = 0; j < m; ++j) BAH_CUDA_TRY(cudaEventCreateWithFlags(&c.itev[j], cudaEventDisableTiming));
+    if (const char* e = getenv("BAH_NO_GRAPHS")) c.use_graphs = (e[0] == '0');
+    return BAH_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -843,42 +1008,100 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
             }
         }
     }
-    // Krylov workspace
-    const size_t n = c.vec_len();
-    const int m = c.m;
-    const size_t nbt = c.nbatch;
-    const size_t so = m + 2;
-    TRY(c.alloc_t(&c.V, n * (m + 1) * nbt));
-    TRY(c.alloc(&c.Z, n * m * c.vsz * nbt));
-    TRY(c.alloc_t(&c.W, n * nbt)); TRY(c.alloc_t(&c.R, n * nbt)); TRY(c.alloc_t(&c.Bs, n * nbt));
-    TRY(c.alloc_t(&c.X, n * nbt));
-    TRY(c.alloc(&c.ztmp, n * c.vsz));
-    TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m * nbt));
-    TRY(c.alloc_t(&c.h1v, so * nbt)); TRY(c.alloc_t(&c.h2v, so * nbt));
-    TRY(c.alloc_t(&c.gsflag, nbt));
-    TRY(c.alloc_t(&c.cs, so * nbt)); TRY(c.alloc_t(&c.sn, so * nbt)); TRY(c.alloc_t(&c.g, so * nbt));
-    TRY(c.alloc_t(&c.y, so * nbt));
-    TRY(c.alloc_t(&c.partial, so * RED_CTAS * nbt));
-    TRY(c.alloc_t(&c.dpart, (size_t)RED_CTAS * nbt));
-    TRY(c.alloc_t(&c.nrm, 8 * nbt));
-    TRY(c.alloc_t(&c.status, 4 * nbt));
-    TRY(c.alloc_t(&c.active, nbt));
-    TRY(c.alloc_t(&c.jk, nbt));
-    BAH_CUDA_TRY(cudaMemsetAsync(c.nrm, 0, 8 * nbt * sizeof(double), st));
-    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hstatus, (4 * (size_t)(m + 1) * nbt + 8 * nbt) * sizeof(double)));
-    BAH_CUDA_TRY(cudaMallocHost((void**)&c.hint, kIntSlots * nbt * sizeof(int)));
-    c.ks.sv = (size_t)(m + 1) * n; c.ks.sw = n; c.ks.sp = so * RED_CTAS; c.ks.so = so;
-    c.ks.sh = (size_t)(m + 1) * m; c.ks.sz = (size_t)m * n; c.ks.sx = n; c.ks.active = c.active;
-    BAH_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
-    c.ig.assign(m, Ctx::IterGraph());
-    c.itev.assign(m, nullptr);
-    for (int j = 0; j < m; ++j) BAH_CUDA_TRY(cudaEventCreateWithFlags(&c.itev[j], cudaEventDisableTiming));
-    if (const char* e = getenv("BAH_NO_GRAPHS")) c.use_graphs = (e[0] == '0');
+    TRY(alloc_krylov(c, st));
     if (const char* e = getenv("BAH_FUSED")) c.fused = (e[0] == '1');
     if (const char* e = getenv("BAH_TILED")) c.tiled = (e[0] == '1');
     if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
+    return BAH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// three-dimensional context: medium, fine stencils, Galerkin hierarchy with
+// the mixed intergrid, coarsest inverses, multigrid vectors, Krylov workspace
+// ---------------------------------------------------------------------------
+static int build3(Ctx& c, const bah_medium* med, cudaStream_t st) {
+    const size_t np = c.np;
+    double *lam, *mu, *rho, *gam, *cinv, *mue[3];
+    double2 *mrt, *dg[3];
+    TRY(c.alloc_t(&lam, np)); TRY(c.alloc_t(&mu, np)); TRY(c.alloc_t(&rho, np)); TRY(c.alloc_t(&gam, np));
+    BAH_CUDA_TRY(cudaMemcpyAsync(lam, med->lambda, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(mu, med->mu, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(rho, med->rho, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(gam, med->gamma, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    TRY(c.alloc_t(&cinv, np)); TRY(c.alloc_t(&mrt, np));
+    for (int e = 0; e < 3; ++e) { TRY(c.alloc_t(&mue[e], np)); TRY(c.alloc_t(&dg[e], np)); }
+    c.gam = gam;
+    Op3& o = c.op3;
+    o.n[0] = c.n1; o.n[1] = c.n2; o.n[2] = c.n3;
+    const double h[3] = {c.h1, c.h2, c.h3};
+    for (int a = 0; a < 3; ++a) { o.ih[a] = 1.0 / h[a]; o.ih2[a] = 1.0 / (h[a] * h[a]); }
+    o.muc = mu; o.cinv = cinv; o.mrt = mrt;
+    for (int e = 0; e < 3; ++e) { o.mue[e] = mue[e]; o.dg[e] = dg[e]; }
+    // level grids and FP64 stencils
+    c.d3.assign(c.L, {0, 0, 0});
+    for (int l = 0; l < c.L; ++l) c.d3[l] = {c.n1 >> l, c.n2 >> l, c.n3 >> l};
+    auto pts = [&](int l) { return (size_t)c.d3[l][0] * c.d3[l][1] * c.d3[l][2]; };
+    c.s3.assign(c.L, {nullptr, nullptr, nullptr, nullptr});
+    c.s3s.assign(c.L, {nullptr, nullptr, nullptr, nullptr});
+    for (int q = 0; q < 4; ++q) TRY(c.alloc_t(&c.s3[0][q], 7 * np));
+    launch_prep3(o, c.omega, c.alpha, lam, mu, rho, gam, cinv, mrt, mue, dg, c.s3[0].data(), st);
+    int* err;
+    TRY(c.alloc_t(&err, 2));
+    BAH_CUDA_TRY(cudaMemsetAsync(err, 0, 2 * sizeof(int), st));
+    for (int l = 1; l < c.L; ++l)
+        for (int q = 0; q < 4; ++q) {
+            TRY(c.alloc_t(&c.s3[l][q], 27 * pts(l)));
+            launch_galerkin3(q, c.d3[l - 1].data(), l == 1 ? 7 : 27, c.s3[l - 1][q], c.s3[l][q], err, st);
+        }
+    for (int l = 0; l + 1 < c.L; ++l)
+        for (int q = 0; q < 4; ++q) {
+            const size_t cnt = (l == 0 ? 7 : 27) * pts(l);
+            if (c.mode == BAH_MIXED) {
+                TRY(c.alloc(&c.s3s[l][q], cnt * sizeof(float2)));
+                launch_convert<double2, float2>(c.s3[l][q], (float2*)c.s3s[l][q], cnt, st);
+            } else {
+                c.s3s[l][q] = c.s3[l][q];
+            }
+        }
+    BAH_CUDA_TRY(cudaGetLastError());
+    int herr = 0;
+    BAH_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+        set_error("3-D Galerkin product produced a coupling beyond one coarse point");
+        return BAH_ERR_CUDA;
+    }
+    // coarsest inverses
+    {
+        const size_t nc = pts(c.L - 1);
+        void* work;
+        TRY(c.alloc(&work, (nc * nc + nc) * sizeof(double2)));
+        for (int q = 0; q < 4; ++q) {
+            TRY(c.alloc_t(&c.inv3[q], nc * nc));
+            TRY(coarse_invert3(q, c.d3[c.L - 1].data(), c.s3[c.L - 1][q], c.inv3[q], (double2*)work, err + 1, st));
+            if (c.mode == BAH_MIXED) {
+                TRY(c.alloc(&c.inv3s[q], nc * nc * sizeof(float2)));
+                launch_convert<double2, float2>(c.inv3[q], (float2*)c.inv3s[q], nc * nc, st);
+            } else {
+                c.inv3s[q] = c.inv3[q];
+            }
+        }
+    }
+    // multigrid vectors
+    c.v3X.assign(c.L, {nullptr, nullptr, nullptr, nullptr});
+    c.v3B = c.v3X; c.v3T = c.v3X;
+    for (int l = 0; l < c.L; ++l)
+        for (int q = 0; q < 4; ++q) {
+            const size_t bytes = pts(l) * c.vsz;
+            TRY(c.alloc(&c.v3X[l][q], bytes)); TRY(c.alloc(&c.v3B[l][q], bytes)); TRY(c.alloc(&c.v3T[l][q], bytes));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.v3X[l][q], 0, bytes, st));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.v3B[l][q], 0, bytes, st));
+            BAH_CUDA_TRY(cudaMemsetAsync(c.v3T[l][q], 0, bytes, st));
+        }
+    TRY(alloc_krylov(c, st));
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
     return BAH_OK;
 }
 
@@ -1104,8 +1327,9 @@ static int fgmres_batch(Ctx& c, const double2* b, double2* x, int nr, double rto
         {
             RhsStride rs;
             rs.s0 = n; rs.s1 = n; rs.s2 = n; rs.active = c.active;
-            Prof pr(c, BAH_K_OPERATOR, st, nr * op_bytes(c, 16.0, true));
-            launch_elastic_apply<double2>(c.op, x, c.R, b, 0, st, nb, rs);
+            Prof pr(c, BAH_K_OPERATOR, st, nr * (c.dim == 3 ? op_bytes3(c, 16.0, true) : op_bytes(c, 16.0, true)));
+            // 3-D: only the nr right-hand sides of this batch (x holds no more)
+            apply_h(c, x, rs.s0, c.R, rs.s1, b, rs.s2, 0, c.dim == 3 ? nr : nb, st, rs.active);
         }
         {
             Prof pr(c, BAH_K_NORM, st, (double)nr * n * 16.0, 2);
@@ -1154,7 +1378,8 @@ struct bah_ctx {
 };
 
 namespace bah {
-const OpCoef* context_op(const bah_ctx* ctx) { return &ctx->c.op; }
+// the 2-D operator coefficients (null for a 3-D context)
+const OpCoef* context_op(const bah_ctx* ctx) { return ctx->c.dim == 2 ? &ctx->c.op : nullptr; }
 size_t context_vec_len(const bah_ctx* ctx) { return ctx->c.vec_len(); }
 }  // namespace bah
 
@@ -1199,12 +1424,17 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     *out = nullptr;
     g_err.clear();
     if (!grid || !med) { set_error("grid or medium is NULL"); return BAH_ERR_ARG; }
-    if (grid->dim == 3) { set_error("3-D grids are not implemented (2-D only)"); return BAH_ERR_UNSUPPORTED; }
-    if (grid->dim != 2) { set_error("dim must be 2"); return BAH_ERR_ARG; }
+    if (grid->dim != 2 && grid->dim != 3) { set_error("dim must be 2 or 3"); return BAH_ERR_ARG; }
+    const int dim = grid->dim;
     if (!med->lambda || !med->mu || !med->rho || !med->gamma) { set_error("medium array is NULL"); return BAH_ERR_ARG; }
     if (!(med->omega > 0.0)) { set_error("omega must be > 0"); return BAH_ERR_ARG; }
-    if (grid->n[0] < 4 || grid->n[1] < 4 || !(grid->h[0] > 0.0) || !(grid->h[1] > 0.0)) {
-        set_error("need n >= 4 cells per axis and h > 0");
+    for (int a = 0; a < dim; ++a)
+        if (grid->n[a] < 4 || !(grid->h[a] > 0.0)) {
+            set_error("need n >= 4 cells per axis and h > 0");
+            return BAH_ERR_ARG;
+        }
+    if (dim == 3 && (long long)grid->n[0] * grid->n[1] * grid->n[2] * 4 > 2147483647LL) {
+        set_error("3-D grid too large (4 * cells must fit in a 32-bit index)");
         return BAH_ERR_ARG;
     }
     bah_opts o;
@@ -1221,12 +1451,21 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
         return BAH_ERR_ARG;
     }
     if (o.cycle != BAH_CYCLE_V && o.cycle != BAH_CYCLE_W) { set_error("bad cycle"); return BAH_ERR_ARG; }
+    if (dim == 3 && o.intergrid != BAH_INTERGRID_MIXED) {
+        set_error("3-D grids need intergrid = BAH_INTERGRID_MIXED (Eq. 4.4)");
+        return BAH_ERR_UNSUPPORTED;
+    }
+    if (dim == 3 && o.krylov_arith != BAH_KRYLOV_FP64) {
+        set_error("3-D grids support krylov_arith = BAH_KRYLOV_FP64 only");
+        return BAH_ERR_UNSUPPORTED;
+    }
 
     bah_ctx* h = new (std::nothrow) bah_ctx();
     if (!h) { set_error("host allocation failed"); return BAH_ERR_OOM; }
     Ctx& c = h->c;
-    c.dim = 2; c.n1 = grid->n[0]; c.n2 = grid->n[1]; c.np = c.n1 * c.n2;
+    c.dim = dim; c.n1 = grid->n[0]; c.n2 = grid->n[1]; c.np = c.n1 * c.n2;
     c.h1 = grid->h[0]; c.h2 = grid->h[1]; c.omega = med->omega;
+    if (dim == 3) { c.n3 = grid->n[2]; c.h3 = grid->h[2]; c.np *= c.n3; }
     c.o = o;
     c.mode = o.precision;
     c.vsz = c.mode == BAH_MIXED ? sizeof(float2) : sizeof(double2);
@@ -1236,27 +1475,35 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     // levels
     int L = 1;
     {
-        int a = c.n1, b = c.n2;
+        int a = c.n1, b = c.n2, d = dim == 3 ? c.n3 : 2;
+        auto halvable = [&]() { return a % 2 == 0 && b % 2 == 0 && a / 2 >= 2 && b / 2 >= 2 &&
+                                       (dim == 2 || (d % 2 == 0 && d / 2 >= 2)); };
+        auto cells = [&]() { return (long long)a * b * (dim == 3 ? d : 1); };
         if (o.levels > 0) {
             for (int l = 1; l < o.levels; ++l) {
-                if (a % 2 || b % 2 || a / 2 < 2 || b / 2 < 2) {
+                if (!halvable()) {
                     delete h;
                     set_error("grid cannot be coarsened to the requested number of levels");
                     return BAH_ERR_ARG;
                 }
-                a /= 2; b /= 2; ++L;
+                a /= 2; b /= 2; d /= 2; ++L;
             }
         } else {
             const int maxc = o.max_coarse_cells > 0 ? o.max_coarse_cells : 256;
-            while ((long long)a * b > maxc && a % 2 == 0 && b % 2 == 0 && a / 2 >= 2 && b / 2 >= 2) {
-                a /= 2; b /= 2; ++L;
+            while (cells() > maxc && halvable()) {
+                a /= 2; b /= 2; d /= 2; ++L;
             }
         }
-        if ((long long)a * b > 4096) {
+        if (cells() > 4096) {
             delete h;
             set_error("coarsest level larger than 4096 cells; use more levels");
             return BAH_ERR_ARG;
         }
+    }
+    if (dim == 3 && L < 2) {
+        delete h;
+        set_error("3-D grids need at least 2 multigrid levels (the coarsest solve takes a Galerkin 27-point stencil)");
+        return BAH_ERR_ARG;
     }
     c.L = L;
     c.alpha = o.shift_alpha >= 0.0 ? o.shift_alpha : (L < 5 ? kAlphaByLevels[L] : kAlphaDeep);
@@ -1266,7 +1513,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
         set_error("cudaStreamCreate failed");
         return BAH_ERR_CUDA;
     }
-    int s = build(c, med, st);
+    int s = dim == 3 ? build3(c, med, st) : build(c, med, st);
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (s != BAH_OK) {
@@ -1291,7 +1538,8 @@ int bah_get_info(const bah_ctx* h, bah_info* out) {
     const Ctx& c = h->c;
     out->levels = c.L;
     out->shift_alpha = c.alpha;
-    out->coarse_points = c.ln1[c.L - 1] * c.ln2[c.L - 1];
+    out->coarse_points = c.dim == 3 ? c.d3[c.L - 1][0] * c.d3[c.L - 1][1] * c.d3[c.L - 1][2]
+                                    : c.ln1[c.L - 1] * c.ln2[c.L - 1];
     out->cluster_level = c.sm_l0;
     out->cluster_ctas = c.sm_cs;
     out->cluster_smem_bytes = (long long)c.sm_bytes;
@@ -1304,7 +1552,7 @@ int bah_apply_operator(bah_ctx* h, const void* x, void* y, int nrhs, int conj, v
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = c.vec_len();
     for (int k = 0; k < nrhs; ++k)
-        launch_elastic_apply<double2>(c.op, (const double2*)x + k * n, (double2*)y + k * n, nullptr, conj ? 1 : 0, st);
+        apply_h(c, (const double2*)x + k * n, 0, (double2*)y + k * n, 0, nullptr, 0, conj ? 1 : 0, 1, st);
     BAH_CUDA_TRY(cudaGetLastError());
     return BAH_OK;
 }
@@ -1344,7 +1592,7 @@ int bah_spectral_radius(bah_ctx* h, const void* x0, int iters, double* history, 
     launch_scale_copy((const double2*)x0, c.nrm, 0, x, n, 0, 0, 1, ks, st);
     std::vector<double> hist(iters);
     for (int k = 0; k < iters; ++k) {
-        launch_elastic_apply<double2>(c.op, x, y, nullptr, 0, st);
+        apply_h(c, x, 0, y, 0, nullptr, 0, 0, 1, st);
         if (c.mode == BAH_MIXED) {
             precond_any(c, (const double2*)y, n, c.ztmp, n, one, st);
             launch_convert<float2, double2>((const float2*)c.ztmp, z, n, st);
@@ -1375,6 +1623,18 @@ int bah_block_cycle(bah_ctx* h, int block, const void* b, void* x, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     const size_t np = c.np;
     Batch one;
+    if (c.dim == 3) {
+        if (c.mode == BAH_MIXED) {
+            launch_convert<double2, float2>((const double2*)b, (float2*)c.v3B[0][block], np, st);
+            MG3<BAH_MIXED>::cycle(c, 0, block, (float2*)c.ztmp, true, st);
+            launch_convert<float2, double2>((const float2*)c.ztmp, (double2*)x, np, st);
+        } else {
+            BAH_CUDA_TRY(cudaMemcpyAsync(c.v3B[0][block], b, np * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            MG3<BAH_FP64>::cycle(c, 0, block, (double2*)x, true, st);
+        }
+        BAH_CUDA_TRY(cudaGetLastError());
+        return BAH_OK;
+    }
     if (c.mode == BAH_MIXED) {
         launch_convert<double2, float2>((const double2*)b, (float2*)c.vB[0][block], np, st);
         float2* o[1] = {(float2*)c.ztmp};
@@ -1391,6 +1651,7 @@ int bah_block_cycle(bah_ctx* h, int block, const void* b, void* x, void* stream)
 
 int bah_level_stencil(const bah_ctx* h, int block, int level, double* out, int* rx, int* rz, int* n1, int* n2) {
     if (!h || block < 0 || block > h->c.dim || level < 0 || level >= h->c.L) { set_error("bad argument"); return BAH_ERR_ARG; }
+    if (h->c.dim == 3) { set_error("bah_level_stencil describes 2-D stencils only"); return BAH_ERR_UNSUPPORTED; }
     const StencilF64& s = h->c.s64[level][block];
     if (rx) *rx = s.rx;
     if (rz) *rz = s.rz;
@@ -1449,7 +1710,8 @@ static int solve_impl(bah_ctx* h, const void* b, void* x, int nrhs, double rtol,
                                      dev_b ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         {
             Prof pr(c, BAH_K_SMALL, st, (double)nr * c.np * 32.0);
-            launch_sanitize(c.Bs, c.n1, c.n2, nr, st);
+            if (c.dim == 3) launch_sanitize3(c.Bs, c.n1, c.n2, c.n3, nr, st);
+            else launch_sanitize(c.Bs, c.n1, c.n2, nr, st);
             if (adjoint) launch_conj(c.Bs, (size_t)nr * n, st);
         }
         double2* xd = dev_x ? xk : c.X;
@@ -1503,6 +1765,7 @@ int bah_gradient(bah_ctx* h, const void* x_fwd, const void* y_adj, int nrhs, dou
                  double* g_rho, void* stream) {
     if (!h || !x_fwd || !y_adj || !g_lambda || !g_mu || !g_rho || nrhs < 0) { set_error("bad argument"); return BAH_ERR_ARG; }
     Ctx& c = h->c;
+    if (c.dim == 3) { set_error("the adjoint gradient is implemented for 2-D grids"); return BAH_ERR_UNSUPPORTED; }
     if (nrhs == 0) return BAH_OK;
     launch_gradient(c.n1, c.n2, c.h1, c.h2, c.omega, c.cinv, c.gam, c.vec_len(), nrhs, (const double2*)x_fwd,
                     (const double2*)y_adj, g_lambda, g_mu, g_rho, (cudaStream_t)stream);

@@ -139,6 +139,10 @@ extern "C" int bah_residual_norm_static(bah_ctx* ctx, const void* b, const void*
         set_error("bah_residual_norm_static: nrhs exceeds BAH_STATIC_MAX_RHS (64), the size of its static scratch");
         return BAH_ERR_ARG;
     }
+    if (!context_op(ctx)) {
+        set_error("bah_residual_norm_static is implemented for 2-D grids");
+        return BAH_ERR_UNSUPPORTED;
+    }
     if (nrhs == 0) return BAH_OK;
     int dev = 0;
     BAH_CUDA_TRY(cudaGetDevice(&dev));

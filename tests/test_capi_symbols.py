@@ -49,3 +49,20 @@ def test_default_options_follow_the_paper(built):
     assert list(monkey.jacobi_w[:3]) == [0.8, 0.8, 0.3]          # Sec. 4.4.1
     assert monkey.restart == 20 and monkey.precision == bah.BAH_MIXED
     assert bah.status_string(bah.BAH_ERR_ARG) == "BAH_ERR_ARG"
+
+
+def test_3d_option_checks_run_before_any_device_call(built):
+    """3-D contexts need the mixed intergrid of Eq. 4.4 (the paper's 3-D
+    transfer), the FP64 Krylov basis and at least two levels; each violation is
+    reported by bah_create before it touches a device."""
+    import numpy as np
+    n = (8, 8, 8)
+    med = [np.full(n[::-1], v) for v in (2.0, 1.0, 1.0, 0.0)]
+    cases = [(dict(intergrid=bah.BAH_INTERGRID_BILINEAR), bah.BAH_ERR_UNSUPPORTED),
+             (dict(intergrid=bah.BAH_INTERGRID_MIXED, krylov_arith=bah.BAH_KRYLOV_DF), bah.BAH_ERR_UNSUPPORTED),
+             (dict(intergrid=bah.BAH_INTERGRID_MIXED, levels=1), bah.BAH_ERR_ARG),
+             (dict(intergrid=bah.BAH_INTERGRID_MIXED, levels=4), bah.BAH_ERR_ARG)]
+    for kw, want in cases:
+        with pytest.raises(bah.BahError) as e:
+            bah.bah_create(n, (0.1, 0.1, 0.1), *med, 3.0, bah.bah_default_opts(**kw))
+        assert e.value.status == want, (kw, bah.last_error())
