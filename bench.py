@@ -286,7 +286,9 @@ def run_bah(args):
     stream = torch.cuda.current_stream()
 
     def solve_once(s, bb, xx):
-        nr = bb.shape[0] if bb.ndim == 4 else 1
+        # right-hand sides in the buffer: its entries over one padded vector's
+        nr = (bb.numel() if hasattr(bb, "numel") else bb.size) // s.vector_len
+        assert nr * s.vector_len == (bb.numel() if hasattr(bb, "numel") else bb.size)
         st, stats = bah.bah_solve(s.ctx, bb, xx, nr, 1e-6)
         if nr == 1:
             return st, stats[0]
