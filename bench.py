@@ -7,6 +7,11 @@ nu in [0.25, 0.45], rho = 0.31 Vp^0.25, 10 points per shear wavelength,
 in HBM, setup excluded.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bah|reference]
+                  [--config c2|c3|c4|c5]
+
+--config selects another workload: c3 (1024^2 random field), c4 (1024x512
+layered, 64 sources in one batch) or c5 (128^3 random field, run with the
+paper's 3-D cycle: W(2,2), mixed intergrid, Jacobi 0.8/0.8/0.2).
 
 The main arm (bah) times the mixed-precision solve (bfloat16 coefficients,
 FP32 multigrid, FP64 FGMRES / operator / coarsest solve) and, beside it, the
@@ -118,6 +123,16 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def rhs_count(buf, vector_len):
+    """Right-hand sides held by a torch tensor or numpy array: its entries over
+    one padded vector's (a single 3-D vector has four array dimensions, so the
+    array's rank tells nothing)."""
+    total = int(buf.numel()) if hasattr(buf, "numel") else int(buf.size)
+    if vector_len <= 0 or total % vector_len:
+        raise ValueError(f"buffer of {total} entries is not a whole number of {vector_len}-entry vectors")
+    return total // vector_len
 
 
 def oracle_counts():
@@ -286,9 +301,7 @@ def run_bah(args):
     stream = torch.cuda.current_stream()
 
     def solve_once(s, bb, xx):
-        # right-hand sides in the buffer: its entries over one padded vector's
-        nr = (bb.numel() if hasattr(bb, "numel") else bb.size) // s.vector_len
-        assert nr * s.vector_len == (bb.numel() if hasattr(bb, "numel") else bb.size)
+        nr = rhs_count(bb, s.vector_len)
         st, stats = bah.bah_solve(s.ctx, bb, xx, nr, 1e-6)
         if nr == 1:
             return st, stats[0]
