@@ -99,7 +99,8 @@ def parse():
     ap.add_argument("--max-coarse", type=int, default=256)
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--krylov", default=None, choices=["fp64", "df"])
-    ap.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per batch (default: all sources)")
+    ap.add_argument("--rhs-block", type=int, default=0,
+                    help="right-hand sides per batch (default: all sources; -1: chosen by the autotuner)")
     ap.add_argument("--gradient", action="store_true", help="also time the adjoint gradient of a receiver misfit")
     ap.add_argument("--maxit", type=int, default=20000)
     # the benchmark's tuned cycle: V(1,3) with alpha 0.8 (searched at a resolution of 0.1 on this
@@ -278,6 +279,7 @@ def run_bah(args):
     nsrc = len(mine)
     job_units = nsrc_all if nsrc_all > 1 else world      # solves completed by the whole job per step
     rhs_block = args.rhs_block if args.rhs_block > 0 else nsrc
+    tuned = None
     opts = dict(precision=bah.BAH_MIXED, levels=args.levels, max_coarse_cells=args.max_coarse, restart=args.restart,
                 krylov_arith=bah.BAH_KRYLOV_DF if args.krylov == "df" else bah.BAH_KRYLOV_FP64,
                 rhs_block=rhs_block, maxit=args.maxit, shift_alpha=args.alpha,
@@ -285,6 +287,12 @@ def run_bah(args):
                 nu_pre=int(args.nu.split(",")[0]), nu_post=int(args.nu.split(",")[1]),
                 jacobi_w=tuple(float(v) for v in args.jacobi.split(",")),
                 intergrid=bah.BAH_INTERGRID_MIXED if args.intergrid == "mixed" else bah.BAH_INTERGRID_BILINEAR)
+    if args.rhs_block < 0:
+        # batch size and launch variant by timing short solves (autotune.py), before the timed context
+        from paper_2411_15897_gb300 import autotune
+        tuned = autotune.tune(prob, nsrc, {k: v for k, v in opts.items() if k not in ("rhs_block", "maxit")}, iters=10)
+        os.environ.update(autotune.VARIANTS[tuned.variant])
+        rhs_block = opts["rhs_block"] = tuned.rhs_block
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
     solver = bah.Solver.from_problem(prob, **opts)
@@ -527,7 +535,7 @@ def run_bah(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.config, args.config), "grid": list(prob.n),
                    "unknowns": int(sum(W.compact_sizes(prob.n))), "sources": nsrc_all, "sources_per_rank": nsrc,
-                   "rhs_block": rhs_block,
+                   "rhs_block": rhs_block, "autotune": tuned.as_dict() if tuned else None,
                    "levels": levels, "cycle": f"{args.cycle}({args.nu})", "alpha": solver.alpha,
                    "jacobi": args.jacobi, "intergrid": args.intergrid, "context_bytes": context_bytes,
                    "cluster_levels_from": solver.info["cluster_level"], "restart": args.restart, "iters": iters[-1],
