@@ -44,7 +44,8 @@ template <int NS> __host__ __device__ constexpr int scentre() { return NS == 7 ?
 // the edge means of mu.  mue[e] belongs to the pair of axes other than e; at a
 // point whose coordinates along that pair are (a, b) it is the mean of mu over
 // the four cells around the edge at nodes (a, b), zero on boundary edges
-// (reading R2 of the 2-D operator, per axis pair).
+// (where the tangential derivative is dropped with the zero normal
+// displacement), the same averaging as the 2-D operator's nodes.
 // ---------------------------------------------------------------------------
 __global__ void k_prep3_cells(int n1, int n2, int n3, double omega, const double* __restrict__ lam,
                               const double* __restrict__ mu, const double* __restrict__ rho,
