@@ -66,15 +66,16 @@ def test_block_eigen_closed_form_2d():
         np.testing.assert_allclose(S.A[1] @ v2, ev2 * v2, rtol=0, atol=1e-11 * abs(ev2) * np.abs(v2).max())
 
 
-def test_Hp_closed_form_pressure_velocity():
+@pytest.mark.parametrize("n,h,modes", [((8, 6), (0.25, 0.3), [(0, 0), (2, 1), (7, 5)]),
+                                        ((6, 5, 4), (0.25, 0.3, 0.2), [(0, 0, 0), (2, 1, 3), (5, 4, 1)])])
+def test_Hp_closed_form_pressure_velocity(n, h, modes):
     """Eq. 3.2 / 3.4 with a constant medium: (lambda+mu) H_p acts on the Neumann
     modes as (lambda+2mu) lap - omega^2 rho~, an acoustic operator with the
-    pressure velocity Vp (Sec. 3)."""
-    n, h = (8, 6), (0.25, 0.3)
+    pressure velocity Vp (Sec. 3), in 2-D and 3-D."""
     lam, mu, rho, gam, om = 3.0, 1.5, 1.2, 0.7, 5.0
     S = const_system(n, h, lam, mu, rho, gam, om)
     rt = rho * (1 - 1j * gam / om)
-    for k in [(0, 0), (2, 1), (7, 5)]:
+    for k in modes:
         v = cos_mode(n, k)
         ev = ((lam + 2 * mu) * lap_eig(n, h, k) - om ** 2 * rt) / (lam + mu)
         np.testing.assert_allclose(S.Hp @ v, ev * v, rtol=0, atol=1e-11 * (abs(ev) + 100))
@@ -82,10 +83,11 @@ def test_Hp_closed_form_pressure_velocity():
         np.testing.assert_allclose(S.Ap @ v, evp * v, rtol=0, atol=1e-11 * (abs(evp) + 100))
 
 
-def test_Hp_identity_variable_medium():
+@pytest.mark.parametrize("n", [(9, 8), (6, 5, 4)])
+def test_Hp_identity_variable_medium(n):
     """H_p = B B^T + A_p C equals B B^T diag((lambda+2mu)/(lambda+mu)) -
-    omega^2 diag(rho~/(lambda+mu)) (algebra of Eq. 3.2, 3.4)."""
-    p = W.random_medium((9, 8), 5)
+    omega^2 diag(rho~/(lambda+mu)) (algebra of Eq. 3.2, 3.4), in 2-D and 3-D."""
+    p = W.random_medium(n, 5)
     S = elastic.from_problem(p)
     rhs = S.BBt @ sp.diags((S.lam + 2 * S.mu) / (S.lam + S.mu)) - S.omega ** 2 * sp.diags(S.rho_t / (S.lam + S.mu))
     assert abs(S.Hp - rhs).max() < 1e-9 * abs(rhs).max()
