@@ -93,16 +93,18 @@ def test_Hp_identity_variable_medium(n):
     assert abs(S.Hp - rhs).max() < 1e-9 * abs(rhs).max()
 
 
-def test_mu0_reduction_to_acoustic():
+@pytest.mark.parametrize("n,h,modes", [((8, 7), (0.2, 0.25), [(1, 0), (3, 4), (6, 6)]),
+                                        ((6, 5, 4), (0.2, 0.25, 0.3), [(1, 0, 0), (3, 4, 2), (5, 1, 3)])])
+def test_mu0_reduction_to_acoustic(n, h, modes):
     """Eq. 2.4: with mu = 0 the elastic system reduces to an acoustic Helmholtz
     equation with velocity sqrt(lambda/rho): the Schur complement -C - B A^{-1}
-    B^T, times omega^2 rho, acts on the Neumann modes as lap - omega^2/Vp^2."""
-    n, h = (8, 7), (0.2, 0.25)
+    B^T, times omega^2 rho, acts on the Neumann modes as lap - omega^2/Vp^2
+    (2-D and 3-D)."""
     lam, rho, om = 4.0, 1.5, 3.0
     S = const_system(n, h, lam, 0.0, rho, 0.0, om)
     Ainv = sp.diags(1.0 / sp.block_diag(S.A).diagonal())
     Schur = -S.C - S.B @ Ainv @ S.Bt
-    for k in [(1, 0), (3, 4), (6, 6)]:
+    for k in modes:
         v = cos_mode(n, k)
         ev = lap_eig(n, h, k) - om ** 2 * rho / lam
         np.testing.assert_allclose(om ** 2 * rho * (Schur @ v), ev * v, atol=1e-10 * (abs(ev) + 1))
@@ -152,11 +154,12 @@ def test_manufactured_solution_second_order():
         assert 3.0 < ep0 / ep1 < 5.5, errs
 
 
-def test_interior_commutator_vanishes_constant_medium():
+@pytest.mark.parametrize("n,h", [((9, 7), (0.2, 0.2)), ((6, 5, 4), (0.2, 0.2, 0.2))])
+def test_interior_commutator_vanishes_constant_medium(n, h):
     """Footnote to Eq. 2.10 and Sec. 4 (homogeneous media): on a MAC grid with
     constant coefficients the commutator Xi = B A - A_p B is exactly zero
-    (here on every row, with the boundary reading R1)."""
-    S = const_system((9, 7), (0.2, 0.2))
+    (here on every row, with the boundary reading R1), in 2-D and 3-D."""
+    S = const_system(n, h)
     X = S.commutator()
     scale = abs(S.B).max() * abs(S.Ablk).max()
     assert abs(X).max() < 1e-12 * scale
