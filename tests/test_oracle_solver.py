@@ -153,10 +153,12 @@ def test_theorem1_spectrum():
     assert abs(np.abs(eT).max() - np.abs(eZ).max()) < 1e-8 * scale
 
 
-def test_exact_block_preconditioner_matches_dense_definition():
+@pytest.mark.parametrize("n", [(7, 6), (5, 4, 4)])
+def test_exact_block_preconditioner_matches_dense_definition(n):
     """With exact block inverses one preconditioning step equals the dense
-    solution of P e = D r (Eq. 3.1, 3.5), with and without a shift."""
-    p = W.random_medium((7, 6), 11)
+    solution of P e = D r (Eq. 3.1, 3.5), with and without a shift, in 2-D and
+    3-D."""
+    p = W.random_medium(n, 11)
     S = elastic.from_problem(p)
     rng = np.random.default_rng(3)
     r = rng.standard_normal(S.H.shape[0]) + 1j * rng.standard_normal(S.H.shape[0])
