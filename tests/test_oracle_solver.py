@@ -343,3 +343,50 @@ def test_linear_medium_rho_below_one_without_shift():
     rT, _ = theorem1.power_T(S, precond.exact(S, 0.0).apply, x0, 150)
     assert rZ < 1.0
     assert abs(rZ - rT) <= 0.02 * rT
+
+
+@pytest.mark.parametrize("n,kinds", [((8, 8), ['c', 'c']), ((8, 8, 8), ['n', 'c', 'c'])])
+def test_w_cycle_is_two_coarse_iterations(n, kinds):
+    """Sec. 2.2: a W-cycle solves the coarse problem with two iterations of
+    the coarse cycle where the V-cycle takes one.  As linear operators on three
+    levels: with B_1 the level-1 cycle (an approximate inverse of A_1) and
+    E_1 = I - B_1 A_1, the V-cycle is the two-grid cycle of level 0 with the
+    coarse solve B_1 and the W-cycle the same with (I - E_1^2) A_1^{-1}."""
+    p = W.random_medium(n, 71, abc=1)
+    S = elastic.from_problem(p)
+    A = (S.Hp_shifted(0.4) if kinds[0] == 'c' else S.A_shifted(0, 0.4)).tocsr()
+    intergrid = "mixed" if len(n) == 3 else "bilinear"
+
+    def as_matrix(cyc, size, **kw):
+        return np.column_stack([cyc(np.eye(size)[:, i].astype(complex), **kw) for i in range(size)])
+
+    hV = mg.build_hierarchy(A, n, kinds, 3, cycle="V", intergrid=intergrid)
+    hW = mg.build_hierarchy(A, n, kinds, 3, cycle="W", intergrid=intergrid)
+    N0, N1 = A.shape[0], hV.ops[1].shape[0]
+    MV = as_matrix(lambda b: mg.cycle(hV, b), N0)
+    MW = as_matrix(lambda b: mg.cycle(hW, b), N0)
+    B1 = as_matrix(lambda b: mg.cycle(hV, b, level=1), N1)
+    A1 = hV.ops[1].toarray()
+    E1 = np.eye(N1) - B1 @ A1
+    B1w = (np.eye(N1) - E1 @ E1) @ np.linalg.inv(A1)
+
+    def two_grid(Bc):
+        """Level-0 cycle (nu_pre sweeps from zero, coarse correction with Bc,
+        nu_post sweeps) as a matrix."""
+        A0 = hV.ops[0].toarray()
+        d = hV.diag[0]
+        w = mg.jacobi_weight(0, hV.weights)
+        Sm = np.eye(N0) - w * (A0 / d[:, None])           # one sweep's error propagation
+        Ns = w * np.diag(1.0 / d)                          # one sweep from zero
+        X = np.zeros((N0, N0), complex)
+        for k in range(hV.nu_pre):
+            X = Sm @ X + Ns
+        R, P = hV.R[0].toarray(), hV.P[0].toarray()
+        X = X + P @ Bc @ R @ (np.eye(N0) - A0 @ X)
+        for _ in range(hV.nu_post):
+            X = Sm @ X + Ns
+        return X
+
+    np.testing.assert_allclose(MV, two_grid(B1), atol=1e-10 * np.abs(MV).max())
+    np.testing.assert_allclose(MW, two_grid(B1w), atol=1e-10 * np.abs(MW).max())
+    assert np.abs(MW - MV).max() > 1e-3 * np.abs(MV).max()
