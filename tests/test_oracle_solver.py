@@ -116,6 +116,26 @@ def test_jacobi_is_textbook_and_vcycle_contracts():
     assert res[-1] / res[0] < 0.5 ** 5
 
 
+def test_jacobi_weights_apply_per_level_from_the_finest():
+    """Sec. 4.4.1 (and Sec. 4.5 in 3-D): the damping weights are listed for the
+    first (finest), second and third level, the last one repeating below.  A
+    two-level cycle with one pre-sweep and no post-sweep is
+    x_1 + P A_c^{-1} R (b - A x_1) with x_1 = w_0 D^{-1} b, w_0 the FIRST listed
+    weight."""
+    p = W.random_medium((16, 16), 3)
+    S = elastic.from_problem(p)
+    A = S.Hp_shifted(0.4).tocsr()
+    wts = (0.5, 0.7, 0.9)
+    h = mg.build_hierarchy(A, (16, 16), ['c', 'c'], 2, weights=wts, nu_pre=1, nu_post=0)
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    x1 = 0.5 * b / A.diagonal()
+    P, R = h.P[0], h.R[0]
+    ref = x1 + P @ np.linalg.solve((R @ A @ P).toarray(), R @ (b - A @ x1))
+    np.testing.assert_allclose(mg.cycle(h, b), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    assert [mg.jacobi_weight(lv, wts) for lv in range(5)] == [0.5, 0.7, 0.9, 0.9, 0.9]
+
+
 def test_galerkin_constant_coefficient_cell_stencil():
     """Galerkin coarsening (Eq. 4.3) of the 1-D cell-centred Laplacian
     [-1 2 -1] with bilinear P and R = P^T/2 gives, away from the boundary, the
