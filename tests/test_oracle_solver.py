@@ -267,6 +267,23 @@ def test_unrestarted_gmres_finite_termination():
     assert r.converged and r.iters <= N
 
 
+def test_stopping_rule_is_relative_and_scale_invariant():
+    """Sec. 4 stopping rule (relative residual < 1e-6): ||b - H x|| <= rtol ||b||,
+    so scaling b by a power of two (exact in floating point) scales x by the
+    same factor and leaves the iteration count unchanged; an absolute rule
+    would stop earlier for small b and later for large b."""
+    p = W.random_medium((12, 10), 13)
+    S = elastic.from_problem(p)
+    H = S.H
+    b = W.padded_to_compact(W.point_source(p), p.n)
+    pc = precond.multigrid(S, 2, 0.1)
+    runs = [fgmres.fgmres(lambda v: H @ v, sc * b, pc.apply, restart=200, rtol=1e-6, maxit=500)
+            for sc in (2.0 ** -14, 1.0, 2.0 ** 20)]
+    assert all(r.converged and r.relres_true <= 1e-6 for r in runs)
+    assert runs[0].iters == runs[1].iters == runs[2].iters
+    np.testing.assert_array_equal(runs[2].x, 2.0 ** 20 * runs[1].x)
+
+
 def test_solve_reaches_direct_solution_c1():
     """Workload C1: the block-acoustic FGMRES(20) solution has true relative
     residual <= 1e-6 and matches the sparse direct solution to the accuracy the
