@@ -8,11 +8,15 @@ from oracle import elastic, gradient as G
 
 
 def setup(n=(10, 8), seed=3, nsrc=2):
-    p = W.random_medium(n, seed, abc=2)
+    p = W.random_medium(n, seed, abc=2 if len(n) == 2 else 1)
     S = elastic.from_problem(p)
-    srcs = [(2 + 4 * k, 3) for k in range(nsrc)]
+    if len(n) == 2:
+        srcs = [(2 + 4 * k, 3) for k in range(nsrc)]
+        rec = [(i, 2) for i in range(n[0])]
+    else:                      # sources and a receiver plane on the u_3 faces at x_3-index 2
+        srcs = [(1 + 2 * k, 2, 3) for k in range(nsrc)]
+        rec = [(i, j, 2) for j in range(n[1]) for i in range(n[0])]
     B = np.column_stack([W.padded_to_compact(W.point_source(p, s), p.n) for s in srcs])
-    rec = [(i, 2) for i in range(n[0])]
     rows = G.receiver_rows(S, rec)
     # observed data from a perturbed ("true") medium
     rng = np.random.default_rng(seed + 100)
@@ -40,11 +44,14 @@ def test_receiver_rows_pick_the_u_d_component():
     assert np.flatnonzero(c)[0] == G.receiver_rows(S, [(3, 2)])[0]
 
 
+@pytest.mark.parametrize("n", [(10, 8), (5, 4, 4)])
 @pytest.mark.parametrize("field", ["lambda", "mu", "rho"])
-def test_adjoint_gradient_matches_central_differences(field):
+def test_adjoint_gradient_matches_central_differences(field, n):
     """dJ/dm_k by the adjoint state equals the central difference of J with
-    exact (sparse direct) solves, on random cells of a 10x8 random medium."""
-    p, S, B, D, rows = setup()
+    exact (sparse direct) solves, on random cells of a 10x8 (2-D) and a
+    5x4x4 (3-D, three displacement blocks and edge means per axis pair)
+    random medium."""
+    p, S, B, D, rows = setup(n)
     J0, g, X, Y = G.gradient(S, B, D, rows, params=(field,))
     rng = np.random.default_rng(11)
     for k in rng.choice(S.ncells, 6, replace=False):
