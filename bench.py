@@ -66,6 +66,8 @@ WORKLOADS = {
 # Jacobi 0.8, 0.8, 0.2) on 5 levels (coarsest 8^3) with the FP64 Krylov basis
 PRESETS = {
     "2d": dict(levels=0, alpha=0.8, cycle="V", nu="1,3", jacobi="0.8,0.8,0.3", intergrid="bilinear", krylov="df"),
+    # many sources: the library's own cycle, V(1,2) with the shift by level count (1.0 at 7 levels)
+    "c4": dict(alpha=-1.0, nu="1,2"),
     "c5": dict(levels=5, alpha=0.4, cycle="W", nu="2,2", jacobi="0.8,0.8,0.2", intergrid="mixed", krylov="fp64"),
 }
 WORKLOAD = WORKLOADS["c2"]
@@ -113,7 +115,7 @@ def parse():
     ap.add_argument("--krylov-fp64-steps", type=int, default=2,
                     help="also time the same solve with the Krylov basis in IEEE FP64")
     args = ap.parse_args()
-    for k, v in PRESETS.get(args.config, PRESETS["2d"]).items():
+    for k, v in {**PRESETS["2d"], **PRESETS.get(args.config, {})}.items():
         if getattr(args, k) is None:
             setattr(args, k, v)
     return args
@@ -134,6 +136,31 @@ def rhs_count(buf, vector_len):
     if vector_len <= 0 or total % vector_len:
         raise ValueError(f"buffer of {total} entries is not a whole number of {vector_len}-entry vectors")
     return total // vector_len
+
+
+def auto_levels(n, max_coarse):
+    """The level count the library picks with levels = 0: halve every axis
+    while the grid has more than max_coarse cells and every axis stays even
+    and at least 2 after halving."""
+    n = list(n)
+    L = 1
+    while int(np.prod(n)) > max_coarse and all(v % 2 == 0 and v // 2 >= 2 for v in n):
+        n = [v // 2 for v in n]
+        L += 1
+    return L
+
+
+def workload_config(args, prob, levels, alpha, world):
+    """The ``config`` object of the JSON line: the workload and the solver
+    settings that define the measured solve, identical in both arms."""
+    nsrc_all = len(prob.sources)
+    return {"workload": WORKLOADS.get(args.config, args.config), "grid": [int(v) for v in prob.n],
+            "unknowns": int(sum(W.compact_sizes(prob.n))), "sources": nsrc_all, "levels": int(levels),
+            "cycle": f"{args.cycle}({args.nu})", "alpha": round(float(alpha), 6), "jacobi": args.jacobi,
+            "intergrid": args.intergrid, "restart": args.restart, "rtol": 1e-6,
+            "l2": f"GPU arm: flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "parallelism": (f"sources split over {world} GPUs, no exchange during the solves" if nsrc_all > 1
+                            else f"independent replicas of the solve on {world} GPUs")}
 
 
 def oracle_counts():
@@ -173,12 +200,15 @@ def run_reference(args):
     prob = W.config(args.config)
     counts = oracle_counts().get(args.config)
     from oracle import precond
-    levels = counts["levels"] if counts else 6
-    alpha = counts["alpha"] if counts else precond.default_alpha(levels)
-    nu = tuple(counts.get("nu", (1, 2))) if counts else (1, 2)
-    its = counts["iters"] if counts else None
+    levels = args.levels if args.levels else auto_levels(prob.n, args.max_coarse)
+    alpha = args.alpha if args.alpha >= 0 else precond.default_alpha(levels)
+    nu = tuple(int(v) for v in args.nu.split(","))
+    same = (bool(counts) and counts.get("levels") == levels and abs(counts.get("alpha", -1.0) - alpha) < 1e-12
+            and tuple(counts.get("nu", (1, 2))) == nu)
+    its = counts["iters"] if same else None
     per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=args.warmup + args.steps,
-                               nu=nu)
+                               nu=nu, cycle=args.cycle, weights=tuple(float(v) for v in args.jacobi.split(",")),
+                               intergrid=args.intergrid)
     per = per[args.warmup:]
     t_iter = statistics.mean(per)
     if its is None:
@@ -191,8 +221,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * args.cpu_iters * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOADS.get(args.config, args.config), "levels": levels,
-                                        "alpha": alpha, "cycle": f"V{nu}"},
+        "data": "synthetic", "config": workload_config(args, prob, levels, alpha, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.cpu_iters} FGMRES iterations per step after setup ({setup:.1f} s); {note}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -533,15 +562,10 @@ def run_bah(args):
                      else "f64 Krylov basis, Gram-Schmidt and operator")
                   + ", f64 Hessenberg / Givens / true residual"),
         "data": "synthetic",
-        "config": {"workload": WORKLOADS.get(args.config, args.config), "grid": list(prob.n),
-                   "unknowns": int(sum(W.compact_sizes(prob.n))), "sources": nsrc_all, "sources_per_rank": nsrc,
-                   "rhs_block": rhs_block, "autotune": tuned.as_dict() if tuned else None,
-                   "levels": levels, "cycle": f"{args.cycle}({args.nu})", "alpha": solver.alpha,
-                   "jacobi": args.jacobi, "intergrid": args.intergrid, "context_bytes": context_bytes,
-                   "cluster_levels_from": solver.info["cluster_level"], "restart": args.restart, "iters": iters[-1],
-                   "relres_true": relres, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                   "parallelism": (f"sources split over {world} GPUs, no exchange during the solves" if nsrc_all > 1
-                                   else f"independent replicas of the solve on {world} GPUs")},
+        "config": workload_config(args, prob, levels, solver.alpha, world),
+        "run": {"sources_per_rank": nsrc, "rhs_block": rhs_block, "autotune": tuned.as_dict() if tuned else None,
+                "context_bytes": context_bytes, "cluster_levels_from": solver.info["cluster_level"],
+                "iters": iters[-1], "relres_true": relres},
         "fp64": fp64,
         "krylov_fp64": kfp64,
         "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,

@@ -204,7 +204,10 @@ int bah_solve_adjoint(bah_ctx* ctx, const void* b, void* y, int nrhs, double rto
  * observed data, nrec complex values per source (device).  Writes
  * adj_s = Q^H (Q x_s - d_s) (nrhs full padded vectors, zero off the
  * receivers) and misfit[s] = 1/2 ||Q x_s - d_s||^2 (device, nrhs doubles).
- * Indices must lie in [0, vector_len); they are not checked on the device. */
+ * An index listed more than once is a receiver counted more than once: its
+ * data enter J once per listing and adj_s sums the residuals of every
+ * listing (added in the order of rec).  Indices must lie in
+ * [0, vector_len); they are not checked on the device. */
 int bah_misfit(bah_ctx* ctx, const void* x, const void* d, const int* rec, int nrec, int nrhs, void* adj_src,
                double* misfit, void* stream);
 
@@ -292,27 +295,29 @@ int bah_profile_read(bah_ctx* ctx, bah_profile* out);
 /* ---------------------------------------------------------------------------
  * Allocation-free relative residual.  The paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc at the point where they
- * need the number -- code running inside CUDA stream capture (an allocation
- * there breaks the capture), real-time loops that forbid allocator calls
- * after start-up, and hosts whose device memory belongs to another
- * allocator.
+ * need the number -- real-time loops that forbid allocator calls after
+ * start-up (an allocation can block for an unbounded time), and hosts whose
+ * device memory all belongs to another allocator (a framework's caching
+ * pool, which a direct cudaMalloc would bypass or find exhausted).
  *
  * relres[k] = ||b_k - H x_k||_2 / ||b_k||_2 (0 when b_k = 0) for k < nrhs,
  * written to the DEVICE array relres (nrhs doubles) on the stream, without
  * synchronising.  b, x: nrhs device vectors in the layout above
- * (boundary-normal entries read as zero).
+ * (boundary-normal entries read as zero).  2-D contexts only.
  *
  * Scratch: the per-block partial sums live in one file-scope device array of
  * 2 * BAH_STATIC_MAX_RHS * 296 doubles (296 KiB), which every GPU that loads
  * the library holds until the process exits.  The call launches two kernels
  * and allocates nothing (no cudaMalloc, no allocating library routine).
  * The first call on a device looks up that array's device address with the
- * device current; make that first call before any stream capture.  Every
- * call overwrites the slots it reads, so nothing needs clearing, but all
- * calls share the array: calls that overlap on the GPU (other streams or
- * threads) race and must be serialised by the caller.
+ * device current and keeps it; make that first call before any stream
+ * capture, and do not call this function on a device after cudaDeviceReset
+ * (which unloads the array).  Every call overwrites the slots it reads, so
+ * nothing needs clearing, but all calls share the array: calls that overlap
+ * on the GPU (other streams or threads) race and must be serialised by the
+ * caller.
  * Errors: BAH_ERR_ARG (NULL pointer, nrhs < 0, nrhs > BAH_STATIC_MAX_RHS),
- * BAH_ERR_CUDA.
+ * BAH_ERR_UNSUPPORTED (a 3-D context), BAH_ERR_CUDA.
  * ------------------------------------------------------------------------- */
 #define BAH_STATIC_MAX_RHS 64
 int bah_residual_norm_static(bah_ctx* ctx, const void* b, const void* x, int nrhs, double* relres, void* stream);

@@ -102,7 +102,7 @@ def gradient(sys: ElasticSystem, B, D, rows, params=("lambda", "mu", "rho")):
     Y = np.zeros_like(X)
     for s in range(B.shape[1]):
         rhs = np.zeros(H.shape[0], dtype=np.complex128)
-        rhs[rows] = R[:, s]
+        np.add.at(rhs, rows, R[:, s])       # Q^H r: a receiver listed twice contributes twice
         Y[:, s] = luH.solve(rhs)
     out = {}
     for prm in params:

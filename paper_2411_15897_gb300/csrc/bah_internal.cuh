@@ -168,38 +168,7 @@ template <class V, class CC> struct LvlSet {
     int staged;        // Galerkin-level sweeps may stage their inputs in shared memory
 };
 
-// device-resident descriptor of one multigrid level for the cooperative cycle
-struct CoopLevel {
-    int n1, n2;
-    double w;                 // Jacobi damping on this level
-    const void* S[3];         // stencils (storage precision), levels >= 1
-    int rx[3], rz[3];
-    void* b[3];               // right-hand side, iterate and temporary per block
-    void* x[3];
-    void* t[3];
-};
-struct CoopArgs {
-    const CoopLevel* lv;      // device array indexed by level
-    int l0, L, b0, nb, nu_pre, nu_post, intergrid;
-    const void* inv[3];       // coarsest inverses in the cycle's vector type (FP64 or FP32 complex)
-    double2* bc64[3];         // coarsest right-hand side in FP64
-    unsigned* bar_count;
-    unsigned* bar_gen;
-    int* err;
-};
-
-// cluster cycle: levels l0..L-1 of one block set, one cluster per block and
-// right-hand side (per-level buffers hold consecutive right-hand sides at a
-// stride of the level's point count)
 constexpr int kMaxLevels = 16;
-struct ClusterArgs {
-    const CoopLevel* lv;      // device array indexed by level
-    int l0, L, b0, nb, nu_pre, nu_post, intergrid;
-    int wcycle;               // 0: V-cycle, 1: W-cycle
-    int warm;                 // 1: start level l0 from the values in its x buffer
-    const void* inv[3];       // coarsest inverses in the cycle's vector type
-    const int* active;        // per-right-hand-side flags, or null
-};
 // shared-memory-resident cluster multigrid (mixed mode): levels l0 .. L-1 of
 // one block set, one cluster per block and right-hand side; lv[k] is level
 // l0 + k, its rows split in slabs of rp rows per CTA, and off_* are byte
@@ -227,11 +196,6 @@ size_t smmg_layout(SmArgs& a, const int* n1, const int* n2, const int* nslot_max
 // sets the kernel attributes; returns how many clusters of cs CTAs fit (0: none)
 int smmg_prepare(int rm, int cs, size_t smem);
 int launch_cluster_mg(const SmArgs& a, int rm, int nrhs, int cs, size_t smem, cudaStream_t st);
-
-template <int MODE>
-int cluster_size_for(int max_radius, int want, int coarse_pts);
-template <int MODE>
-int launch_cluster_cycle(const ClusterArgs& a, int max_radius, int nrhs, int csize, int coarse_pts, cudaStream_t st);
 
 // right-hand-side batching: element strides between consecutive right-hand
 // sides for up to three pointers of a launch (blockIdx.y or .z is the
@@ -289,30 +253,9 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 template <int MODE>
 void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                      typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride = 0);
-// tiled fused level visit (zero initial guess, one pre- and two post-sweeps):
-// the smoothed iterate into s.blk[z].xout and R r into coarse_b; then
-// x_out = two sweeps on (x_in + P e)
-template <int MODE>
-void launch_down_tiled(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
-                       const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
-                       typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride);
-template <int MODE>
-void launch_up_tiled(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
-                     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
-                     const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride);
 template <int MODE>
 void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                         const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride = 0);
-template <int MODE>
-void launch_smooth_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
-                            const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
-                            typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st);
-template <int MODE>
-void launch_prolong_smooth(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
-                           const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
-                           const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st);
-template <int MODE>
-int launch_coop_cycle(const CoopArgs& a, int max_radius, int nsm, cudaStream_t st);
 template <int MODE>
 void launch_coarse_apply(int nb, int npts, const typename Prec<MODE>::V* const* inv, const typename Prec<MODE>::V* const* b,
                          typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs = 1, RhsStride rs = RhsStride());

@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
         for (int lt = tid; lt < nown(a.lv[k]); lt += nth) d[lt] = s[lt];
     };
 
-    // ---- the cycle: an explicit walk over the recursion (see k_cluster_cycle) ----
+    // ---- the cycle: an explicit walk over the recursion of Algorithm 1 ----
     unsigned xs[kMaxLevels], ts[kMaxLevels];
     int stage[kMaxLevels];
     bool warm[kMaxLevels];

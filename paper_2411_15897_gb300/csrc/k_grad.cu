@@ -21,8 +21,11 @@ void launch_conj(double2* v, size_t n, cudaStream_t st) {
     k_conj<<<RED_CTAS * 2, 256, 0, st>>>(v, n);
 }
 
-// adj[s][rec[q]] = x[s][rec[q]] - d[s][q]  (adj zeroed beforehand);
-// misfit[s] = 1/2 sum_q |x - d|^2  (one CTA per source, fixed order)
+// adj_s = Q^H (Q x_s - d_s) (adj zeroed beforehand): adj[s][rec[q]] gathers
+// x[s][rec[q]] - d[s][q] of every q naming that entry, so a receiver listed
+// twice is counted twice, as in J; one thread adds them in the order of q, so
+// the result does not depend on scheduling.  misfit[s] = 1/2 sum_q |x - d|^2
+// (one CTA per source, fixed-order block reduction).
 __global__ void __launch_bounds__(256) k_misfit(const double2* __restrict__ x, const double2* __restrict__ d,
                                                 const int* __restrict__ rec, int nrec, size_t vlen, double2* adj,
                                                 double* misfit) {
@@ -32,10 +35,14 @@ __global__ void __launch_bounds__(256) k_misfit(const double2* __restrict__ x, c
     double2* as = adj + (size_t)s * vlen;
     double acc = 0.0;
     for (int q = threadIdx.x; q < nrec; q += blockDim.x) {
-        const int i = rec[q];
-        const double2 r = csub(xs[i], ds[q]);
-        as[i] = r;
+        const double2 r = csub(xs[rec[q]], ds[q]);
         acc += r.x * r.x + r.y * r.y;
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < nrec; ++q) {
+            const int i = rec[q];
+            as[i] = cadd(as[i], csub(xs[i], ds[q]));
+        }
     }
     __shared__ double sh[256];
     sh[threadIdx.x] = acc;

@@ -6,6 +6,7 @@
 //     solve with P = [A B^T; 0 H_p] (Eq. 3.5).
 #include "bah_internal.cuh"
 #include "df.cuh"
+#include "op_rows.cuh"
 
 namespace bah {
 
@@ -52,47 +53,9 @@ __global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __re
     const double2 z = make_double2(0.0, 0.0);
     auto U1 = [&](int ii, int jj) { return (ii >= 1 && ii < n1 && jj >= 0 && jj < n2) ? ld64(x1, jj * n1 + ii) : z; };
     auto U2 = [&](int ii, int jj) { return (ii >= 0 && ii < n1 && jj >= 1 && jj < n2) ? ld64(x2, jj * n1 + ii) : z; };
-    const double2 p = ld64(xp, t);
-    const double sg = conj ? -1.0 : 1.0;
-
-    // u1 row: grad_h^T A_e(mu) grad_h - omega^2 M on x_1-faces, plus (grad_h p)_1
-    double2 y1 = z, y2 = z;
-    if (i >= 1) {
-        const double2 u = U1(i, j);
-        double2 d = c.d1[t];
-        d.y *= sg;
-        double2 a = cmul(d, u);
-        const double2 uw = U1(i - 1, j), ue = U1(i + 1, j), us = U1(i, j - 1), un = U1(i, j + 1);
-        const double kw = c.cx[t - 1], ke = c.cx[t];
-        const double ks = c.nz[t], kn = (j + 1 < n2) ? c.nz[t + n1] : 0.0;
-        a.x -= kw * uw.x + ke * ue.x + ks * us.x + kn * un.x;
-        a.y -= kw * uw.y + ke * ue.y + ks * us.y + kn * un.y;
-        const double2 pw = ld64(xp, t - 1);
-        a.x += c.ihx * (p.x - pw.x);
-        a.y += c.ihx * (p.y - pw.y);
-        y1 = a;
-    }
-    if (j >= 1) {
-        const double2 u = U2(i, j);
-        double2 d = c.d2[t];
-        d.y *= sg;
-        double2 a = cmul(d, u);
-        const double2 us = U2(i, j - 1), un = U2(i, j + 1), uw = U2(i - 1, j), ue = U2(i + 1, j);
-        const double ks = c.cz[t - n1], kn = c.cz[t];
-        const double kw = c.nx[t], ke = (i + 1 < n1) ? c.nx[t + 1] : 0.0;
-        a.x -= ks * us.x + kn * un.x + kw * uw.x + ke * ue.x;
-        a.y -= ks * us.y + kn * un.y + kw * uw.y + ke * ue.y;
-        const double2 ps = ld64(xp, t - n1);
-        a.x += c.ihz * (p.x - ps.x);
-        a.y += c.ihz * (p.y - ps.y);
-        y2 = a;
-    }
-    // p row: B u - C p,  B = grad_h^T (minus divergence)
-    const double2 u1c = U1(i, j), u1e = U1(i + 1, j), u2c = U2(i, j), u2n = U2(i, j + 1);
-    const double ci = c.cinv[t];
-    double2 yp;
-    yp.x = c.ihx * (u1c.x - u1e.x) + c.ihz * (u2c.x - u2n.x) - ci * p.x;
-    yp.y = c.ihx * (u1c.y - u1e.y) + c.ihz * (u2c.y - u2n.y) - ci * p.y;
+    auto P = [&](int g) { return ld64(xp, g); };
+    double2 y1, y2, yp;
+    elastic_rows(c, i, j, t, conj ? -1.0 : 1.0, U1, U2, P, y1, y2, yp);
     if (b) {
         if (i >= 1) y1 = csub(b[t], y1);
         if (j >= 1) y2 = csub(b[np + t], y2);

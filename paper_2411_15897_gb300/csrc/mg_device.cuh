@@ -1,6 +1,5 @@
-// Per-point multigrid arithmetic shared by the level kernels (k_mg.cu) and
-// the tiled fused level kernels (k_mg_tiled.cu): the level-0 5-point operator
-// read from per-point coefficient arrays, the Galerkin stencil of radius
+// Per-point multigrid arithmetic shared by the level kernels: the level-0
+// 5-point operator read from per-point coefficient arrays, the Galerkin stencil of radius
 // (rx, rz) <= RM, and the diagonal.  The iterate is read through an accessor
 // X(flat index), so callers may serve it from global or shared memory; the
 // arithmetic (and its order) is the same for every caller.

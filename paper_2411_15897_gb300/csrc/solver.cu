@@ -103,22 +103,11 @@ struct Ctx {
     cudaStream_t cap_stream = nullptr;
     std::vector<cudaEvent_t> itev;
     bool use_graphs = true;
-    bool fused = false;                  // fused multigrid kernels (BAH_FUSED=1) when nu_pre == 1 and nu_post >= 1
     bool staged = true;                  // shared-memory staging of Galerkin-level sweeps (BAH_STAGED=0: off)
-    bool tiled = false;                  // tiled fused level visits (opt-in, BAH_TILED=1): measured 3% slower
-                                         // than the separate launches on the 512x512 workload
-    // cooperative cycle over levels 1..L-1 (one launch per block set)
-    bool coop = false;                   // opt-in (BAH_COOP=1): measured slower than separate launches
-    int cl_l0 = 0;                       // first level run by the cluster kernel (0: off)
-    int cl_size = 0;                     // CTAs per cluster
     int sm_l0 = 0;                       // first level of the shared-memory cluster multigrid (0: off)
     int sm_cs = 0, sm_rm = 2;            // its CTAs per cluster and stencil radius bound
     size_t sm_bytes = 0;                 // its dynamic shared memory per CTA
     int nsm = 0;
-    CoopLevel* coop_lv[4] = {nullptr, nullptr, nullptr, nullptr};   // device descriptors per block set
-    double2* bc64[3] = {nullptr, nullptr, nullptr};
-    unsigned* bar = nullptr;                      // [0] count, [1] generation
-    int* coop_err = nullptr;
 
     // three-dimensional grids (dim == 3): n1 x n2 x n3 cells
     int n3 = 1;
@@ -314,64 +303,6 @@ struct MG {
         return t;
     }
 
-    // levels 1..L-1 of the cycle in one cooperative launch (one right-hand
-    // side): right-hand side in vB[1], result in vX[1]
-    static void coop_levels(Ctx& c, int b0, int nb, cudaStream_t st) {
-        CoopArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.lv = c.coop_lv[b0 == 2 ? 0 : (b0 == 1 ? 3 : (nb == 2 ? 1 : 2))];
-        a.l0 = 1; a.L = c.L; a.b0 = b0; a.nb = nb;
-        a.nu_pre = c.o.nu_pre; a.nu_post = c.o.nu_post; a.intergrid = c.o.intergrid;
-        int rmax = 1;
-        for (int z = 0; z < nb; ++z) {
-            a.inv[z] = c.invs[b0 + z];
-            a.bc64[z] = c.bc64[b0 + z];
-            rmax = std::max(rmax, std::max(c.s64[1][b0 + z].rx, c.s64[1][b0 + z].rz));
-        }
-        a.bar_count = c.bar; a.bar_gen = c.bar + 1; a.err = c.coop_err;
-        double bytes = 0;
-        const double vs = sizeof(V), ccs = sizeof(CC);
-        for (int l = 1; l < c.L - 1; ++l) {
-            const double npl = (double)c.ln1[l] * c.ln2[l];
-            bytes += 14.5 * vs * npl * nb + 3.0 * coef_bytes(c, l, b0, nb) + ccs * npl * nb;
-        }
-        const double npc = (double)c.ln1[c.L - 1] * c.ln2[c.L - 1];
-        bytes += nb * (npc * npc * vs + 32.0 * npc);
-        Prof pr(c, BAH_K_COOP, st, bytes);
-        launch_coop_cycle<MODE>(a, rmax, c.nsm, st);
-    }
-
-    // levels cl_l0..L-1 of a V-cycle in one cluster launch: right-hand sides in
-    // vB[cl_l0], results in vX[cl_l0] (bt.nr right-hand sides at the level's stride)
-    static void cluster_levels(Ctx& c, int b0, int nb, const Batch& bt, cudaStream_t st, bool warm = false) {
-        ClusterArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.lv = c.coop_lv[b0 == 2 ? 0 : (b0 == 1 ? 3 : (nb == 2 ? 1 : 2))];
-        a.l0 = c.cl_l0; a.L = c.L; a.b0 = b0; a.nb = nb;
-        a.wcycle = c.o.cycle == BAH_CYCLE_W; a.warm = warm;
-        a.nu_pre = c.o.nu_pre; a.nu_post = c.o.nu_post; a.intergrid = c.o.intergrid;
-        a.active = bt.active;
-        int rmax = 1;
-        for (int z = 0; z < nb; ++z) {
-            a.inv[z] = c.invs[b0 + z];
-            for (int l = c.cl_l0; l < c.L; ++l)
-                rmax = std::max(rmax, std::max(c.s64[l][b0 + z].rx, c.s64[l][b0 + z].rz));
-        }
-        const double vs = sizeof(V);
-        double bytes = 0, visits = 1;
-        for (int l = c.cl_l0; l < c.L - 1; ++l) {
-            const double npl = (double)c.ln1[l] * c.ln2[l];
-            const int sweeps = c.o.nu_pre + c.o.nu_post + 1;      // smoothing sweeps and the residual
-            bytes += visits * (sweeps * (coef_bytes(c, l, b0, nb) + 3.0 * vs * npl * nb * bt.nr) +
-                               3.5 * vs * npl * nb * bt.nr);
-            if (a.wcycle && l + 1 < c.L - 1) visits *= 2;
-        }
-        const int npc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
-        bytes += visits * nb * ((double)npc * npc * vs + 2.0 * npc * vs * bt.nr);
-        Prof pr(c, BAH_K_CLUSTER, st, bytes);
-        launch_cluster_cycle<MODE>(a, rmax, bt.nr, c.cl_size, npc, st);
-    }
-
     // levels sm_l0..L-1 held in one cluster's shared memory per block and
     // right-hand side (mixed mode): right-hand sides in vB[sm_l0], results in
     // vX[sm_l0]; warm: start from the values in vX[sm_l0]
@@ -450,52 +381,7 @@ struct MG {
         V* cx[3];
         for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
         const bool wcyc = c.o.cycle == BAH_CYCLE_W;
-        const bool tiled = c.tiled && !x0 && c.o.nu_pre == 1 && c.o.nu_post == 2 && c.ln1[l] >= 8 && c.ln2[l] >= 8;
-        if (tiled && !(bt.nr == 1 && c.fused)) {
-            // one launch for the zero-guess sweep, the residual and the
-            // restriction (smoothed iterate into oth), one for the prolongation
-            // and the two post-sweeps (oth + P e -> cur)
-            {
-                Prof pr(c, BAH_K_TILED, st, nr * nb * npl * (vs * 2.25 + (double)ccs) + cb_);
-                launch_down_tiled<MODE>(set(c, l, b0, nb, nullptr, 0, oth, oth_s, bt), pf5, w, cb, c.o.intergrid, st,
-                                        nplc);
-            }
-            if (c.sm_l0 == l + 1) {
-                smem_levels(c, b0, nb, bt, st);
-                if (wcyc && l + 1 < c.L - 1) smem_levels(c, b0, nb, bt, st, true);
-            } else if (c.cl_l0 == l + 1) {
-                cluster_levels(c, b0, nb, bt, st);
-                if (wcyc && l + 1 < c.L - 1) cluster_levels(c, b0, nb, bt, st, true);
-            } else {
-                cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
-                if (wcyc && l + 1 < c.L - 1) cycle(c, l + 1, b0, nb, cx, nplc, bt, st, true);
-            }
-            {
-                Prof pr(c, BAH_K_TILED, st, nr * nb * npl * vs * 3.25 + 2.0 * cb_);
-                launch_up_tiled<MODE>(set(c, l, b0, nb, oth, oth_s, cur, cur_s, bt), pf5, w, cx, st, nplc);
-            }
-        } else if (bt.nr == 1 && c.fused && !wcyc && !x0 && c.o.nu_pre == 1 && c.o.nu_post >= 1) {
-            // pre-smoothing + residual + restriction in one launch
-            {
-                Prof pr(c, BAH_K_RESTRICT, st, cb_ + nb * npl * vs * 2.25);
-                launch_smooth_restrict<MODE>(set(c, l, b0, nb, nullptr, 0, cur, cur_s, bt), pf5, w, cb,
-                                             c.o.intergrid, st);
-            }
-            if (c.sm_l0 == l + 1) smem_levels(c, b0, nb, bt, st);
-            else if (c.cl_l0 == l + 1) cluster_levels(c, b0, nb, bt, st);
-            else cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
-            // prolongation + correction + first post-smoothing sweep
-            {
-                Prof pr(c, BAH_K_PROLONG, st, sweep + nb * npl * vs * 0.25);
-                launch_prolong_smooth<MODE>(set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt), pf5, w, cx, st);
-                swap_cur();
-            }
-            for (int s = 1; s < c.o.nu_post; ++s) {
-                Prof pr(c, BAH_K_JACOBI, st, sweep);
-                launch_jacobi<MODE>(set(c, l, b0, nb, cur, cur_s, oth, oth_s, bt), pf5, w, 0, st);
-                swap_cur();
-            }
-        } else {
+        {
             // With a zero initial guess the caller's buffer holds nothing yet: if the
             // sweeps below swap the two buffers an odd number of times, start in the
             // other one, so that the last sweep lands in the caller's buffer and no
@@ -534,13 +420,9 @@ struct MG {
                 launch_restrict<MODE>(rs, cb, c.o.intergrid, st, nplc);
             }
             // coarse-grid correction
-            if (l == 0 && c.coop && !wcyc && bt.nr == 1) coop_levels(c, b0, nb, st);
-            else if (c.sm_l0 == l + 1) {
+            if (c.sm_l0 == l + 1) {
                 smem_levels(c, b0, nb, bt, st);
                 if (wcyc && l + 1 < c.L - 1) smem_levels(c, b0, nb, bt, st, true);
-            } else if (c.cl_l0 == l + 1) {
-                cluster_levels(c, b0, nb, bt, st);
-                if (wcyc && l + 1 < c.L - 1) cluster_levels(c, b0, nb, bt, st, true);
             } else {
                 cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
                 if (wcyc && l + 1 < c.L - 1) cycle(c, l + 1, b0, nb, cx, nplc, bt, st, true);
@@ -912,75 +794,15 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
             BAH_CUDA_TRY(cudaMemsetAsync(c.vB[l][b], 0, bytes, st));
             BAH_CUDA_TRY(cudaMemsetAsync(c.vT[l][b], 0, bytes, st));
         }
-    // cooperative cycle descriptors
     {
         int dev = 0;
         BAH_CUDA_TRY(cudaGetDevice(&dev));
         BAH_CUDA_TRY(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
-        int coopok = 0;
-        BAH_CUDA_TRY(cudaDeviceGetAttribute(&coopok, cudaDevAttrCooperativeLaunch, dev));
-        if (const char* e = getenv("BAH_COOP")) c.coop = (e[0] == '1');
-        if (!coopok || c.L < 3) c.coop = false;
-        const int npc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
-        for (int b = 0; b < 3; ++b) TRY(c.alloc_t(&c.bc64[b], npc));
-        TRY(c.alloc(( void**)&c.bar, 2 * sizeof(unsigned)));
-        TRY(c.alloc_t(&c.coop_err, 1));
-        BAH_CUDA_TRY(cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), st));
-        BAH_CUDA_TRY(cudaMemsetAsync(c.coop_err, 0, sizeof(int), st));
-        // block sets: {p}, {u1, u2}, {u1}, {u2}
-        for (int set = 0; set < 4; ++set) {
-            const int b0 = set == 0 ? 2 : (set == 3 ? 1 : 0), nb = set == 1 ? 2 : 1;
-            std::vector<CoopLevel> lv(c.L);
-            for (int l = 0; l < c.L; ++l) {
-                CoopLevel& q = lv[l];
-                std::memset(&q, 0, sizeof(q));
-                q.n1 = c.ln1[l]; q.n2 = c.ln2[l];
-                q.w = c.o.jacobi_w[std::min(l, c.o.n_jacobi_w - 1)];
-                for (int z = 0; z < nb; ++z) {
-                    const int b = b0 + z;
-                    q.S[z] = c.sst[l][b];
-                    q.rx[z] = c.s64[l][b].rx; q.rz[z] = c.s64[l][b].rz;
-                    q.b[z] = c.vB[l][b]; q.x[z] = c.vX[l][b]; q.t[z] = c.vT[l][b];
-                }
-            }
-            TRY(c.alloc_t(&c.coop_lv[set], c.L));
-            BAH_CUDA_TRY(cudaMemcpyAsync(c.coop_lv[set], lv.data(), c.L * sizeof(CoopLevel), cudaMemcpyHostToDevice, st));
-        }
-    }
-    // cluster kernel for the small levels (opt-in, BAH_CLUSTER=1): from the
-    // first level below the fine grid with at most BAH_CLUSTER_PTS points
-    // (default 16384); BAH_CLUSTER_SIZE sets the CTAs per cluster (default 16,
-    // halved until the device can co-schedule a cluster).  Measured slower than
-    // separate launches on the 512x512 workload: each phase waits on L2
-    // latency, and the coarsest dense product has too few loads in flight on
-    // one cluster's SMs.
-    {
-        bool on = false;
-        if (const char* e = getenv("BAH_CLUSTER")) on = e[0] == '1';
-        on = on && c.L >= 2 && c.L <= kMaxLevels;
-        long long maxpts = 16384;
-        if (const char* e = getenv("BAH_CLUSTER_PTS")) maxpts = atoll(e);
-        int want = 16;
-        if (const char* e = getenv("BAH_CLUSTER_SIZE")) want = std::max(2, std::min(16, atoi(e)));
-        c.cl_l0 = 0;
-        if (on) {
-            for (int l = 1; l < c.L - 1; ++l)
-                if ((long long)c.ln1[l] * c.ln2[l] <= maxpts) { c.cl_l0 = l; break; }
-        }
-        if (c.cl_l0 > 0) {
-            int rmax = 1;
-            for (int l = c.cl_l0; l < c.L; ++l)
-                for (int b = 0; b < 3; ++b) rmax = std::max(rmax, std::max(c.s64[l][b].rx, c.s64[l][b].rz));
-            const int npc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
-            c.cl_size = c.mode == BAH_MIXED ? cluster_size_for<BAH_MIXED>(rmax, want, npc)
-                                            : cluster_size_for<BAH_FP64>(rmax, want, npc);
-            if (c.cl_size < 2) c.cl_l0 = 0;
-        }
     }
     // shared-memory cluster multigrid (mixed mode; BAH_SMEM_MG=0 turns it off):
     // from the first level below the fine grid whose levels, down to the
     // coarsest, fit in the shared memory of one cluster (16 CTAs, else 8)
-    if (c.mode == BAH_MIXED && c.L >= 3 && c.L <= kMaxLevels && c.cl_l0 == 0) {
+    if (c.mode == BAH_MIXED && c.L >= 3 && c.L <= kMaxLevels) {
         bool on = true;
         if (const char* e = getenv("BAH_SMEM_MG")) on = e[0] != '0';
         int dev = 0, optin = 0;
@@ -1009,8 +831,6 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
         }
     }
     TRY(alloc_krylov(c, st));
-    if (const char* e = getenv("BAH_FUSED")) c.fused = (e[0] == '1');
-    if (const char* e = getenv("BAH_TILED")) c.tiled = (e[0] == '1');
     if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
@@ -1726,15 +1546,6 @@ static int solve_impl(bah_ctx* h, const void* b, void* x, int nrhs, double rtol,
         if (s != BAH_OK && first_fail == BAH_OK) first_fail = s;
     }
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
-    if (c.coop) {
-        int err = 0;
-        BAH_CUDA_TRY(cudaMemcpy(&err, c.coop_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err) {
-            set_error("grid barrier of the cooperative multigrid cycle timed out");
-            cudaMemset(c.coop_err, 0, sizeof(int));
-            return BAH_ERR_CUDA;
-        }
-    }
     return first_fail;
 }
 

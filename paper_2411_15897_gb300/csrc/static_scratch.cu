@@ -3,21 +3,27 @@
 // memory.
 //
 // Why it exists: some callers cannot call cudaMalloc at the point where they
-// need this number -- code running inside CUDA stream capture (a cudaMalloc
-// there breaks the capture), real-time or embedded loops that forbid
-// allocator calls after start-up, and hosts whose device memory belongs to
-// another allocator.  The rest of the library keeps its scratch in the
-// context; this entry point keeps its scratch (the per-block partial sums of
-// the reduction) in one file-scope device array instead, so a call only
-// launches kernels.
+// need this number -- real-time or embedded loops that forbid allocator calls
+// after start-up (an allocation can block for an unbounded time), and hosts
+// whose device memory all belongs to another allocator (a framework's caching
+// pool, which a direct cudaMalloc would bypass or find exhausted).  The rest
+// of the library keeps its scratch in the context; this entry point keeps its
+// scratch (the per-block partial sums of the reduction) in one file-scope
+// device array instead, so a call only launches kernels.
 //
 // The kernel is a variant of the library's residual + norm pair: one pass
-// forms b - H x cell by cell (the FP64 operator of the mixed system, written
-// out again here) and reduces |b - Hx|^2 and |b|^2 per block into the static
-// array; a second kernel sums the partials in a fixed order and writes the
-// ratio.  The results agree with the relative residual bah_solve reports up
-// to rounding order.
+// forms b - H x cell by cell (with the same per-cell operator rows as the
+// operator kernels, op_rows.cuh) and reduces |b - Hx|^2 and |b|^2 per block
+// into the static array; a second kernel sums the partials in a fixed order
+// and writes the ratio.  The results agree with the relative residual
+// bah_solve reports up to rounding order.
+//
+// The device address of the array is looked up once per device and kept for
+// the life of the process.  cudaDeviceReset unloads the library's device code
+// and with it the array, so the cached address is stale afterwards: this
+// entry point must not be called on a device after cudaDeviceReset.
 #include "bah_internal.cuh"
+#include "op_rows.cuh"
 
 namespace bah {
 
@@ -30,8 +36,6 @@ static __device__ __align__(256) double g_static_scratch[2 * BAH_STATIC_MAX_RHS 
 
 // device address of g_static_scratch per device, looked up on the first call
 static double* g_scratch_addr[64] = {nullptr};
-
-__device__ __forceinline__ double2 s_ld(const double2* p, int idx) { return p[idx]; }
 
 __device__ __forceinline__ double block_sum_d(double v) {
     __shared__ double sh[8];
@@ -63,44 +67,21 @@ __global__ void __launch_bounds__(256) k_static_residual_partial(OpCoef c, const
     double rr = 0.0, bn = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < np; t += gridDim.x * blockDim.x) {
         const int i = t % n1, j = t / n1;
-        auto U1 = [&](int ii, int jj) { return (ii >= 1 && ii < n1 && jj >= 0 && jj < n2) ? s_ld(x1, jj * n1 + ii) : z; };
-        auto U2 = [&](int ii, int jj) { return (ii >= 0 && ii < n1 && jj >= 1 && jj < n2) ? s_ld(x2, jj * n1 + ii) : z; };
-        const double2 p = xp[t];
+        auto U1 = [&](int ii, int jj) { return (ii >= 1 && ii < n1 && jj >= 0 && jj < n2) ? x1[jj * n1 + ii] : z; };
+        auto U2 = [&](int ii, int jj) { return (ii >= 0 && ii < n1 && jj >= 1 && jj < n2) ? x2[jj * n1 + ii] : z; };
+        auto P = [&](int g) { return xp[g]; };
+        double2 y1, y2, yp;
+        elastic_rows(c, i, j, t, 1.0, U1, U2, P, y1, y2, yp);
         if (i >= 1) {
-            const double2 u = U1(i, j);
-            double2 a = cmul(c.d1[t], u);
-            const double2 uw = U1(i - 1, j), ue = U1(i + 1, j), us = U1(i, j - 1), un = U1(i, j + 1);
-            const double kw = c.cx[t - 1], ke = c.cx[t];
-            const double ks = c.nz[t], kn = (j + 1 < n2) ? c.nz[t + n1] : 0.0;
-            a.x -= kw * uw.x + ke * ue.x + ks * us.x + kn * un.x;
-            a.y -= kw * uw.y + ke * ue.y + ks * us.y + kn * un.y;
-            const double2 pw = xp[t - 1];
-            a.x += c.ihx * (p.x - pw.x);
-            a.y += c.ihx * (p.y - pw.y);
-            const double2 r = csub(b[t], a);
+            const double2 r = csub(b[t], y1);
             rr += r.x * r.x + r.y * r.y;
             bn += b[t].x * b[t].x + b[t].y * b[t].y;
         }
         if (j >= 1) {
-            const double2 u = U2(i, j);
-            double2 a = cmul(c.d2[t], u);
-            const double2 us = U2(i, j - 1), un = U2(i, j + 1), uw = U2(i - 1, j), ue = U2(i + 1, j);
-            const double ks = c.cz[t - n1], kn = c.cz[t];
-            const double kw = c.nx[t], ke = (i + 1 < n1) ? c.nx[t + 1] : 0.0;
-            a.x -= ks * us.x + kn * un.x + kw * uw.x + ke * ue.x;
-            a.y -= ks * us.y + kn * un.y + kw * uw.y + ke * ue.y;
-            const double2 ps = xp[t - n1];
-            a.x += c.ihz * (p.x - ps.x);
-            a.y += c.ihz * (p.y - ps.y);
-            const double2 r = csub(b[np + t], a);
+            const double2 r = csub(b[np + t], y2);
             rr += r.x * r.x + r.y * r.y;
             bn += b[np + t].x * b[np + t].x + b[np + t].y * b[np + t].y;
         }
-        const double2 u1c = U1(i, j), u1e = U1(i + 1, j), u2c = U2(i, j), u2n = U2(i, j + 1);
-        const double ci = c.cinv[t];
-        double2 yp;
-        yp.x = c.ihx * (u1c.x - u1e.x) + c.ihz * (u2c.x - u2n.x) - ci * p.x;
-        yp.y = c.ihx * (u1c.y - u1e.y) + c.ihz * (u2c.y - u2n.y) - ci * p.y;
         const double2 r = csub(b[2 * np + t], yp);
         rr += r.x * r.x + r.y * r.y;
         bn += b[2 * np + t].x * b[2 * np + t].x + b[2 * np + t].y * b[2 * np + t].y;

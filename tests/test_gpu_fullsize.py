@@ -1,0 +1,84 @@
+"""Full-size parity of the two larger 2-D workloads, in the launch
+configuration the benchmark times, against the CPU oracle's assembled H.
+
+* 1024 x 1024 smooth random medium (log Vp Gaussian random field): the mixed
+  solve must reach a true relative residual ||b - H x|| / ||b|| <= 1e-6
+  recomputed with the oracle's H (the stopping rule of Sec. 4); the plain FP64
+  solve of the same system must too, and the two solutions are compared: the
+  relative difference is bounded by the conditioning times the two residuals,
+  so it is reported and checked against a loose bound only.
+* 1024 x 512 layered medium with 64 point sources in one batch: every
+  source's true residual, recomputed with the oracle's H, must be <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import elastic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+import bench  # noqa: E402
+import paper_2411_15897_gb300 as bah  # noqa: E402
+
+
+def bench_opts(config, **over):
+    """Solver options of the benchmark's preset for a workload."""
+    pr = dict(bench.PRESETS["2d"])
+    pr.update(bench.PRESETS.get(config, {}))
+    nu = [int(v) for v in pr["nu"].split(",")]
+    o = dict(precision=bah.BAH_MIXED, levels=pr["levels"], shift_alpha=pr["alpha"],
+             cycle=bah.BAH_CYCLE_W if pr["cycle"] == "W" else bah.BAH_CYCLE_V, nu_pre=nu[0], nu_post=nu[1],
+             jacobi_w=tuple(float(v) for v in pr["jacobi"].split(",")),
+             intergrid=bah.BAH_INTERGRID_MIXED if pr["intergrid"] == "mixed" else bah.BAH_INTERGRID_BILINEAR,
+             krylov_arith=bah.BAH_KRYLOV_DF if pr["krylov"] == "df" else bah.BAH_KRYLOV_FP64, maxit=20000)
+    o.update(over)
+    return o
+
+
+def true_relres(S, p, b, x):
+    bc = W.padded_to_compact(b, p.n)
+    xc = W.padded_to_compact(x, p.n)
+    return float(np.linalg.norm(bc - S.H @ xc) / np.linalg.norm(bc)), xc
+
+
+def test_c3_full_size_mixed_and_fp64_against_oracle_operator():
+    p = W.config("c3")
+    S = elastic.from_problem(p)
+    b = W.point_source(p)
+    xs = {}
+    for name, prec in (("mixed", bah.BAH_MIXED), ("fp64", bah.BAH_FP64)):
+        s = bah.Solver.from_problem(p, **bench_opts("c3", precision=prec))
+        x, status, st = s.solve(torch.from_numpy(b).cuda(), rtol=1e-6)
+        assert status == bah.BAH_OK, (name, st)
+        torch.cuda.synchronize()
+        rr, xc = true_relres(S, p, b, x.cpu().numpy())
+        assert rr <= 1e-6, (name, rr, st)
+        xs[name] = xc
+        s.close()
+    err = float(np.linalg.norm(xs["mixed"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
+    print(f"C3 ||x_mixed - x_fp64|| / ||x_fp64|| = {err:.3e}")
+    assert err <= 1e-2, err
+
+
+def test_c4_full_size_64_sources_one_batch_against_oracle_operator():
+    p = W.config("c4")
+    S = elastic.from_problem(p)
+    B = W.all_sources(p)
+    assert B.shape[0] == 64
+    s = bah.Solver.from_problem(p, **bench_opts("c4", rhs_block=64))
+    x, status, st = s.solve(torch.from_numpy(B).cuda(), rtol=1e-6)
+    assert status == bah.BAH_OK, [q for q in st if q["status"] != bah.BAH_OK][:3]
+    torch.cuda.synchronize()
+    X = x.cpu().numpy()
+    Bc = np.column_stack([W.padded_to_compact(B[k], p.n) for k in range(64)])
+    Xc = np.column_stack([W.padded_to_compact(X[k], p.n) for k in range(64)])
+    R = Bc - S.H @ Xc
+    rr = np.linalg.norm(R, axis=0) / np.linalg.norm(Bc, axis=0)
+    print(f"C4 true relative residuals: max {rr.max():.3e}, iterations max {max(q['iters'] for q in st)}")
+    assert rr.max() <= 1e-6, rr.max()
+    s.close()

@@ -86,6 +86,33 @@ def test_misfit_adjoint_source_and_adjoint_solve():
     s.close()
 
 
+def test_misfit_repeated_receivers_sum():
+    """A receiver index listed twice (with different data) enters the misfit
+    twice and the adjoint source as the sum of both residuals: Q^H (Q x - d)
+    as the oracle forms it (np.add.at), to 1e-13."""
+    p, B, Bc, rec, rows, D = problem()
+    s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, rhs_block=2)
+    rec2 = np.concatenate([rec, rec[3:6], rec[4:5]]).astype(np.int32)
+    rows2 = np.concatenate([rows, rows[3:6], rows[4:5]])
+    D2 = np.concatenate([D, D[3:6] * (1 + 0.3j), D[4:5] * (0.5 - 1j)])
+    xh = np.stack([W.random_vector(p.n, 70 + k) for k in range(2)])
+    x = torch.from_numpy(xh).cuda()
+    Dd = torch.from_numpy(np.ascontiguousarray(D2.T)).cuda()
+    adj = torch.empty_like(x)
+    mis = torch.empty(2, dtype=torch.float64, device="cuda")
+    bah.bah_misfit(s.ctx, x, Dd, torch.from_numpy(rec2).cuda(), rec2.size, 2, adj, mis)
+    torch.cuda.synchronize()
+    for k in range(2):
+        xc = W.padded_to_compact(xh[k], p.n)
+        resid = xc[rows2] - D2[:, k]
+        ref = np.zeros_like(xc)
+        np.add.at(ref, rows2, resid)
+        assert abs(mis[k].item() - 0.5 * np.sum(np.abs(resid) ** 2)) <= 1e-12 * mis[k].item()
+        ac = W.padded_to_compact(adj[k].cpu().numpy(), p.n)
+        assert np.abs(ac - ref).max() <= 1e-13 * np.abs(ref).max()
+    s.close()
+
+
 def _J(p, lam, mu, rho, b, d, r, rtol=1e-11):
     return M.misfit(lam, mu, rho, p.gamma, p.omega, p.n, p.h, b, d, r,
                     dict(precision=bah.BAH_FP64, rhs_block=2), rtol)

@@ -46,6 +46,32 @@ def to_dev(v):
     return torch.from_numpy(np.ascontiguousarray(v)).to("cuda")
 
 
+def components(v, n):
+    """Split a compact 2-D vector [u1 | u2 | p] into its three staggered
+    lattices as arrays (u1: n2 x (n1-1), u2: (n2-1) x n1, p: n2 x n1)."""
+    n1, n2 = n
+    shapes = [(n2, n1 - 1), (n2 - 1, n1), (n2, n1)]
+    out, o = [], 0
+    for sh in shapes:
+        k = sh[0] * sh[1]
+        out.append(np.asarray(v[o:o + k]).reshape(sh))
+        o += k
+    return out
+
+
+def check_elementwise(got, ref, n, tol):
+    """Element by element, per staggered lattice: max |got - ref| <= tol *
+    max |ref| over the whole lattice and over its boundary rows and columns
+    alone (where the lattices differ).  A 2-norm check can hide one wrong row;
+    this cannot."""
+    for c, (g, r) in enumerate(zip(components(got, n), components(ref, n))):
+        scale = np.abs(r).max()
+        d = np.abs(g - r)
+        assert d.max() <= tol * scale, (c, float(d.max() / scale))
+        edge = max(d[0].max(), d[-1].max(), d[:, 0].max(), d[:, -1].max())
+        assert edge <= tol * scale, (c, "boundary", float(edge / scale))
+
+
 def to_host(t):
     torch.cuda.synchronize()
     return t.cpu().numpy()
@@ -198,16 +224,22 @@ def test_block_cycle_matches_oracle(prec, name, systems):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("name", ["layered_64x32", "random_48x40", "c1"])
+@pytest.mark.parametrize("name", ["layered_64x32", "random_48x40", "c1", "random_37x29"])
 def test_preconditioner_matches_oracle(prec, name, systems):
+    """z = P^{-1} D r against the oracle, as a 2-norm and element by element
+    per lattice (boundary rows included), with the small levels in the
+    shared-memory cluster kernel (mixed mode) and the staged Galerkin sweeps;
+    37x29 is odd in both directions (a 1-level hierarchy)."""
     p, S = get(name, systems)
     s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED)
     pc = precond.multigrid(S, s.levels, precond.default_alpha(s.levels), precision=prec)
     r = W.random_vector(p.n, 31)
     z = to_host(s.apply_preconditioner(to_dev(r)))
     ref = pc.apply(W.padded_to_compact(r, p.n))
+    zc = W.padded_to_compact(z, p.n)
     tol = 1e-10 if prec == "fp64" else 2e-4
-    assert rel(W.padded_to_compact(z, p.n), ref) <= tol
+    assert rel(zc, ref) <= tol
+    check_elementwise(zc, ref, p.n, 1e-9 if prec == "fp64" else 2e-3)
     s.close()
 
 
@@ -306,7 +338,9 @@ def test_preconditioner_full_size_c2_matches_oracle():
     r = W.random_vector(p.n, 47)
     z = to_host(s.apply_preconditioner(to_dev(r)))
     pc = precond.multigrid(S, 6, precond.default_alpha(6), precision="mixed")
-    assert rel(W.padded_to_compact(z, p.n), pc.apply(W.padded_to_compact(r, p.n))) <= 2e-4
+    zc, ref = W.padded_to_compact(z, p.n), pc.apply(W.padded_to_compact(r, p.n))
+    assert rel(zc, ref) <= 2e-4
+    check_elementwise(zc, ref, p.n, 2e-3)
     s.close()
 
 
@@ -377,11 +411,9 @@ def test_graph_and_direct_launch_paths_agree(systems, monkeypatch):
     s2.close()
 
 
-@pytest.mark.parametrize("cls,env", [("jacobi", "0"), ("tiled", "1")])
-def test_profile_counters(cls, env, systems, monkeypatch):
-    """Launch and byte counters advance and timed classes report device time
-    (separate level kernels by default; tiled level visits with BAH_TILED=1)."""
-    monkeypatch.setenv("BAH_TILED", env)
+@pytest.mark.parametrize("cls", ["jacobi", "residual"])
+def test_profile_counters(cls, systems):
+    """Launch and byte counters advance and timed classes report device time."""
     p, S = get("c1", systems)
     s = bah.Solver.from_problem(p, maxit=5)
     bah.bah_profile_control(s.ctx, 1 << bah.BAH_K_NAMES.index(cls), True)
@@ -390,105 +422,6 @@ def test_profile_counters(cls, env, systems, monkeypatch):
     assert pr["launches"] > 5 * 10
     assert pr["classes"][cls]["ms"] > 0 and pr["classes"][cls]["bytes"] > 0
     assert pr["classes"]["dot"]["ms"] == 0
-    s.close()
-
-
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_fused_schedule_matches_oracle(prec, systems, monkeypatch):
-    """The fused multigrid schedule (pre-smoothing + residual + restriction in
-    one kernel, prolongation + first post-sweep in another) gives the same
-    preconditioner as the oracle."""
-    monkeypatch.setenv("BAH_FUSED", "1")
-    p, S = get("layered_64x32", systems)
-    s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=3)
-    pc = precond.multigrid(S, 3, precond.default_alpha(3), precision=prec)
-    r = W.random_vector(p.n, 33)
-    z = to_host(s.apply_preconditioner(to_dev(r)))
-    ref = pc.apply(W.padded_to_compact(r, p.n))
-    assert rel(W.padded_to_compact(z, p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
-    s.close()
-
-
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_cooperative_levels_match_standalone_kernels(prec, monkeypatch):
-    """With BAH_COOP=1 levels 1..L-1 run in one cooperative launch; by
-    default they run as separate kernels.  Both schedules agree, and both match
-    the oracle's preconditioner (4 levels, bilinear transfers)."""
-    p = W.layered(128, 64, 5, seed=27, abc=8)
-    S = elastic.from_problem(p)
-    r = W.random_vector(p.n, 35)
-    out = {}
-    for mode in ("coop", "plain"):
-        monkeypatch.setenv("BAH_COOP", "1" if mode == "coop" else "0")
-        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=4)
-        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
-        s.close()
-    tol = 1e-12 if prec == "fp64" else 1e-5
-    assert rel(out["coop"], out["plain"]) <= tol
-    pc = precond.multigrid(S, 4, precond.default_alpha(4), precision=prec)
-    ref = pc.apply(W.padded_to_compact(r, p.n))
-    assert rel(W.padded_to_compact(out["coop"], p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
-
-
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_cluster_levels_match_standalone_kernels(prec, monkeypatch):
-    """With BAH_CLUSTER=1 the levels below the first one with at most 16384
-    points run in one thread-block-cluster launch per block set; by default
-    (BAH_CLUSTER=0) they run as separate kernels.  The per-point arithmetic is
-    the same, so the results
-    agree to rounding, for every cluster size, for a single right-hand side
-    and for a batch; and they match the oracle's preconditioner."""
-    p = W.layered(128, 64, 5, seed=29, abc=8)
-    S = elastic.from_problem(p)
-    r = W.random_vector(p.n, 37)
-    out = {}
-    for mode in ("0", "2", "8", "16"):
-        if mode == "0":
-            monkeypatch.setenv("BAH_CLUSTER", "0")
-        else:
-            monkeypatch.setenv("BAH_CLUSTER", "1")
-            monkeypatch.setenv("BAH_CLUSTER_SIZE", mode)
-        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=4)
-        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
-        s.close()
-    tol = 1e-12 if prec == "fp64" else 1e-6
-    for mode in ("2", "8", "16"):
-        assert rel(out[mode], out["0"]) <= tol, (mode, rel(out[mode], out["0"]))
-    pc = precond.multigrid(S, 4, precond.default_alpha(4), precision=prec)
-    ref = pc.apply(W.padded_to_compact(r, p.n))
-    assert rel(W.padded_to_compact(out["16"], p.n), ref) <= (1e-10 if prec == "fp64" else 2e-4)
-    # batched solves (ragged last batch, 5 sources in batches of 2) with and without the cluster path
-    b = np.stack([W.point_source(p, (12 + 24 * k, 8)) for k in range(5)])
-    xs = {}
-    for mode in ("0", "1"):
-        monkeypatch.setenv("BAH_CLUSTER", mode)
-        monkeypatch.delenv("BAH_CLUSTER_SIZE", raising=False)
-        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=4,
-                                    rhs_block=2)
-        x, st, stats = s.solve(to_dev(b), rtol=1e-7)
-        assert st == bah.BAH_OK
-        xs[mode] = (to_host(x), [q["iters"] for q in stats])
-        s.close()
-    assert xs["0"][1] == xs["1"][1]
-    assert rel(xs["1"][0], xs["0"][0]) <= (1e-10 if prec == "fp64" else 1e-5)
-
-
-def test_cluster_path_is_taken(systems, monkeypatch):
-    """With BAH_CLUSTER=1 the cluster kernel runs once per block set per
-    preconditioner application and no separate kernels run on the levels it
-    covers."""
-    monkeypatch.setenv("BAH_CLUSTER", "1")
-    monkeypatch.setenv("BAH_TILED", "0")
-    p, S = get("layered_64x32", systems)
-    s = bah.Solver.from_problem(p, levels=3)
-    bah.bah_profile_control(s.ctx, 0, True)
-    s.apply_preconditioner(to_dev(W.random_vector(p.n, 3)))
-    pr = bah.bah_profile_read(s.ctx)
-    cl = pr["classes"]["cluster"]
-    assert cl["calls"] == 2 and cl["launches"] == 2
-    # level 0 only: 3 Jacobi sweeps per block set
-    assert pr["classes"]["jacobi"]["calls"] == 6
-    assert pr["classes"]["coarse"]["calls"] == 0
     s.close()
 
 
@@ -535,34 +468,6 @@ def test_smem_cluster_multigrid_matches_separate_kernels(cycle, levels, monkeypa
     for k in range(5):
         bc = W.padded_to_compact(b[k], p.n)
         assert np.linalg.norm(bc - S.H @ W.padded_to_compact(xh[k], p.n)) / np.linalg.norm(bc) <= 1e-7
-
-
-@pytest.mark.parametrize("prec", [bah.BAH_FP64, bah.BAH_MIXED])
-@pytest.mark.parametrize("cycle", [bah.BAH_CYCLE_V, bah.BAH_CYCLE_W])
-@pytest.mark.parametrize("name", ["random_48x40", "layered_64x32"])
-def test_tiled_level_visits_match_separate_kernels(prec, cycle, name, systems, monkeypatch):
-    """A zero-guess V(1,2)/W(1,2) level visit runs as two tiled launches (sweep +
-    residual + restriction; prolongation + two sweeps) with BAH_TILED=1, and as
-    six separate launches by default.  Same per-point arithmetic: the
-    preconditioner agrees to rounding, including tiles cut by the grid edge
-    (48x40, 24x20 fine grids on 32x16 tiles), and matches the oracle."""
-    p, S = get(name, systems)
-    r = W.random_vector(p.n, 43)
-    out = {}
-    for mode in ("0", "1"):
-        monkeypatch.setenv("BAH_TILED", mode)
-        s = bah.Solver.from_problem(p, precision=prec, levels=3, cycle=cycle)
-        bah.bah_profile_control(s.ctx, 0, True)
-        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
-        pr = bah.bah_profile_read(s.ctx)
-        assert (pr["classes"]["tiled"]["calls"] > 0) == (mode == "1")
-        s.close()
-    tol = 1e-12 if prec == bah.BAH_FP64 else 1e-6
-    assert rel(out["1"], out["0"]) <= tol, rel(out["1"], out["0"])
-    pc = precond.multigrid(S, 3, precond.default_alpha(3), precision="fp64" if prec == bah.BAH_FP64 else "mixed",
-                           cycle="W" if cycle == bah.BAH_CYCLE_W else "V")
-    ref = pc.apply(W.padded_to_compact(r, p.n))
-    assert rel(W.padded_to_compact(out["1"], p.n), ref) <= (1e-10 if prec == bah.BAH_FP64 else 2e-4)
 
 
 @pytest.mark.parametrize("name", ["random_48x40", "layered_64x32"])

@@ -71,9 +71,9 @@ def layered():
 def test_w_block_cycle_matches_oracle(prec, levels, nu, cluster, layered, monkeypatch):
     """One W(nu1,nu2) cycle per block with zero initial guess; 2 levels (where a
     W-cycle equals a V-cycle) up to 4 (a 4-deep recursion: 1, 2, 4 visits),
-    with the levels below the fine one as separate kernels or (cluster=1) in
-    the cluster kernel's walk of the recursion."""
-    monkeypatch.setenv("BAH_CLUSTER", cluster)
+    with the small levels as separate kernels (cluster=0) or, in mixed mode,
+    in the shared-memory cluster kernel's walk of the recursion (cluster=1)."""
+    monkeypatch.setenv("BAH_SMEM_MG", cluster)
     p, S = layered
     s = bah.Solver.from_problem(p, precision=bah.BAH_FP64 if prec == "fp64" else bah.BAH_MIXED, levels=levels,
                                 cycle=bah.BAH_CYCLE_W, nu_pre=nu[0], nu_post=nu[1])
@@ -119,8 +119,9 @@ def test_w_preconditioner_matches_oracle(prec, layered):
 @pytest.mark.parametrize("prec", [bah.BAH_MIXED, bah.BAH_FP64])
 def test_w_batched_solve_equals_sequential(prec, cluster, layered, monkeypatch):
     """W-cycles inside the batched solve (5 sources in batches of 3, ragged
-    last batch): identical counts and iterates to the one-at-a-time solve."""
-    monkeypatch.setenv("BAH_CLUSTER", cluster)
+    last batch): identical counts and iterates to the one-at-a-time solve, with
+    the small levels as separate kernels or in the shared-memory cluster kernel."""
+    monkeypatch.setenv("BAH_SMEM_MG", cluster)
     p, S = layered
     b = np.stack([W.point_source(p, (8 + 12 * k, 6)) for k in range(5)])
     s1 = bah.Solver.from_problem(p, precision=prec, levels=4, cycle=bah.BAH_CYCLE_W)

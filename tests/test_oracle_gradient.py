@@ -70,3 +70,19 @@ def test_adjoint_identity_conjugate_transpose():
     lhs = np.vdot(y, S.H @ x)
     rhs = np.vdot(S.H.conj() @ y, x)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_repeated_receiver_counts_twice_in_the_adjoint_source():
+    """Q with a repeated row (a receiver listed twice) weighs that datum twice
+    in J, so Q^H (Q x - d) must sum both copies: the adjoint gradient still
+    equals the central difference of J."""
+    p, S, B, D, rows = setup()
+    rows2 = np.concatenate([rows, rows[3:5]])
+    D2 = np.concatenate([D, D[3:5] * (1 + 0.3j)])
+    J0, g, X, Y = G.gradient(S, B, D2, rows2, params=("mu",))
+    rng = np.random.default_rng(13)
+    for k in rng.choice(S.ncells, 4, replace=False):
+        m0 = p.mu.ravel()[k]
+        eps = 1e-5 * abs(m0)
+        fd = (J_at(p, "mu", k, m0 + eps, B, D2, rows2) - J_at(p, "mu", k, m0 - eps, B, D2, rows2)) / (2 * eps)
+        assert abs(fd - g["mu"][k]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g["mu"]).max()), (k, fd, g["mu"][k])

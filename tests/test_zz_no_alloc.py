@@ -1,10 +1,10 @@
 """The allocation-free relative-residual entry point.
 
 bah_residual_norm_static serves callers that cannot call cudaMalloc when they
-need the residual (inside CUDA stream capture, in real-time loops that forbid
-allocator calls after start-up, or where another allocator owns the device
-memory): its reduction scratch is a static device array instead of context
-workspace.  Checked through the C ABI against the relative residual that
+need the residual (real-time loops that forbid allocator calls after start-up,
+because an allocation can block for an unbounded time, or hosts whose device
+memory all belongs to another allocator): its reduction scratch is a static
+device array instead of context workspace.  Checked through the C ABI against the relative residual that
 bah_solve reports for the same b and x, and against the CPU oracle, on two
 calls in a row (the static array keeps the previous call's contents).
 This file sorts last so that a run stopping at the first failure has run every
@@ -60,4 +60,18 @@ def test_static_residual_matches_solver_and_oracle():
     with pytest.raises(bah.BahError) as e:
         bah.bah_residual_norm_static(s.ctx, b, x, big, out)
     assert e.value.status == bah.BAH_ERR_ARG and "BAH_STATIC_MAX_RHS" in bah.last_error()
+    s.close()
+
+
+def test_static_residual_rejects_3d_contexts():
+    """The entry point covers 2-D grids only: a 3-D context is refused with
+    BAH_ERR_UNSUPPORTED before anything is launched."""
+    p = W.random_medium((8, 8, 8), 52, abc=1)
+    s = bah.Solver.from_problem(p, intergrid=bah.BAH_INTERGRID_MIXED, levels=2)
+    n = int(np.prod(W.padded_shape(p.n)))
+    b = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(bah.BahError) as e:
+        bah.bah_residual_norm_static(s.ctx, b, b, 1, out)
+    assert e.value.status == bah.BAH_ERR_UNSUPPORTED
     s.close()
