@@ -266,15 +266,15 @@ int bah_level_stencil(const bah_ctx* ctx, int block, int level, double* out, int
 #define BAH_K_RESIDUAL  4   /* multigrid residual, all levels */
 #define BAH_K_RESTRICT  5   /* restriction (Eq. 4.1, 4.2, 4.4) */
 #define BAH_K_PROLONG   6   /* prolongation + correction */
-#define BAH_K_COARSE    7   /* coarsest-level FP64 inverse apply */
+#define BAH_K_COARSE    7   /* coarsest-level FP64 inverse applied in FP64 */
 #define BAH_K_DOT       8   /* Gram-Schmidt block dot products (2 kernels) */
 #define BAH_K_AXPY      9   /* Gram-Schmidt update w -= V h */
 #define BAH_K_NORM     10   /* 2-norms (2 kernels) */
 #define BAH_K_UPDATE   11   /* x += Z y */
 #define BAH_K_SMALL    12   /* Givens update, triangular solve, scaling, copies, conversions */
-#define BAH_K_COOP     13   /* cooperative launch running all levels below the fine grid */
+#define BAH_K_DOWN     13   /* fused level visit, down: zero-guess sweep + residual + restriction */
 #define BAH_K_CLUSTER  14   /* thread-block-cluster launch running the small levels of a cycle */
-#define BAH_K_TILED    15   /* tiled fused level visit: sweep + residual + restriction, prolongation + 2 sweeps */
+#define BAH_K_UP       15   /* fused level visit, up: prolongation + correction + post-sweeps */
 #define BAH_NKCLASS    16
 
 typedef struct {

@@ -257,7 +257,7 @@ def bah_solve(ctx, b, x, nrhs=1, rtol=1e-6, stream=None):
 
 
 BAH_K_NAMES = ("operator", "distrib", "urhs", "jacobi", "residual", "restrict", "prolong", "coarse", "dot",
-               "axpy", "norm", "update", "small", "coop", "cluster", "tiled")
+               "axpy", "norm", "update", "small", "down", "cluster", "up")
 
 
 class bah_profile(C.Structure):

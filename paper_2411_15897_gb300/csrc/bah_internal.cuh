@@ -186,8 +186,8 @@ struct SmArgs {
     const __nv_bfloat162* S[2][kMaxLevels];   // global stencils (levels below the coarsest)
     const float2* gb[2];      // level-l0 right-hand sides (right-hand side r at r * points)
     float2* gx[2];            // level-l0 iterates / results
-    const float2* inv[2];     // coarsest inverses, FP32 complex
-    unsigned off_inv, off_g;  // own inverse rows; gathered coarsest right-hand side
+    const double2* inv[2];    // coarsest FP64 inverses (global memory; the product is formed in FP64)
+    unsigned off_g;           // gathered coarsest right-hand side
     const int* active;
 };
 // fills the shared-memory layout of a (n1, n2, slot counts per level from l0);
@@ -238,6 +238,8 @@ template <class Vin>
 void launch_elastic_apply_df(const OpCoef& c, const Vin* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs);
 // y = H x for FP32 x in double-float arithmetic (no FP64 instructions), y as double-float
 void launch_elastic_apply_dfa(const OpCoefDF& c, const float2* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs);
+// the same, rounded once to FP64 on output (the FP64 Krylov basis)
+void launch_elastic_apply_dfa(const OpCoefDF& c, const float2* x, double2* y, cudaStream_t st, int nrhs, RhsStride rs);
 // FP64 arrays to double-float pairs
 void launch_to_df(const double* src, float2* dst, size_t n, cudaStream_t st);
 void launch_to_df_c(const double2* src, float4* dst, size_t n, cudaStream_t st);
@@ -253,11 +255,23 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 template <int MODE>
 void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                      typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride = 0);
+// fused level visits (k_mg_fused.cu): zero-guess sweep + residual +
+// restriction (smoothed iterate into s.blk[z].xout, R r into coarse_b), and
+// prolongation with correction + nu sweeps (x_out = nu sweeps on x_in + P e;
+// x_out must not alias x_in).  Return nonzero if the launch could not be made.
+template <int MODE>
+int launch_level_down(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                      const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                      typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride);
+template <int MODE>
+int launch_level_up(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
+                    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
+                    const typename Prec<MODE>::V* const* coarse_x, int nu, cudaStream_t st, size_t coarse_stride);
 template <int MODE>
 void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                         const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride = 0);
 template <int MODE>
-void launch_coarse_apply(int nb, int npts, const typename Prec<MODE>::V* const* inv, const typename Prec<MODE>::V* const* b,
+void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
                          typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs = 1, RhsStride rs = RhsStride());
 template <int MODE, class RIN = double2>
 void launch_distributor(int n1, int n2, double ihx, double ihz,

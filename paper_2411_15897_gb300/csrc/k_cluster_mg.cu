@@ -5,8 +5,9 @@
 // to 16 CTAs, one CTA per SM.  Each level's grid rows are split into equal
 // slabs, one per CTA; a CTA stores, for the points of its slab, the level's
 // Galerkin stencil (bfloat16 complex, slot-major), the iterate, a work
-// vector and the right-hand side, and on the coarsest level its rows of the
-// dense inverse (FP32 complex).  A stencil, restriction or prolongation tap
+// vector and the right-hand side.  The coarsest level is solved with the
+// dense FP64 inverse, read from global memory (it stays in L2) and applied in
+// FP64 arithmetic to the gathered FP32 right-hand side.  A stencil, restriction or prolongation tap
 // that falls into another CTA's slab is read from that CTA's shared memory
 // through the cluster's distributed shared memory (mapa + ld.shared::cluster).
 //
@@ -14,9 +15,10 @@
 // damped Jacobi, Jacobi, residual, restriction, the coarsest solve,
 // prolongation and correction -- with the same per-point arithmetic, and the
 // W-cycle's second coarse visits (Sec. 2.2), separated by the hardware
-// cluster barrier.  Global memory is touched only to load the stencils, the
-// inverse rows and the level-l0 right-hand side (and iterate, on a warm
-// start) at the start, and to store the level-l0 result at the end.
+// cluster barrier.  Global memory is touched only to load the stencils and
+// the level-l0 right-hand side (and iterate, on a warm start) at the start,
+// to read the rows of the coarsest inverse, and to store the level-l0 result
+// at the end.
 //
 // Deadlock freedom: the hardware co-schedules all CTAs of a cluster, every
 // thread of every CTA executes the same sequence of barriers (the control
@@ -101,12 +103,6 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
         for (int s = 0; s < nsl; ++s)
             for (int t = tid; t < own; t += nth)
                 cp_async4(sbase + L.off_c + (uint32_t)(s * cap + t) * 4u, S + (size_t)s * np + g0 + t);
-    }
-    {
-        const SmLevel& L = a.lv[kc];
-        const int npc = L.n1 * L.n2, own = nown(L), g0 = p0(L);
-        const V* src = a.inv[z] + (size_t)g0 * npc;
-        for (int e = tid; e < own * npc; e += nth) cp_async8(sbase + a.off_inv + (uint32_t)e * 8u, src + e);
     }
     {
         const SmLevel& L = a.lv[0];
@@ -266,29 +262,39 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
             x[lt] = acc;
         }
     };
-    auto coarse = [&]() {                                   // x_c = A_c^{-1} b_c on own rows
+    auto coarse = [&]() {                                   // x_c = A_c^{-1} b_c on own rows, in FP64
         const SmLevel& L = a.lv[kc];
-        const int npc = L.n1 * L.n2, own = nown(L);
+        const int npc = L.n1 * L.n2, own = nown(L), g0 = p0(L);
         V* gath = vec(a.off_g);
         for (int g = tid; g < npc; g += nth) gath[g] = ld_cluster_at(row_addr(L, L.off_b, g / L.n1) + (uint32_t)(g % L.n1) * 8u);
         __syncthreads();
-        const V* inv = vec(a.off_inv);
         V* x = vec(L.off_x);
         const int lane = tid & 31;
         for (int row = tid >> 5; row < own; row += nth >> 5) {
-            const V* arow = inv + (size_t)row * npc;
-            float re = 0.f, im = 0.f;
-            for (int c = lane; c < npc; c += 32) {
-                const V m = arow[c];
-                const V v = gath[c];
-                re += m.x * v.x - m.y * v.y;
-                im += m.x * v.y + m.y * v.x;
+            // the FP64 inverse row from global memory (L2-resident), eight loads in flight per lane
+            const double2* arow = a.inv[z] + (size_t)(g0 + row) * npc;
+            double re = 0.0, im = 0.0;
+            auto mac = [&](const double2& m, const V& v) {
+                const double vx = (double)v.x, vy = (double)v.y;
+                re = fma(m.x, vx, re);
+                re = fma(-m.y, vy, re);
+                im = fma(m.x, vy, im);
+                im = fma(m.y, vx, im);
+            };
+            int c = lane;
+            for (; c + 32 * 7 < npc; c += 32 * 8) {
+                double2 m[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) m[u] = __ldg(arow + c + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) mac(m[u], gath[c + 32 * u]);
             }
+            for (; c < npc; c += 32) mac(__ldg(arow + c), gath[c]);
             for (int o = 16; o > 0; o >>= 1) {
                 re += __shfl_xor_sync(0xffffffffu, re, o);
                 im += __shfl_xor_sync(0xffffffffu, im, o);
             }
-            if (lane == 0) x[row] = cmk<V>(re, im);
+            if (lane == 0) x[row] = cmk<V>((float)re, (float)im);
         }
     };
     auto zero_vec = [&](int k, unsigned off) {
@@ -414,7 +420,6 @@ size_t smmg_layout(SmArgs& a, const int* n1, const int* n2, const int* nslot_max
     }
     const SmLevel& Lc = a.lv[nlev - 1];
     const size_t npc = (size_t)Lc.n1 * Lc.n2;
-    a.off_inv = take((size_t)Lc.rp * Lc.n1 * npc * 8);
     a.off_g = take(npc * 8);
     return off;
 }

@@ -43,7 +43,29 @@ __device__ __forceinline__ bool inactive(const KS& ks, int r) { return ks.active
 // ||w'|| < ||w|| / sqrt(2).  The pass-2 kernels read the per-right-hand-side
 // flag and return at once when it is clear.
 // ---------------------------------------------------------------------------
-// rows 0..k-1: conj(V_y) w; row k: |w|^2 (imaginary part 0)
+// The FP64 pipe (2 FMA/clk/SM on GB300, 1/64 of FP32) bounds these kernels,
+// so every complex multiply-add is written as four explicit fused
+// multiply-adds into the accumulator (a plain "acc += a*b + c*d" compiles to a
+// multiply, an FMA and an add: six FP64 instructions per complex MAC).
+__device__ __forceinline__ void cmac_conj(double2& acc, const double2& a, const double2& b) {   // acc += conj(a) b
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cmsub(double2& acc, const double2& c, const double2& v) {       // acc -= c v
+    acc.x = fma(-c.x, v.x, acc.x);
+    acc.x = fma(c.y, v.y, acc.x);
+    acc.y = fma(-c.x, v.y, acc.y);
+    acc.y = fma(-c.y, v.x, acc.y);
+}
+
+// Partial sums of rows y0 .. y0+kG-1 (blockIdx.y = row group): row y < k is
+// conj(V_y) w, row k is |w|^2 (imaginary part 0).  Each thread loads w once per
+// element for the kG rows of its group.  The kG complex partials of the CTA are
+// reduced through shared memory: thread t sums quantity t / 16 over a slice of
+// 16 threads, then 16-lane shuffles finish it (few FP64 adds per thread).
+constexpr int kDotG = 8;
 __global__ void __launch_bounds__(256) k_dot_norm_partial(const double2* __restrict__ V, int k,
                                                           const double2* __restrict__ w, size_t n,
                                                           double2* __restrict__ partial, const int* flag, KS ks) {
@@ -53,37 +75,45 @@ __global__ void __launch_bounds__(256) k_dot_norm_partial(const double2* __restr
     V += r * ks.sv;
     w += r * ks.sw;
     partial += r * ks.sp;
-    const int y = blockIdx.y;
-    double2 acc = make_double2(0.0, 0.0);
+    const int y0 = blockIdx.y * kDotG;
+    const int ny = min(kDotG, k + 1 - y0);          // rows of this group (the norm row is row k)
+    double2 acc[kDotG];
+#pragma unroll
+    for (int q = 0; q < kDotG; ++q) acc[q] = make_double2(0.0, 0.0);
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    // accumulated in element order; the loads of kU elements go out together
-    constexpr int kU = 4;
-    auto mac = [&](const double2& a, const double2& b) {
-        acc.x += a.x * b.x + a.y * b.y;
-        acc.y += a.x * b.y - a.y * b.x;
-    };
-    if (y < k) {
-        const double2* v = V + (size_t)y * n;
-        for (; e + (kU - 1) * stride < n; e += kU * stride) {
-            double2 a[kU], b[kU];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+        const double2 b = __ldg(w + e);
+        double2 a[kDotG];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                a[u] = __ldg(v + e + u * stride);
-                b[u] = __ldg(w + e + u * stride);
+        for (int q = 0; q < kDotG; ++q)
+            if (q < ny && y0 + q < k) a[q] = __ldg(V + (size_t)(y0 + q) * n + e);
+#pragma unroll
+        for (int q = 0; q < kDotG; ++q) {
+            if (q >= ny) break;
+            if (y0 + q < k) {
+                cmac_conj(acc[q], a[q], b);
+            } else {
+                acc[q].x = fma(b.x, b.x, acc[q].x);
+                acc[q].x = fma(b.y, b.y, acc[q].x);
             }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) mac(a[u], b[u]);
-        }
-        for (; e < n; e += stride) mac(__ldg(v + e), __ldg(w + e));
-    } else {
-        for (; e < n; e += stride) {
-            const double2 b = __ldg(w + e);
-            acc.x += b.x * b.x + b.y * b.y;
         }
     }
-    acc = block_sum2(acc);
-    if (threadIdx.x == 0) partial[(size_t)y * gridDim.x + blockIdx.x] = acc;
+    __shared__ double sh[2 * kDotG][256];
+#pragma unroll
+    for (int q = 0; q < kDotG; ++q) {
+        sh[2 * q][threadIdx.x] = acc[q].x;
+        sh[2 * q + 1][threadIdx.x] = acc[q].y;
+    }
+    __syncthreads();
+    const int qv = threadIdx.x >> 4, sl = threadIdx.x & 15;     // quantity, slice
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) s += sh[qv][sl * 16 + u];
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (sl == 0 && (qv >> 1) < ny) {
+        double* dst = reinterpret_cast<double*>(partial + (size_t)(y0 + (qv >> 1)) * gridDim.x + blockIdx.x);
+        dst[qv & 1] = s;
+    }
 }
 __global__ void __launch_bounds__(256) k_reduce_rows(const double2* __restrict__ partial, int np, double2* out,
                                                      const int* flag, KS ks) {
@@ -107,7 +137,8 @@ __global__ void __launch_bounds__(256) k_reduce_rows(const double2* __restrict__
 }
 void launch_dot_norm(const double2* V, int k, const double2* w, size_t n, double2* partial, double2* out,
                      const int* flag, int nrhs, const KS& ks, cudaStream_t st) {
-    launch_pdl(k_dot_norm_partial, dim3(dim3(RED_CTAS, k + 1, nrhs)), dim3(256), 0, st, V, k, w, n, partial, flag, ks);
+    const int groups = (k + 1 + kDotG - 1) / kDotG;
+    launch_pdl(k_dot_norm_partial, dim3(dim3(RED_CTAS, groups, nrhs)), dim3(256), 0, st, V, k, w, n, partial, flag, ks);
     launch_pdl(k_reduce_rows, dim3(dim3(1, k + 1, nrhs)), dim3(256), 0, st, partial, RED_CTAS, out, flag, ks);
 }
 
@@ -129,21 +160,18 @@ __global__ void __launch_bounds__(512) k_axpy_norm(const double2* __restrict__ V
     constexpr int kU = 8;   // rows whose loads go out together
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double2 acc = w[e];
-        auto sub = [&](const double2& v, const double2& cc) {
-            acc.x -= cc.x * v.x - cc.y * v.y;
-            acc.y -= cc.x * v.y + cc.y * v.x;
-        };
         int i = 0;
         for (; i + kU <= k; i += kU) {
             double2 v[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) v[u] = __ldg(V + (size_t)(i + u) * n + e);
 #pragma unroll
-            for (int u = 0; u < kU; ++u) sub(v[u], c[i + u]);
+            for (int u = 0; u < kU; ++u) cmsub(acc, c[i + u], v[u]);
         }
-        for (; i < k; ++i) sub(__ldg(V + (size_t)i * n + e), c[i]);
+        for (; i < k; ++i) cmsub(acc, c[i], __ldg(V + (size_t)i * n + e));
         w[e] = acc;
-        nn += acc.x * acc.x + acc.y * acc.y;
+        nn = fma(acc.x, acc.x, nn);
+        nn = fma(acc.y, acc.y, nn);
     }
     double2 rs = block_sum2(make_double2(nn, 0.0));
     if (threadIdx.x == 0) npart[blockIdx.x] = rs.x;

@@ -315,20 +315,18 @@ void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>
 }
 
 // ---------------------------------------------------------------------------
-// coarsest level: x = A_c^{-1} b with the stored inverse (one warp per row).
-// The inverse is computed in FP64 at setup and stored in the cycle's vector
-// type: FP64 in the FP64 mode, rounded once to FP32 in the mixed mode, where
-// the product is accumulated in FP32 like the rest of the cycle.
+// coarsest level: x = A_c^{-1} b with the stored FP64 inverse (one warp per
+// row).  The product is formed in FP64 in both modes -- the coarsest-grid
+// solve is one of the steps kept in FP64 -- from the right-hand side in the
+// cycle's precision; the result is rounded once to the cycle's precision.
+// Each lane issues its eight row loads before the first multiply-add.
 // ---------------------------------------------------------------------------
-constexpr int kCoarseSmem = 3072;   // points staged in shared memory (48 KB of FP64 complex)
+constexpr int kCoarseSmem = 3072;   // points staged in shared memory
 
-template <int MODE>
-__global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const typename MGT<MODE>::V> inv,
-                                                      PtrSet<const typename MGT<MODE>::V> b,
-                                                      PtrSet<typename MGT<MODE>::V> x, const int* active) {
+template <class V>
+__global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const double2> inv, PtrSet<const V> b,
+                                                      PtrSet<V> x, const int* active) {
     pdl_prologue();
-    using V = typename MGT<MODE>::V;
-    using R = typename MGT<MODE>::R;
     const int z = blockIdx.y;
     const int rr = blockIdx.z;
     if (active && !active[rr]) return;
@@ -343,28 +341,39 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const typ
         __syncthreads();
     }
     if (warp >= npts) return;
-    const V* row = inv.p[z] + (size_t)warp * npts;
-    R re = 0, im = 0;
-    for (int c = lane; c < npts; c += 32) {
-        const V a = row[c];
-        const V v = staged ? bsh[c] : bb[c];
-        re += a.x * v.x - a.y * v.y;
-        im += a.x * v.y + a.y * v.x;
+    const double2* row = inv.p[z] + (size_t)warp * npts;
+    double re = 0.0, im = 0.0;
+    auto mac = [&](const double2& a, const V& v) {
+        const double vx = (double)v.x, vy = (double)v.y;
+        re = fma(a.x, vx, re);
+        re = fma(-a.y, vy, re);
+        im = fma(a.x, vy, im);
+        im = fma(a.y, vx, im);
+    };
+    constexpr int kU = 8;
+    int c = lane;
+    for (; c + 32 * (kU - 1) < npts; c += 32 * kU) {
+        double2 a[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) a[u] = __ldg(row + c + 32 * u);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) mac(a[u], staged ? bsh[c + 32 * u] : bb[c + 32 * u]);
     }
+    for (; c < npts; c += 32) mac(__ldg(row + c), staged ? bsh[c] : bb[c]);
     for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) x.p[z][rr * x.s + warp] = cmk<V>(re, im);
+    if (lane == 0) x.p[z][rr * x.s + warp] = cmk<V>((typename VecTraits<V>::R)re, (typename VecTraits<V>::R)im);
 }
 
 template <int MODE>
-void launch_coarse_apply(int nb, int npts, const typename Prec<MODE>::V* const* inv,
-                         const typename Prec<MODE>::V* const* b, typename Prec<MODE>::V* const* x, cudaStream_t st,
-                         int nrhs, RhsStride rs) {
-    PtrSet<const typename Prec<MODE>::V> pi;
-    PtrSet<const typename Prec<MODE>::V> pb;
-    PtrSet<typename Prec<MODE>::V> px;
+void launch_coarse_apply(int nb, int npts, const double2* const* inv, const typename Prec<MODE>::V* const* b,
+                         typename Prec<MODE>::V* const* x, cudaStream_t st, int nrhs, RhsStride rs) {
+    using V = typename Prec<MODE>::V;
+    PtrSet<const double2> pi;
+    PtrSet<const V> pb;
+    PtrSet<V> px;
     for (int z = 0; z < 3; ++z) {
         pi.p[z] = z < nb ? inv[z] : nullptr;
         pb.p[z] = z < nb ? b[z] : nullptr;
@@ -373,8 +382,8 @@ void launch_coarse_apply(int nb, int npts, const typename Prec<MODE>::V* const* 
     pb.s = rs.s0;
     px.s = rs.s1;
     dim3 g((npts * 32 + 255) / 256, nb, nrhs);
-    const size_t smem = npts <= kCoarseSmem ? (size_t)npts * sizeof(typename Prec<MODE>::V) : 0;
-    launch_pdl(k_coarse_apply<MODE>, dim3(g), dim3(256), smem, st, npts, pi, pb, px, rs.active);
+    const size_t smem = npts <= kCoarseSmem ? (size_t)npts * sizeof(V) : 0;
+    launch_pdl(k_coarse_apply<V>, dim3(g), dim3(256), smem, st, npts, pi, pb, px, rs.active);
 }
 
 #define INST(MODE)                                                                                                 \
@@ -386,7 +395,7 @@ void launch_coarse_apply(int nb, int npts, const typename Prec<MODE>::V* const* 
                                         cudaStream_t, size_t);                                                     \
     template void launch_prolong_add<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                           \
                                            const Prec<MODE>::V* const*, cudaStream_t, size_t);                     \
-    template void launch_coarse_apply<MODE>(int, int, const Prec<MODE>::V* const*, const Prec<MODE>::V* const*,   \
+    template void launch_coarse_apply<MODE>(int, int, const double2* const*, const Prec<MODE>::V* const*,   \
                                             Prec<MODE>::V* const*, cudaStream_t, int, RhsStride);
 INST(BAH_FP64)
 INST(BAH_MIXED)

@@ -73,8 +73,16 @@ __global__ void __launch_bounds__(256) k_elastic_apply(OpCoef c, const Vin* __re
 // the FP64 kernel to about 2^-47 relative without FP64 instructions.  Same
 // stencil as k_elastic_apply (Eq. 2.6), y = H x only.
 // ---------------------------------------------------------------------------
+// the double-float result (hi, lo per real) as a double-float pair, or rounded
+// once to FP64 (hi + lo is exact in FP64: both parts are FP32 values of one
+// 48-bit significand)
+__device__ __forceinline__ void st_dfa(float4* y, size_t i, const float4& v) { y[i] = v; }
+__device__ __forceinline__ void st_dfa(double2* y, size_t i, const float4& v) {
+    y[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+template <class Vout>
 __global__ void __launch_bounds__(256) k_elastic_apply_dfa(OpCoefDF c, const float2* __restrict__ x,
-                                                           float4* __restrict__ y, RhsStride rs) {
+                                                           Vout* __restrict__ y, RhsStride rs) {
     pdl_prologue();
     const int n1 = c.n1, n2 = c.n2, np = n1 * n2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,13 +153,17 @@ __global__ void __launch_bounds__(256) k_elastic_apply_dfa(OpCoefDF c, const flo
     pi.add(df_mul(ihx, df_diff_f(u1c.y, u1e.y)));
     pi.add(df_mul(ihz, df_diff_f(u2c.y, u2n.y)));
     pi.add(df_neg(df_mul_f(ci, p.y)));
-    y[t] = y1;
-    y[np + t] = y2;
-    y[2 * np + t] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+    st_dfa(y, t, y1);
+    st_dfa(y, np + t, y2);
+    st_dfa(y, 2 * np + t, make_float4(pr.hi, pr.lo, pi.hi, pi.lo));
 }
 void launch_elastic_apply_dfa(const OpCoefDF& c, const float2* x, float4* y, cudaStream_t st, int nrhs, RhsStride rs) {
     const int np = c.n1 * c.n2;
-    launch_pdl(k_elastic_apply_dfa, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, c, x, y, rs);
+    launch_pdl(k_elastic_apply_dfa<float4>, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, c, x, y, rs);
+}
+void launch_elastic_apply_dfa(const OpCoefDF& c, const float2* x, double2* y, cudaStream_t st, int nrhs, RhsStride rs) {
+    const int np = c.n1 * c.n2;
+    launch_pdl(k_elastic_apply_dfa<double2>, dim3(dim3((np + 255) / 256, nrhs)), dim3(256), 0, st, c, x, y, rs);
 }
 __global__ void k_to_df(const double* __restrict__ s, float2* __restrict__ d, size_t n) {
     const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;

@@ -60,7 +60,6 @@ struct Ctx {
     std::vector<std::array<StencilF64, 3>> s64;   // FP64 stencils per level (level 0: 3x3 fine operator)
     std::vector<std::array<void*, 3>> sst;        // storage-precision stencils, levels >= 1
     double2* inv[3] = {nullptr, nullptr, nullptr};
-    void* invs[3] = {nullptr, nullptr, nullptr};  // inverse in the multigrid's storage type (FP32 copy when mixed)
     std::vector<std::array<void*, 3>> vX, vB, vT; // multigrid vectors per level and block
     // Krylov workspace
     int m = 20;
@@ -104,6 +103,7 @@ struct Ctx {
     std::vector<cudaEvent_t> itev;
     bool use_graphs = true;
     bool staged = true;                  // shared-memory staging of Galerkin-level sweeps (BAH_STAGED=0: off)
+    bool fuse = true;                    // fused level visits above the cluster levels (BAH_FUSED_LEVELS=0: off)
     int sm_l0 = 0;                       // first level of the shared-memory cluster multigrid (0: off)
     int sm_cs = 0, sm_rm = 2;            // its CTAs per cluster and stencil radius bound
     size_t sm_bytes = 0;                 // its dynamic shared memory per CTA
@@ -118,7 +118,6 @@ struct Ctx {
     std::vector<std::array<void*, 4>> s3s;         // the same in the cycle's vector type (levels below the coarsest)
     std::vector<std::array<void*, 4>> v3B, v3X, v3T;
     double2* inv3[4] = {nullptr, nullptr, nullptr, nullptr};
-    void* inv3s[4] = {nullptr, nullptr, nullptr, nullptr};
 
     static void clear_graph(IterGraph& G) {
         if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -330,12 +329,12 @@ struct MG {
                 }
                 a.gb[z] = (const float2*)c.vB[l0][b];
                 a.gx[z] = (float2*)c.vX[l0][b];
-                a.inv[z] = (const float2*)c.invs[b];
+                a.inv[z] = c.inv[b];
             }
             double bytes = 0;
             for (int k = 0; k < nlev - 1; ++k) bytes += coef_bytes(c, l0 + k, b0, nb) * bt.nr;
             const double npc = (double)c.ln1[c.L - 1] * c.ln2[c.L - 1];
-            bytes += nb * bt.nr * (npc * npc * 8.0 + (double)c.ln1[l0] * c.ln2[l0] * 8.0 * (warm ? 3 : 2));
+            bytes += nb * bt.nr * (npc * npc * 16.0 + (double)c.ln1[l0] * c.ln2[l0] * 8.0 * (warm ? 3 : 2));
             Prof pr(c, BAH_K_CLUSTER, st, bytes);
             launch_cluster_mg(a, c.sm_rm, bt.nr, c.sm_cs, c.sm_bytes, st);
         }
@@ -353,13 +352,13 @@ struct MG {
         const double vs = sizeof(V), ccs = sizeof(CC);
         const double nr = bt.nr;
         if (l == c.L - 1) {
-            const V* inv[3];
+            const double2* inv[3];
             const V* bb[3];
             V* xx[3];
-            for (int z = 0; z < nb; ++z) { inv[z] = (const V*)c.invs[b0 + z]; bb[z] = (const V*)c.vB[l][b0 + z]; xx[z] = out[z]; }
+            for (int z = 0; z < nb; ++z) { inv[z] = c.inv[b0 + z]; bb[z] = (const V*)c.vB[l][b0 + z]; xx[z] = out[z]; }
             RhsStride rs;
             rs.s0 = npl; rs.s1 = ostride; rs.active = bt.active;
-            Prof pr(c, BAH_K_COARSE, st, nb * (double)npl * npl * vs + nr * nb * 2.0 * npl * vs);
+            Prof pr(c, BAH_K_COARSE, st, nb * (double)npl * npl * 16.0 + nr * nb * 2.0 * npl * vs);
             launch_coarse_apply<MODE>(nb, (int)npl, inv, bb, xx, st, bt.nr, rs);
             return;
         }
@@ -381,6 +380,29 @@ struct MG {
         V* cx[3];
         for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
         const bool wcyc = c.o.cycle == BAH_CYCLE_W;
+        if (c.fuse && !x0 && c.o.nu_pre == 1 && c.o.nu_post >= 1 && c.o.nu_post <= 4) {
+            // two launches for the visit: the zero-guess sweep, the residual and
+            // the restriction (smoothed iterate into the spare buffer), then the
+            // prolongation with correction and the post-sweeps into out
+            {
+                Prof pr(c, BAH_K_DOWN, st, nr * nb * npl * vs * 2.25 + cb_);
+                launch_level_down<MODE>(set(c, l, b0, nb, nullptr, 0, oth, oth_s, bt), pf5, w, cb, c.o.intergrid, st,
+                                        nplc);
+            }
+            if (c.sm_l0 == l + 1) {
+                smem_levels(c, b0, nb, bt, st);
+                if (wcyc && l + 1 < c.L - 1) smem_levels(c, b0, nb, bt, st, true);
+            } else {
+                cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
+                if (wcyc && l + 1 < c.L - 1) cycle(c, l + 1, b0, nb, cx, nplc, bt, st, true);
+            }
+            {
+                Prof pr(c, BAH_K_UP, st, nr * nb * npl * vs * 3.25 + cb_);
+                launch_level_up<MODE>(set(c, l, b0, nb, oth, oth_s, out, ostride, bt), pf5, w, cx, c.o.nu_post, st,
+                                      nplc);
+            }
+            return;
+        }
         {
             // With a zero initial guess the caller's buffer holds nothing yet: if the
             // sweeps below swap the two buffers an odd number of times, start in the
@@ -498,8 +520,8 @@ struct MG3 {
         const size_t np = pts(c, l);
         if (l == c.L - 1) {
             const double vb = sizeof(V);
-            Prof pr(c, BAH_K_COARSE, st, (double)np * np * vb + 2.0 * np * vb);
-            const V* inv[1] = {(const V*)c.inv3s[q]};
+            Prof pr(c, BAH_K_COARSE, st, (double)np * np * 16.0 + 2.0 * np * vb);
+            const double2* inv[1] = {c.inv3[q]};
             const V* bb[1] = {b};
             V* xx[1] = {x};
             launch_coarse_apply<MODE>(1, (int)np, inv, bb, xx, st);
@@ -612,7 +634,8 @@ static void op_apply_z(Ctx& c, const void* z, size_t zstride, void* y, size_t ys
         else if (c.mode == BAH_MIXED) launch_elastic_apply_df<float2>(c.op, (const float2*)z, (float4*)y, st, bt.nr, rs);
         else launch_elastic_apply_df<double2>(c.op, (const double2*)z, (float4*)y, st, bt.nr, rs);
     } else {
-        if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
+        if (c.mode == BAH_MIXED && c.opdf_ok) launch_elastic_apply_dfa(c.opdf, (const float2*)z, (double2*)y, st, bt.nr, rs);
+        else if (c.mode == BAH_MIXED) launch_elastic_apply<float2>(c.op, (const float2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
         else launch_elastic_apply<double2>(c.op, (const double2*)z, (double2*)y, nullptr, 0, st, bt.nr, rs);
     }
 }
@@ -676,10 +699,10 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
                        c.wz, c.d1, c.d2, c.cinv, c.dg[0], c.dg[1], c.dg[2], c.dAp, st);
     BAH_CUDA_TRY(cudaGetLastError());
     c.op = OpCoef{c.n1, c.n2, c.cx, c.cz, c.nx, c.nz, c.d1, c.d2, c.cinv, 1.0 / c.h1, 1.0 / c.h2};
-    // double-float copies of the operator coefficients for w = H z in mixed mode
-    // with the double-float Krylov basis (BAH_OP_F64=1 keeps the FP64 kernel)
+    // double-float copies of the operator coefficients for w = H z on the FP32
+    // flexible basis in mixed mode (BAH_OP_F64=1 keeps the FP64 kernel)
     {
-        bool on = c.mode == BAH_MIXED && c.kdf;
+        bool on = c.mode == BAH_MIXED;
         if (const char* e = getenv("BAH_OP_F64")) on = on && e[0] != '1';
         if (on) {
             const size_t np = c.np;
@@ -772,13 +795,6 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
         for (int b = 0; b < 3; ++b) {
             TRY(c.alloc_t(&c.inv[b], (size_t)nc * nc));
             TRY(coarse_invert(b, c.s64[c.L - 1][b], c.inv[b], (double2*)work, flag, st));
-            if (c.mode == BAH_MIXED) {
-                // the FP64 inverse rounded once to FP32 for the mixed cycle's coarse solve
-                TRY(c.alloc(&c.invs[b], (size_t)nc * nc * sizeof(float2)));
-                launch_convert<double2, float2>(c.inv[b], (float2*)c.invs[b], (size_t)nc * nc, st);
-            } else {
-                c.invs[b] = c.inv[b];
-            }
         }
     }
     // multigrid vectors
@@ -832,6 +848,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     }
     TRY(alloc_krylov(c, st));
     if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
+    if (const char* e = getenv("BAH_FUSED_LEVELS")) c.fuse = (e[0] != '0');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
     return BAH_OK;
@@ -901,12 +918,6 @@ static int build3(Ctx& c, const bah_medium* med, cudaStream_t st) {
         for (int q = 0; q < 4; ++q) {
             TRY(c.alloc_t(&c.inv3[q], nc * nc));
             TRY(coarse_invert3(q, c.d3[c.L - 1].data(), c.s3[c.L - 1][q], c.inv3[q], (double2*)work, err + 1, st));
-            if (c.mode == BAH_MIXED) {
-                TRY(c.alloc(&c.inv3s[q], nc * nc * sizeof(float2)));
-                launch_convert<double2, float2>(c.inv3[q], (float2*)c.inv3s[q], nc * nc, st);
-            } else {
-                c.inv3s[q] = c.inv3[q];
-            }
         }
     }
     // multigrid vectors

