@@ -324,8 +324,10 @@ def run_bah(args):
         rhs_block = opts["rhs_block"] = tuned.rhs_block
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
+    t_setup = time.perf_counter()
     solver = bah.Solver.from_problem(prob, **opts)
     torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
     free1, _ = torch.cuda.mem_get_info()
     context_bytes = int(free0 - free1)
     levels = solver.levels
@@ -553,7 +555,7 @@ def run_bah(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "strong" if nsrc_all > 1 else "weak", "vs_baseline": None,
+        "ms_per_step": statistics.mean(step_ms), "setup_s": setup_s, "higher_is_better": True, "scaling": "strong" if nsrc_all > 1 else "weak", "vs_baseline": None,
         "dtype": (("mixed: f32 stencils, f32 multigrid, " if prob.dim == 3 else "mixed: bf16 coefficients, f32 multigrid, ")
                   + "f64 coarsest solve (f64 inverse applied in f64), "
                   + ("double-f32 (48-bit) Krylov basis and Gram-Schmidt" if args.krylov == "df"

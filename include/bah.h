@@ -110,6 +110,17 @@ typedef struct {
     int    rhs_block;        /* right-hand sides solved together by bah_solve (1..256); the
                                 context's workspace grows in proportion */
     int    krylov_arith;     /* BAH_KRYLOV_FP64 or BAH_KRYLOV_DF */
+    /* acoustic block solves.  block_rtol = 0: each block is approximately
+     * inverted by one multigrid cycle (Sec. 2.2, 4.4).  block_rtol > 0: each
+     * block is solved to ||s - M e|| <= block_rtol ||s|| by an inner FGMRES in
+     * FP64, preconditioned by that block's multigrid cycle -- the exact-block
+     * preconditioner of Sec. 4.1 (Table 2) and of Theorem 1 (Sec. 3) as
+     * block_rtol -> 0, at any grid size.  The blocks solved are shifted by
+     * block_alpha (Eq. 2.8; 0 = the unshifted blocks of Eq. 3.5), while the
+     * multigrid cycle keeps shift_alpha.  2-D, rhs_block = 1 only. */
+    double block_rtol;
+    int    block_maxit;      /* inner iterations per block solve (block_rtol > 0) */
+    double block_alpha;
 } bah_opts;
 
 typedef struct {
@@ -124,7 +135,8 @@ typedef struct {
  * coarsest cells, V(1,2), Jacobi weights 0.8, 0.8, 0.3 (Sec. 4.4.1), shift by
  * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels as in Sec. 4.4.3,
  * Table 4; 1.0 for deeper hierarchies, found by the same kind of search),
- * bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1, BAH_KRYLOV_FP64. */
+ * bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1, BAH_KRYLOV_FP64,
+ * one multigrid cycle per block (block_rtol 0; block_maxit 500, block_alpha 0). */
 void bah_default_opts(bah_opts* opts);
 
 /* Build a solver for one grid, medium and frequency.  Copies the host medium
@@ -133,6 +145,7 @@ void bah_default_opts(bah_opts* opts);
  * Galerkin hierarchies R A P (Eq. 4.3) and the FP64 inverse of every coarsest
  * block, and allocates all solve workspace.  Synchronous.  *out receives the
  * context; on failure *out is NULL and nothing is leaked.
+ * block_rtol > 0 needs a 2-D grid and rhs_block = 1 (else BAH_ERR_UNSUPPORTED).
  * 3-D grids (dim 3) follow the paper's 3-D multigrid (Sec. 4.5): they need
  * intergrid = BAH_INTERGRID_MIXED (Eq. 4.4; with it every Galerkin level is a
  * 27-point stencil), krylov_arith = BAH_KRYLOV_FP64 and at least 2 levels; the
@@ -166,6 +179,8 @@ typedef struct {
     int       cluster_level;
     int       cluster_ctas;
     long long cluster_smem_bytes;
+    long long block_iters;    /* inner FGMRES iterations of all block solves so far (block_rtol > 0) */
+    int       block_failures; /* block solves that stopped at block_maxit above block_rtol */
 } bah_info;
 int bah_get_info(const bah_ctx* ctx, bah_info* out);
 
@@ -236,6 +251,19 @@ int bah_gradient(bah_ctx* ctx, const void* x_fwd, const void* y_adj, int nrhs, d
  * Uses the context's Krylov workspace (no solve may run on the context at the
  * same time).  Synchronous on the given stream. */
 int bah_spectral_radius(bah_ctx* ctx, const void* x0, int iters, double* history, double* rho, void* stream);
+
+/* Spectral radius of Z = Xi A_s^{-1} B^T H_p,s^{-1} (Theorem 1, Sec. 3), the
+ * operator whose spectrum, with {0}, is that of T when the blocks are solved
+ * exactly; Xi = B A - A_p B is the commutator of Eq. 3.2 (unshifted blocks)
+ * and A_s, H_p,s the blocks shifted by the context's block_alpha (Eq. 2.8),
+ * solved by the context's exact block solves.  Power method as in the paper
+ * (a matrix-free product with Z): x_{k+1} = Z x_k / ||Z x_k|| from the device
+ * vector x0 of cells complex FP64 values on the pressure lattice (not
+ * modified), iters >= 1 steps; history (host, may be NULL) receives
+ * ||Z x_k||, *rho the geometric mean of the last quarter.  Needs a 2-D context
+ * with block_rtol > 0 (else BAH_ERR_UNSUPPORTED); uses the context's Krylov
+ * workspace (no solve may run on it at the same time).  Synchronous. */
+int bah_spectral_radius_z(bah_ctx* ctx, const void* x0, int iters, double* history, double* rho, void* stream);
 
 /* Test hook: one multigrid cycle (the context's cycle type) on acoustic block
  * `block` (0..dim-1 = A_{block+1},s; dim = H_p,s) with zero initial guess.

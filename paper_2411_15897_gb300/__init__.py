@@ -37,6 +37,7 @@ BAH_KRYLOV_DF = 1
 
 # every symbol include/bah.h declares
 EXPORTS = ("bah_default_opts", "bah_create", "bah_destroy", "bah_sizes", "bah_get_info", "bah_spectral_radius",
+           "bah_spectral_radius_z",
            "bah_apply_operator",
            "bah_apply_preconditioner", "bah_solve", "bah_block_cycle", "bah_level_stencil",
            "bah_status_string", "bah_last_error", "bah_profile_control", "bah_profile_read",
@@ -57,12 +58,14 @@ class bah_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("levels", C.c_int), ("max_coarse_cells", C.c_int), ("cycle", C.c_int),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("jacobi_w", C.c_double * 8), ("n_jacobi_w", C.c_int),
                 ("shift_alpha", C.c_double), ("intergrid", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
-                ("rhs_block", C.c_int), ("krylov_arith", C.c_int)]
+                ("rhs_block", C.c_int), ("krylov_arith", C.c_int), ("block_rtol", C.c_double),
+                ("block_maxit", C.c_int), ("block_alpha", C.c_double)]
 
 
 class bah_info(C.Structure):
     _fields_ = [("levels", C.c_int), ("shift_alpha", C.c_double), ("coarse_points", C.c_int),
-                ("cluster_level", C.c_int), ("cluster_ctas", C.c_int), ("cluster_smem_bytes", C.c_longlong)]
+                ("cluster_level", C.c_int), ("cluster_ctas", C.c_int), ("cluster_smem_bytes", C.c_longlong),
+                ("block_iters", C.c_longlong), ("block_failures", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -106,6 +109,8 @@ def lib():
         L.bah_get_info.restype = C.c_int
         L.bah_spectral_radius.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.bah_spectral_radius.restype = C.c_int
+        L.bah_spectral_radius_z.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+        L.bah_spectral_radius_z.restype = C.c_int
         L.bah_apply_operator.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bah_apply_operator.restype = C.c_int
         L.bah_apply_preconditioner.argtypes = [vp, vp, vp, C.c_int, vp]
@@ -200,6 +205,16 @@ def bah_spectral_radius(ctx, x0, iters, stream=None):
     rho = C.c_double()
     _check(lib().bah_spectral_radius(ctx, _ptr(x0), int(iters), hist, C.byref(rho), _stream(stream)),
            "bah_spectral_radius")
+    return rho.value, np.array(hist[:])
+
+
+def bah_spectral_radius_z(ctx, x0, iters, stream=None):
+    """(rho, history) of the power method on Z = Xi A_s^{-1} B^T H_p,s^{-1} (Theorem 1)
+    from the device pressure-lattice vector x0 (needs a context with block_rtol > 0)."""
+    hist = (C.c_double * int(iters))()
+    rho = C.c_double()
+    _check(lib().bah_spectral_radius_z(ctx, _ptr(x0), int(iters), hist, C.byref(rho), _stream(stream)),
+           "bah_spectral_radius_z")
     return rho.value, np.array(hist[:])
 
 

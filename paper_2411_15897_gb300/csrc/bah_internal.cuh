@@ -282,6 +282,9 @@ template <int MODE, class RIN = double2>
 void launch_u_rhs(int n1, int n2, double ihx, double ihz, const RIN* r, const typename Prec<MODE>::V* ep,
                   typename Prec<MODE>::V* su1, typename Prec<MODE>::V* su2, cudaStream_t st, int nrhs = 1,
                   RhsStride rs = RhsStride());
+// y = A x (b null) or y = b - A x for one acoustic block's FP64 fine operator
+void launch_block_apply64(const Fine5<double, double2>& f5, int type, const double2* x, double2* y, const double2* b,
+                          cudaStream_t st);
 void launch_sanitize(double2* v, int n1, int n2, int nvec, cudaStream_t st);
 template <class Vin, class Vout>
 void launch_convert(const Vin* x, Vout* y, size_t n, cudaStream_t st);
@@ -302,8 +305,9 @@ void launch_dot_norm(const double2* V, int k, const double2* w, size_t n, double
                      const int* flag, int nrhs, const KS& ks, cudaStream_t st);
 void launch_axpy_norm(const double2* V, int k, const double2* coef, double2* w, size_t n, double* npart,
                       const int* flag, int nrhs, const KS& ks, cudaStream_t st);
+// flag = 1 (second pass) when ||w'||^2 < eta2 ||w||^2 (DGKS criterion; eta2 = 1/2 classically)
 void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* sc, int nrhs,
-                        const KS& ks, cudaStream_t st);
+                        const KS& ks, cudaStream_t st, double eta2 = 0.5);
 void launch_pass2_norm(const double* npart, const int* flag, double* sc, int nrhs, const KS& ks, cudaStream_t st);
 void launch_norm2(const double2* w, size_t n, double* partial, double* sc, int slot, int nrhs, const KS& ks,
                   cudaStream_t st);

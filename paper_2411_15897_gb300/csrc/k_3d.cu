@@ -398,17 +398,28 @@ __global__ void __launch_bounds__(256) k_restrict3(int type, int f1, int f2, int
     int J[3];
     coords3(p, c1, c2, J);
     if (!valid3(type, J)) { bc[p] = czero<V>(); return; }
+    using R = typename VecTraits<V>::R;
     int f[3][3], cnt[3];
-    double w[3][3];
-    for (int a = 0; a < 3; ++a) cnt[a] = rlist3(a == type, J[a], f[a], w[a]);
-    double2 acc = make_double2(0.0, 0.0);
+    double wd[3][3] = {};
+    R w[3][3];
+    for (int a = 0; a < 3; ++a) {
+        cnt[a] = rlist3(a == type, J[a], f[a], wd[a]);
+        for (int e = 0; e < 3; ++e) w[a][e] = (R)wd[a][e];     // 1/2, 1/4, 3/8, 1/8: exact in FP32
+    }
+    // accumulated in the cycle's arithmetic (FP32 in mixed mode)
+    V acc = czero<V>();
     for (int z = 0; z < cnt[2]; ++z)
-        for (int y = 0; y < cnt[1]; ++y)
+        for (int y = 0; y < cnt[1]; ++y) {
+            const R wzy = w[2][z] * w[1][y];
             for (int x = 0; x < cnt[0]; ++x) {
                 const size_t q = ((size_t)f[2][z] * f2 + f[1][y]) * f1 + f[0][x];
-                acc = cadd(acc, cscale(cconv<double2>(r[q]), w[2][z] * w[1][y] * w[0][x]));
+                const V v = r[q];
+                const R ww = wzy * w[0][x];
+                acc.x += ww * v.x;
+                acc.y += ww * v.y;
             }
-    bc[p] = cconv<V>(acc);
+        }
+    bc[p] = acc;
 }
 
 // x += P e_c on the fine grid
@@ -423,17 +434,27 @@ __global__ void __launch_bounds__(256) k_prolong3(int type, int f1, int f2, int 
     int F[3];
     coords3(p, f1, f2, F);
     if (!valid3(type, F)) return;
+    using R = typename VecTraits<V>::R;
     int K[3][2], cnt[3];
-    double w[3][2];
-    for (int a = 0; a < 3; ++a) cnt[a] = plist3(a == type, F[a], nc[a], K[a], w[a]);
-    double2 acc = make_double2(0.0, 0.0);
+    double wd[3][2] = {};
+    R w[3][2];
+    for (int a = 0; a < 3; ++a) {
+        cnt[a] = plist3(a == type, F[a], nc[a], K[a], wd[a]);
+        for (int e = 0; e < 2; ++e) w[a][e] = (R)wd[a][e];     // 1, 1/2, 3/4, 1/4: exact in FP32
+    }
+    V acc = czero<V>();
     for (int z = 0; z < cnt[2]; ++z)
-        for (int y = 0; y < cnt[1]; ++y)
+        for (int y = 0; y < cnt[1]; ++y) {
+            const R wzy = w[2][z] * w[1][y];
             for (int xx = 0; xx < cnt[0]; ++xx) {
                 const size_t q = ((size_t)K[2][z] * c2 + K[1][y]) * c1 + K[0][xx];
-                acc = cadd(acc, cscale(cconv<double2>(ec[q]), w[2][z] * w[1][y] * w[0][xx]));
+                const V v = ec[q];
+                const R ww = wzy * w[0][xx];
+                acc.x += ww * v.x;
+                acc.y += ww * v.y;
             }
-    x[p] = cadd(x[p], cconv<V>(acc));
+        }
+    x[p] = cadd(x[p], acc);
 }
 
 template <class V>

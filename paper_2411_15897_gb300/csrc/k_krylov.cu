@@ -185,7 +185,7 @@ void launch_axpy_norm(const double2* V, int k, const double2* coef, double2* w, 
 // step: sc[2] = ||w_final||, sc[3] counts second passes; flag = 1 when
 // ||w'||^2 < ||w||^2 / 2
 __global__ void __launch_bounds__(256) k_dgks_decide(const double* npart, int np, const double2* h1norm, int k,
-                                                     int* flag, double* sc, KS ks) {
+                                                     int* flag, double* sc, double eta2, KS ks) {
     pdl_prologue();
     const int r = blockIdx.x;
     if (inactive(ks, r)) return;
@@ -195,15 +195,15 @@ __global__ void __launch_bounds__(256) k_dgks_decide(const double* npart, int np
     double2 s = block_sum2(make_double2(acc, 0.0));
     if (threadIdx.x == 0) {
         const double w0 = h1norm[r * ks.so + k].x;          // ||w||^2 before pass 1
-        const int f = (s.x < 0.5 * w0) ? 1 : 0;
+        const int f = (s.x < eta2 * w0) ? 1 : 0;
         flag[r] = f;
         sc[r * 8 + 2] = sqrt(s.x);
         sc[r * 8 + 3] += (double)f;
     }
 }
 void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* sc, int nrhs,
-                        const KS& ks, cudaStream_t st) {
-    launch_pdl(k_dgks_decide, dim3(nrhs), dim3(256), 0, st, npart, RED_CTAS, h1norm, k, flag, sc, ks);
+                        const KS& ks, cudaStream_t st, double eta2) {
+    launch_pdl(k_dgks_decide, dim3(nrhs), dim3(256), 0, st, npart, RED_CTAS, h1norm, k, flag, sc, eta2, ks);
 }
 // after pass 2: ||w''|| replaces ||w'||
 __global__ void __launch_bounds__(256) k_pass2_norm(const double* npart, int np, const int* flag, double* sc, KS ks) {

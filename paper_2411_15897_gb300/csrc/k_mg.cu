@@ -386,6 +386,29 @@ void launch_coarse_apply(int nb, int npts, const double2* const* inv, const type
     launch_pdl(k_coarse_apply<V>, dim3(g), dim3(256), smem, st, npts, pi, pb, px, rs.active);
 }
 
+// ---------------------------------------------------------------------------
+// one acoustic block's fine operator in FP64 (the 5-point stencil of Eq. 2.6 /
+// 3.4 with the diagonals given in f5): y = A x, or y = b - A x.  The operator
+// of the inner block solves of the exact-block preconditioner.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_block_apply64(Fine5<double, double2> f5, int type,
+                                                       const double2* __restrict__ x, double2* __restrict__ y,
+                                                       const double2* __restrict__ b) {
+    pdl_prologue();
+    const int n1 = f5.n1, n2 = f5.n2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n1 * n2) return;
+    const int i = t % n1, j = t / n1;
+    if (!valid_pt(type, i, j)) { y[t] = make_double2(0.0, 0.0); return; }
+    const double2 ax = apply_fine5_fn<BAH_FP64>(f5, type, i, j, t, [&](int g) { return x[g]; });
+    y[t] = b ? csub(b[t], ax) : ax;
+}
+void launch_block_apply64(const Fine5<double, double2>& f5, int type, const double2* x, double2* y, const double2* b,
+                          cudaStream_t st) {
+    const int np = f5.n1 * f5.n2;
+    launch_pdl(k_block_apply64, dim3((np + 255) / 256), dim3(256), 0, st, f5, type, x, y, b);
+}
+
 #define INST(MODE)                                                                                                 \
     template void launch_jacobi<MODE>(const LvlSet<Prec<MODE>::V, Prec<MODE>::CC>&,                                \
                                       const Fine5<Prec<MODE>::C, Prec<MODE>::CC>*, double, int, cudaStream_t);     \

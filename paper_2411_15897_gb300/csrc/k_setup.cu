@@ -240,63 +240,122 @@ __global__ void k_dense_assemble(int type, const double2* S, int rx, int rz, int
     X[(size_t)r * np + c] = make_double2(c == r ? 1.0 : 0.0, 0.0);
 }
 
-__global__ void k_gj_pivot(int n, int k, double2* A, double2* X, double2* f, int* flag) {
-    __shared__ double bestv[256];
-    __shared__ int besti[256];
-    double bv = -1.0;
-    int bi = k;
-    for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-        double2 a = A[(size_t)r * n + k];
-        double m = a.x * a.x + a.y * a.y;
-        if (m > bv) { bv = m; bi = r; }
-    }
-    bestv[threadIdx.x] = bv;
-    besti[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            if (bestv[threadIdx.x + s] > bestv[threadIdx.x] ||
-                (bestv[threadIdx.x + s] == bestv[threadIdx.x] && besti[threadIdx.x + s] < besti[threadIdx.x])) {
-                bestv[threadIdx.x] = bestv[threadIdx.x + s];
-                besti[threadIdx.x] = besti[threadIdx.x + s];
-            }
-        }
-        __syncthreads();
-    }
-    const int p = besti[0];
-    if (bestv[0] <= 0.0) {
-        if (threadIdx.x == 0) *flag = 1;
-        return;
-    }
-    if (p != k) {
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            double2 t1 = A[(size_t)k * n + c]; A[(size_t)k * n + c] = A[(size_t)p * n + c]; A[(size_t)p * n + c] = t1;
-            double2 t2 = X[(size_t)k * n + c]; X[(size_t)k * n + c] = X[(size_t)p * n + c]; X[(size_t)p * n + c] = t2;
-        }
-    }
-    __syncthreads();
-    const double2 piv = A[(size_t)k * n + k];
-    const double2 ip = cdiv(make_double2(1.0, 0.0), piv);
-    __syncthreads();
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        A[(size_t)k * n + c] = cmul(A[(size_t)k * n + c], ip);
-        X[(size_t)k * n + c] = cmul(X[(size_t)k * n + c], ip);
-    }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) f[r] = (r == k) ? make_double2(0.0, 0.0) : A[(size_t)r * n + k];
+// ---------------------------------------------------------------------------
+// Dense FP64 inverse by Gauss-Jordan elimination with partial pivoting on
+// [A | X], X = I at entry, in one launch of one thread-block cluster.  The
+// matrices stay in global memory (they fit in L2); CTA q of the cluster owns
+// the rows r = q (mod CTAs).  Per column k:
+//   1. each CTA finds its largest |A[r][k]|, r >= k, among its rows;
+//   2. every CTA reads the candidates of all CTAs from distributed shared
+//      memory and takes the same winner p (largest, lowest index on ties);
+//   3. rows k and p are swapped in A and X (columns split over the CTAs);
+//   4. row k is scaled by 1 / A[k][k] (column k itself is never read again);
+//   5. every other row r subtracts A[r][k] times row k.
+// A hardware cluster barrier separates the steps: the control flow is the
+// same in every CTA (the winner, and so a singular pivot, is seen by all), so
+// every CTA arrives at every barrier.
+// ---------------------------------------------------------------------------
+constexpr int kGjThreads = 512;
+
+__device__ __forceinline__ uint32_t gj_mapa(const void* p, unsigned rank) {
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double gj_ld_f64(uint32_t a) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int gj_ld_s32(uint32_t a) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
 }
 
-__global__ void k_gj_eliminate(int n, int k, double2* A, double2* X, const double2* f) {
-    const int r = blockIdx.y;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == k || c >= n) return;
-    const double2 fr = f[r];
-    if (fr.x == 0.0 && fr.y == 0.0) return;
-    if (c >= k) {
-        double2 a = A[(size_t)r * n + c];
-        A[(size_t)r * n + c] = csub(a, cmul(fr, A[(size_t)k * n + c]));
+__global__ void __launch_bounds__(kGjThreads, 1) k_gj_cluster(int n, double2* A, double2* X, int* flag) {
+    const unsigned q = cluster_rank(), nq = cluster_nrank();
+    const int tid = threadIdx.x, nth = blockDim.x;
+    __shared__ double wv[kGjThreads / 32];
+    __shared__ int wi[kGjThreads / 32];
+    __shared__ double cand_v;          // this CTA's pivot candidate, read by every CTA
+    __shared__ int cand_i;
+    __shared__ int piv_row;
+    __shared__ int singular;
+    for (int k = 0; k < n; ++k) {
+        // 1. local candidate among own rows r >= k
+        double bv = -1.0;
+        int bi = n;
+        for (int r = (int)q + (int)nq * tid; r < n; r += (int)nq * nth) {
+            if (r < k) continue;
+            const double2 a = A[(size_t)r * n + k];
+            const double m = a.x * a.x + a.y * a.y;
+            if (m > bv || (m == bv && r < bi)) { bv = m; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { wv[tid >> 5] = bv; wi[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nth / 32; ++w)
+                if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
+            cand_v = bv;
+            cand_i = bi;
+        }
+        cluster_barrier();
+        // 2. the common winner
+        if (tid == 0) {
+            double best = -1.0;
+            int p = n;
+            for (unsigned s = 0; s < nq; ++s) {
+                const double v = gj_ld_f64(gj_mapa(&cand_v, s));
+                const int i = gj_ld_s32(gj_mapa(&cand_i, s));
+                if (v > best || (v == best && i < p)) { best = v; p = i; }
+            }
+            piv_row = p;
+            singular = !(best > 0.0) || p >= n;
+        }
+        __syncthreads();
+        if (singular) {
+            if (q == 0 && tid == 0) *flag = 1;
+            cluster_barrier();              // no CTA exits while another still reads its candidate
+            break;                          // taken by every CTA at the same k
+        }
+        const int p = piv_row;
+        // 3. swap rows k and p (columns split over the cluster)
+        if (p != k) {
+            for (int c = (int)q * nth + tid; c < n; c += (int)nq * nth) {
+                double2 t1 = A[(size_t)k * n + c]; A[(size_t)k * n + c] = A[(size_t)p * n + c]; A[(size_t)p * n + c] = t1;
+                double2 t2 = X[(size_t)k * n + c]; X[(size_t)k * n + c] = X[(size_t)p * n + c]; X[(size_t)p * n + c] = t2;
+            }
+        }
+        cluster_barrier();
+        // 4. scale the pivot row (A[k][k] is left as is: column k is never read again)
+        const double2 ip = cdiv(make_double2(1.0, 0.0), A[(size_t)k * n + k]);
+        for (int c = (int)q * nth + tid; c < n; c += (int)nq * nth) {
+            if (c > k) A[(size_t)k * n + c] = cmul(A[(size_t)k * n + c], ip);
+            X[(size_t)k * n + c] = cmul(X[(size_t)k * n + c], ip);
+        }
+        cluster_barrier();
+        // 5. eliminate column k from every other own row: columns c > k of A, all of X
+        const int nown = (n - (int)q + (int)nq - 1) / (int)nq;
+        const int w2 = 2 * n;
+        for (int e = tid; e < nown * w2; e += nth) {
+            const int r = (int)q + (int)nq * (e / w2), c = e % w2;
+            if (r == k) continue;
+            const double2 f = A[(size_t)r * n + k];
+            if (c < n) {
+                if (c > k) A[(size_t)r * n + c] = csub(A[(size_t)r * n + c], cmul(f, A[(size_t)k * n + c]));
+            } else {
+                const int cx = c - n;
+                X[(size_t)r * n + cx] = csub(X[(size_t)r * n + cx], cmul(f, X[(size_t)k * n + cx]));
+            }
+        }
+        cluster_barrier();
     }
-    double2 x = X[(size_t)r * n + c];
-    X[(size_t)r * n + c] = csub(x, cmul(fr, X[(size_t)k * n + c]));
 }
 
 int coarse_invert(int type, const StencilF64& S, double2* inv, double2* work, int* flag, cudaStream_t st) {
@@ -308,14 +367,46 @@ int coarse_invert(int type, const StencilF64& S, double2* inv, double2* work, in
     return gauss_jordan(n, A, inv, f, flag, st);
 }
 
-int gauss_jordan(int n, double2* A, double2* X, double2* f, int* flag, cudaStream_t st) {
-    dim3 g((n + 127) / 128, n);
-    BAH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
-    for (int k = 0; k < n; ++k) {
-        k_gj_pivot<<<1, 256, 0, st>>>(n, k, A, X, f, flag);
-        k_gj_eliminate<<<g, 128, 0, st>>>(n, k, A, X, f);
+// CTAs per cluster for the Gauss-Jordan kernel: 16 where the device allows
+// non-portable clusters, else 8
+static int gj_cluster_size() {
+    static int cs = 0;
+    if (cs) return cs;
+    cs = 8;
+    if (cudaFuncSetAttribute((const void*)k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(kGjThreads);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, (const void*)k_gj_cluster, &cfg) == cudaSuccess && nc >= 1) cs = 16;
     }
-    BAH_CUDA_TRY(cudaGetLastError());
+    cudaGetLastError();
+    return cs;
+}
+
+int gauss_jordan(int n, double2* A, double2* X, double2* /*f*/, int* flag, cudaStream_t st) {
+    BAH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    const int cs = gj_cluster_size();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kGjThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BAH_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster, n, A, X, flag));
     int h = 0;
     BAH_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     BAH_CUDA_TRY(cudaStreamSynchronize(st));

@@ -104,10 +104,27 @@ struct Ctx {
     bool use_graphs = true;
     bool staged = true;                  // shared-memory staging of Galerkin-level sweeps (BAH_STAGED=0: off)
     bool fuse = true;                    // fused level visits above the cluster levels (BAH_FUSED_LEVELS=0: off)
+    double dgks_eta2 = 0.5;              // second Gram-Schmidt pass when ||w'||^2 < eta2 ||w||^2
     int sm_l0 = 0;                       // first level of the shared-memory cluster multigrid (0: off)
     int sm_cs = 0, sm_rm = 2;            // its CTAs per cluster and stencil radius bound
     size_t sm_bytes = 0;                 // its dynamic shared memory per CTA
     int nsm = 0;
+
+    // exact-block preconditioner (block_rtol > 0): each acoustic block solved
+    // by an inner FGMRES(mi) in FP64, preconditioned by its multigrid cycle
+    bool exact = false;
+    Fine5<double, double2> f5x{};       // FP64 block operators, diagonals shifted by block_alpha
+    int mi = 30;
+    double2 *iV = nullptr, *iZ = nullptr, *iW = nullptr, *iR = nullptr, *iH = nullptr;
+    double2 *ih1 = nullptr, *ih2 = nullptr, *ics = nullptr, *isn = nullptr, *igv = nullptr, *iy = nullptr;
+    double2* ipart = nullptr;
+    double *inrm = nullptr, *idpart = nullptr, *istatus = nullptr;
+    int *iflag = nullptr, *ijk = nullptr;
+    double* histat = nullptr;           // pinned: 8 status / norm slots and one int
+    double2 *ez = nullptr, *etp = nullptr, *esu = nullptr;
+    long long block_iters = 0;
+    int block_failures = 0;
+    int exact_status = BAH_OK;          // first failure of a block solve inside a preconditioner call
 
     // three-dimensional grids (dim == 3): n1 x n2 x n3 cells
     int n3 = 1;
@@ -133,6 +150,7 @@ struct Ctx {
         for (void* p : allocs) cudaFree(p);
         if (hstatus) cudaFreeHost(hstatus);
         if (hint) cudaFreeHost(hint);
+        if (histat) cudaFreeHost(histat);
     }
     int alloc(void** p, size_t bytes) {
         *p = nullptr;
@@ -577,9 +595,124 @@ struct MG3 {
     }
 };
 
+// ---------------------------------------------------------------------------
+// exact-block preconditioner (block_rtol > 0; Sec. 4.1, Table 2; Theorem 1):
+// every acoustic block is solved, not approximated.  The inner solver is
+// FGMRES(mi) in FP64 on the block's fine operator (shifted by block_alpha),
+// right preconditioned by the block's multigrid cycle in the context's
+// precision; x_0 = 0; it stops when ||s - M e|| <= block_rtol ||s||.  Driven
+// from the host (one status read per inner iteration), so these calls are
+// not captured in graphs.
+// ---------------------------------------------------------------------------
+static int read_dev_double(Ctx& c, const double* dev, double* out, cudaStream_t st) {
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.histat, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = c.histat[0];
+    return BAH_OK;
+}
+
+template <int MODE>
+static int block_solve(Ctx& c, int b, const double2* s, double2* e, cudaStream_t st) {
+    using V = typename Prec<MODE>::V;
+    const size_t np = c.np;
+    const int m = c.mi;
+    const double rtol = c.o.block_rtol;
+    KS ks;                                  // one right-hand side: no strides, no flags
+    Batch one;
+    launch_norm2(s, np, c.idpart, c.inrm, 1, 1, ks, st);
+    double bn = 0.0;
+    TRY(read_dev_double(c, c.inrm + 1, &bn, st));
+    BAH_CUDA_TRY(cudaMemsetAsync(e, 0, np * sizeof(double2), st));
+    if (!std::isfinite(bn)) return BAH_ERR_NONFINITE;
+    if (!(bn > 0.0)) return BAH_OK;
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.iR, s, np * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.inrm, c.inrm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double beta = bn;
+    int total = 0;
+    while (beta > rtol * bn) {
+        if (total >= c.o.block_maxit) { ++c.block_failures; break; }
+        launch_scale_copy(c.iR, c.inrm, 0, c.iV, np, 0, 0, 1, ks, st);
+        launch_init_arnoldi(c.inrm, c.igv, m, c.istatus, 1, ks, st);
+        int jd = 0;
+        for (int j = 0; j < m && total < c.o.block_maxit; ++j) {
+            const double2* vj = c.iV + (size_t)j * np;
+            double2* zj = c.iZ + (size_t)j * np;
+            // z_j = (one multigrid cycle of the block) v_j
+            if constexpr (MODE == BAH_MIXED) {
+                launch_convert<double2, float2>(vj, (float2*)c.vB[0][b], np, st);
+                V* o[1] = {(V*)c.ztmp};
+                MG<MODE>::cycle(c, 0, b, 1, o, np, one, st);
+                launch_convert<float2, double2>((const float2*)c.ztmp, zj, np, st);
+            } else {
+                BAH_CUDA_TRY(cudaMemcpyAsync(c.vB[0][b], vj, np * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+                V* o[1] = {zj};
+                MG<MODE>::cycle(c, 0, b, 1, o, np, one, st);
+            }
+            // w = M z_j, Gram-Schmidt with selective reorthogonalisation, Givens, v_{j+1}
+            launch_block_apply64(c.f5x, b, zj, c.iW, nullptr, st);
+            launch_dot_norm(c.iV, j + 1, c.iW, np, c.ipart, c.ih1, nullptr, 1, ks, st);
+            launch_axpy_norm(c.iV, j + 1, c.ih1, c.iW, np, c.idpart, nullptr, 1, ks, st);
+            launch_dgks_decide(c.idpart, c.ih1, j + 1, c.iflag, c.inrm, 1, ks, st);
+            launch_dot_norm(c.iV, j + 1, c.iW, np, c.ipart, c.ih2, c.iflag, 1, ks, st);
+            launch_axpy_norm(c.iV, j + 1, c.ih2, c.iW, np, c.idpart, c.iflag, 1, ks, st);
+            launch_pass2_norm(c.idpart, c.iflag, c.inrm, 1, ks, st);
+            launch_arnoldi_givens(c.iH, m + 1, c.ih1, c.ih2, c.inrm, j, c.ics, c.isn, c.igv, c.istatus, 1, ks, st);
+            launch_scale_copy(c.iW, c.inrm, 2, c.iV + (size_t)(j + 1) * np, np, 0, 0, 1, ks, st);
+            BAH_CUDA_TRY(cudaMemcpyAsync(c.histat, c.istatus, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            BAH_CUDA_TRY(cudaStreamSynchronize(st));
+            ++total;
+            jd = j + 1;
+            const double est = c.histat[0] / bn;
+            if (c.histat[2] != 0.0 || !std::isfinite(est)) return BAH_ERR_NONFINITE;
+            if (est <= rtol || c.histat[1] <= 1e-14 * bn) break;
+        }
+        // e += Z y, then the true residual s - M e
+        int* hj = reinterpret_cast<int*>(c.histat + 4);
+        *hj = jd;
+        BAH_CUDA_TRY(cudaMemcpyAsync(c.ijk, hj, sizeof(int), cudaMemcpyHostToDevice, st));
+        launch_triangular_solve(c.iH, m + 1, c.igv, c.ijk, c.iy, 1, ks, st);
+        launch_update_x<double2>(c.iZ, c.ijk, c.iy, e, np, 1, ks, st);
+        launch_block_apply64(c.f5x, b, e, c.iR, s, st);
+        launch_norm2(c.iR, np, c.idpart, c.inrm, 0, 1, ks, st);
+        BAH_CUDA_TRY(cudaGetLastError());
+        TRY(read_dev_double(c, c.inrm, &beta, st));
+        if (!std::isfinite(beta)) return BAH_ERR_NONFINITE;
+    }
+    c.block_iters += total;
+    return BAH_OK;
+}
+
+// z = P^{-1} D r with every block solved (r: one padded vector, FP64 or
+// double-float; z: FP64): t_p = B r_u - A_p r_p, H_p e_p = t_p,
+// s_u = r_u - B^T e_p, A_k e_k = s_k (Eq. 3.1-3.5)
+template <class RIN>
+static int precond_exact(Ctx& c, const RIN* r, double2* z, cudaStream_t st) {
+    const size_t np = c.np;
+    const double ihx = 1.0 / c.h1, ihz = 1.0 / c.h2;
+    auto solve = [&](int b, const double2* s, double2* e) {
+        return c.mode == BAH_MIXED ? block_solve<BAH_MIXED>(c, b, s, e, st) : block_solve<BAH_FP64>(c, b, s, e, st);
+    };
+    launch_distributor<BAH_FP64, RIN>(c.n1, c.n2, ihx, ihz, c.f5x, r, c.etp, st, 1, RhsStride());
+    TRY(solve(2, c.etp, z + 2 * np));
+    launch_u_rhs<BAH_FP64, RIN>(c.n1, c.n2, ihx, ihz, r, z + 2 * np, c.esu, c.esu + np, st, 1, RhsStride());
+    TRY(solve(0, c.esu, z));
+    TRY(solve(1, c.esu + np, z + np));
+    return BAH_OK;
+}
+
 template <class RIN>
 static void precond_any(Ctx& c, const RIN* r, size_t rstride, void* z, size_t zstride, const Batch& bt,
                         cudaStream_t st) {
+    if (c.exact) {
+        // one right-hand side (rhs_block = 1 with exact blocks); the FP64 result is
+        // rounded once to the flexible basis' precision in mixed mode
+        if (c.exact_status != BAH_OK) return;
+        double2* zz = c.mode == BAH_MIXED ? c.ez : (double2*)z;
+        const int s = precond_exact<RIN>(c, r, zz, st);
+        if (s != BAH_OK) { c.exact_status = s; return; }
+        if (c.mode == BAH_MIXED) launch_convert<double2, float2>(c.ez, (float2*)z, c.vec_len(), st);
+        return;
+    }
     if constexpr (std::is_same<RIN, double2>::value) {
         if (c.dim == 3) {
             for (int k = 0; k < bt.nr; ++k) {
@@ -847,8 +980,41 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
         }
     }
     TRY(alloc_krylov(c, st));
+    if (c.exact) {
+        // the blocks solved exactly: the fine operators of Eq. 2.6 / 3.4 with their
+        // diagonals shifted by block_alpha (a second medium preparation, of which
+        // only the three block diagonals are kept), FP64 coefficients throughout
+        double2* dgb[3];
+        for (int b = 0; b < 3; ++b) TRY(c.alloc_t(&dgb[b], np));
+        {
+            void* scratch = nullptr;
+            BAH_CUDA_TRY(cudaMalloc(&scratch, (size_t)np * (7 * sizeof(double) + 3 * sizeof(double2))));
+            double* sd = (double*)scratch;
+            double2* sc2 = (double2*)(sd + 7 * (size_t)np);
+            launch_medium_prep(c.n1, c.n2, c.h1, c.h2, c.omega, c.o.block_alpha, lam, mu, rho, gam, sd, sd + np,
+                               sd + 2 * (size_t)np, sd + 3 * (size_t)np, sd + 4 * (size_t)np, sd + 5 * (size_t)np,
+                               sc2, sc2 + np, sd + 6 * (size_t)np, dgb[0], dgb[1], dgb[2], sc2 + 2 * (size_t)np, st);
+            cudaError_t e1 = cudaStreamSynchronize(st);
+            cudaFree(scratch);
+            BAH_CUDA_TRY(e1);
+        }
+        c.f5x = Fine5<double, double2>{c.n1, c.n2, c.cx, c.cz, c.nx, c.nz, c.wx, c.wz, dgb[0], dgb[1], dgb[2], c.dAp};
+        const size_t so = c.mi + 2;
+        TRY(c.alloc_t(&c.iV, (size_t)(c.mi + 1) * np)); TRY(c.alloc_t(&c.iZ, (size_t)c.mi * np));
+        TRY(c.alloc_t(&c.iW, np)); TRY(c.alloc_t(&c.iR, np));
+        TRY(c.alloc_t(&c.iH, (size_t)(c.mi + 1) * c.mi));
+        TRY(c.alloc_t(&c.ih1, so)); TRY(c.alloc_t(&c.ih2, so)); TRY(c.alloc_t(&c.ics, so)); TRY(c.alloc_t(&c.isn, so));
+        TRY(c.alloc_t(&c.igv, so)); TRY(c.alloc_t(&c.iy, so));
+        TRY(c.alloc_t(&c.ipart, so * RED_CTAS)); TRY(c.alloc_t(&c.idpart, (size_t)RED_CTAS));
+        TRY(c.alloc_t(&c.inrm, 8)); TRY(c.alloc_t(&c.istatus, 4)); TRY(c.alloc_t(&c.iflag, 1)); TRY(c.alloc_t(&c.ijk, 1));
+        TRY(c.alloc_t(&c.ez, 3 * (size_t)np)); TRY(c.alloc_t(&c.etp, np)); TRY(c.alloc_t(&c.esu, 2 * (size_t)np));
+        BAH_CUDA_TRY(cudaMemsetAsync(c.inrm, 0, 8 * sizeof(double), st));
+        BAH_CUDA_TRY(cudaMallocHost((void**)&c.histat, 16 * sizeof(double)));
+        c.use_graphs = false;             // the block solves read their status on the host
+    }
     if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
     if (const char* e = getenv("BAH_FUSED_LEVELS")) c.fuse = (e[0] != '0');
+    if (const char* e = getenv("BAH_DGKS_ETA2")) c.dgks_eta2 = atof(e);
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
     return BAH_OK;
@@ -994,7 +1160,7 @@ static void iter_body(Ctx& c, int j, cudaStream_t st) {
     }
     {
         Prof pr(c, BAH_K_NORM, st, 0.0);
-        launch_dgks_decide(c.dpart, c.h1v, j + 1, c.gsflag, c.nrm, nb, ks, st);
+        launch_dgks_decide(c.dpart, c.h1v, j + 1, c.gsflag, c.nrm, nb, ks, st, c.dgks_eta2);
     }
     {
         Prof pr(c, BAH_K_DOT, st, 0.0, 2);      // runs only where the flag is set (bytes counted as zero)
@@ -1121,6 +1287,10 @@ static int fgmres_batch(Ctx& c, const double2* b, double2* x, int nr, double rto
         for (int j = 0; j < mm; ++j) {
             if (j + 1 < mm) TRY(launch_iter(c, j + 1, st));    // queued behind step j
             TRY(finish_iter(c, j));
+            if (c.exact_status != BAH_OK) {
+                set_error("an exact block solve failed inside the preconditioner");
+                return c.exact_status;
+            }
             const double* hs = status_slot(c, j);
             ++total;
             bool changed = false;
@@ -1233,6 +1403,9 @@ void bah_default_opts(bah_opts* o) {
     o->maxit = 5000;
     o->rhs_block = 1;
     o->krylov_arith = BAH_KRYLOV_FP64;
+    o->block_rtol = 0.0;
+    o->block_maxit = 500;
+    o->block_alpha = 0.0;
 }
 
 const char* bah_status_string(int s) {
@@ -1282,6 +1455,14 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
         return BAH_ERR_ARG;
     }
     if (o.cycle != BAH_CYCLE_V && o.cycle != BAH_CYCLE_W) { set_error("bad cycle"); return BAH_ERR_ARG; }
+    if (!(o.block_rtol >= 0.0) || o.block_maxit < 1 || !(o.block_alpha >= 0.0)) {
+        set_error("block_rtol and block_alpha must be >= 0 and block_maxit >= 1");
+        return BAH_ERR_ARG;
+    }
+    if (o.block_rtol > 0.0 && (dim != 2 || o.rhs_block != 1)) {
+        set_error("exact block solves (block_rtol > 0) are implemented for 2-D grids with rhs_block = 1");
+        return BAH_ERR_UNSUPPORTED;
+    }
     if (dim == 3 && o.intergrid != BAH_INTERGRID_MIXED) {
         set_error("3-D grids need intergrid = BAH_INTERGRID_MIXED (Eq. 4.4)");
         return BAH_ERR_UNSUPPORTED;
@@ -1303,6 +1484,7 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     c.m = o.restart;
     c.nbatch = o.rhs_block;
     c.kdf = o.krylov_arith == BAH_KRYLOV_DF;
+    c.exact = o.block_rtol > 0.0;
     // levels
     int L = 1;
     {
@@ -1374,6 +1556,8 @@ int bah_get_info(const bah_ctx* h, bah_info* out) {
     out->cluster_level = c.sm_l0;
     out->cluster_ctas = c.sm_cs;
     out->cluster_smem_bytes = (long long)c.sm_bytes;
+    out->block_iters = c.block_iters;
+    out->block_failures = c.block_failures;
     return BAH_OK;
 }
 
@@ -1394,6 +1578,7 @@ int bah_apply_preconditioner(bah_ctx* h, const void* r, void* z, int nrhs, void*
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = c.vec_len();
     Batch one;
+    c.exact_status = BAH_OK;
     for (int k = 0; k < nrhs; ++k) {
         const double2* rk = (const double2*)r + k * n;
         double2* zk = (double2*)z + k * n;
@@ -1405,6 +1590,10 @@ int bah_apply_preconditioner(bah_ctx* h, const void* r, void* z, int nrhs, void*
         }
     }
     BAH_CUDA_TRY(cudaGetLastError());
+    if (c.exact_status != BAH_OK) {
+        set_error("an exact block solve failed inside the preconditioner");
+        return c.exact_status;
+    }
     return BAH_OK;
 }
 
@@ -1419,6 +1608,7 @@ int bah_spectral_radius(bah_ctx* h, const void* x0, int iters, double* history, 
     double2* t = c.Bs;
     KS ks;
     Batch one;
+    c.exact_status = BAH_OK;
     launch_norm2((const double2*)x0, n, c.dpart, c.nrm, 0, 1, ks, st);
     launch_scale_copy((const double2*)x0, c.nrm, 0, x, n, 0, 0, 1, ks, st);
     std::vector<double> hist(iters);
@@ -1433,6 +1623,59 @@ int bah_spectral_radius(bah_ctx* h, const void* x0, int iters, double* history, 
         launch_sub(x, z, t, n, st);
         launch_norm2(t, n, c.dpart, c.nrm, 0, 1, ks, st);
         launch_scale_copy(t, c.nrm, 0, x, n, 0, 0, 1, ks, st);
+        BAH_CUDA_TRY(cudaGetLastError());
+        BAH_CUDA_TRY(cudaMemcpyAsync(&hist[k], c.nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+        BAH_CUDA_TRY(cudaStreamSynchronize(st));
+        if (c.exact_status != BAH_OK) {
+            set_error("an exact block solve failed inside the preconditioner");
+            return c.exact_status;
+        }
+        if (!std::isfinite(hist[k])) { set_error("non-finite value in the power method"); return BAH_ERR_NONFINITE; }
+        if (hist[k] == 0.0) { iters = k + 1; break; }
+    }
+    const int q = std::max(1, iters / 4);
+    double acc = 0.0;
+    for (int k = iters - q; k < iters; ++k) acc += std::log(std::max(hist[k], 1e-300));
+    *rho = std::exp(acc / q);
+    if (history)
+        for (int k = 0; k < iters; ++k) history[k] = hist[k];
+    return BAH_OK;
+}
+
+int bah_spectral_radius_z(bah_ctx* h, const void* x0, int iters, double* history, double* rho, void* stream) {
+    if (!h || !x0 || iters < 1 || !rho) { set_error("bad argument"); return BAH_ERR_ARG; }
+    Ctx& c = h->c;
+    if (!c.exact) {
+        set_error("bah_spectral_radius_z needs exact block solves (a 2-D context with block_rtol > 0)");
+        return BAH_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t np = c.np, n = c.vec_len();
+    const double ihx = 1.0 / c.h1, ihz = 1.0 / c.h2;
+    KS ks;
+    double2* v = c.W;                   // pressure-lattice iterate (np)
+    double2* zero = c.Bs;               // a zero padded vector (the r of s_u = r_u - B^T e)
+    double2* Y = c.X;                   // [A_s^{-1} s_u ; 0]
+    double2* Q = c.R;                   // H [y ; 0] = [A y ; B y]
+    double2* ep = c.etp;                // H_p,s^{-1} v, then Xi y
+    auto solve = [&](int b, const double2* s, double2* e) {
+        return c.mode == BAH_MIXED ? block_solve<BAH_MIXED>(c, b, s, e, st) : block_solve<BAH_FP64>(c, b, s, e, st);
+    };
+    c.exact_status = BAH_OK;
+    BAH_CUDA_TRY(cudaMemsetAsync(zero, 0, n * sizeof(double2), st));
+    BAH_CUDA_TRY(cudaMemsetAsync(Y, 0, n * sizeof(double2), st));
+    launch_norm2((const double2*)x0, np, c.dpart, c.nrm, 0, 1, ks, st);
+    launch_scale_copy((const double2*)x0, c.nrm, 0, v, np, 0, 0, 1, ks, st);
+    std::vector<double> hist(iters);
+    for (int k = 0; k < iters; ++k) {
+        TRY(solve(2, v, ep));                                                    // H_p,s^{-1} v
+        launch_u_rhs<BAH_FP64, double2>(c.n1, c.n2, ihx, ihz, zero, ep, c.esu, c.esu + np, st, 1, RhsStride());
+        TRY(solve(0, c.esu, Y));                                                 // -A_s^{-1} B^T H_p,s^{-1} v
+        TRY(solve(1, c.esu + np, Y + np));
+        apply_h(c, Y, 0, Q, 0, nullptr, 0, 0, 1, st);                            // [A y ; B y]
+        launch_distributor<BAH_FP64, double2>(c.n1, c.n2, ihx, ihz, c.f5x, Q, ep, st, 1, RhsStride());   // B A y - A_p B y
+        launch_norm2(ep, np, c.dpart, c.nrm, 0, 1, ks, st);
+        launch_scale_copy(ep, c.nrm, 0, v, np, 0, 0, 1, ks, st);
         BAH_CUDA_TRY(cudaGetLastError());
         BAH_CUDA_TRY(cudaMemcpyAsync(&hist[k], c.nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
         BAH_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1533,6 +1776,7 @@ static int solve_impl(bah_ctx* h, const void* b, void* x, int nrhs, double rtol,
     const bool dev_b = is_device_ptr(b), dev_x = is_device_ptr(x);
     if (dev_b != dev_x) { set_error("b and x must both be device or both be host pointers"); return BAH_ERR_ARG; }
     int first_fail = BAH_OK;
+    c.exact_status = BAH_OK;
     for (int k0 = 0; k0 < nrhs; k0 += c.nbatch) {
         const int nr = std::min(c.nbatch, nrhs - k0);
         const double2* bk = (const double2*)b + (size_t)k0 * n;
