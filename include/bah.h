@@ -115,7 +115,7 @@ typedef struct {
      * block is solved to ||s - M e|| <= block_rtol ||s|| by an inner FGMRES in
      * FP64, preconditioned by that block's multigrid cycle -- the exact-block
      * preconditioner of Sec. 4.1 (Table 2) and of Theorem 1 (Sec. 3) as
-     * block_rtol -> 0, at any grid size.  The blocks solved are shifted by
+     * block_rtol -> 0, at any grid size (inner restart length 60).  The blocks solved are shifted by
      * block_alpha (Eq. 2.8; 0 = the unshifted blocks of Eq. 3.5), while the
      * multigrid cycle keeps shift_alpha.  2-D, rhs_block = 1 only. */
     double block_rtol;
@@ -136,7 +136,7 @@ typedef struct {
  * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels as in Sec. 4.4.3,
  * Table 4; 1.0 for deeper hierarchies, found by the same kind of search),
  * bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1, BAH_KRYLOV_FP64,
- * one multigrid cycle per block (block_rtol 0; block_maxit 500, block_alpha 0). */
+ * one multigrid cycle per block (block_rtol 0; block_maxit 2000, block_alpha 0). */
 void bah_default_opts(bah_opts* opts);
 
 /* Build a solver for one grid, medium and frequency.  Copies the host medium

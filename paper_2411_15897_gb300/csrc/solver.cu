@@ -90,6 +90,7 @@ struct Ctx {
 
     // Gram-Schmidt flag and per-step graphs
     int* gsflag = nullptr;
+    unsigned* gscount = nullptr;         // last-CTA counters of the fused Gram-Schmidt kernels (2 per right-hand side)
     struct IterGraph {
         cudaGraphExec_t exec = nullptr;
         unsigned mask = ~0u;
@@ -103,7 +104,7 @@ struct Ctx {
     std::vector<cudaEvent_t> itev;
     bool use_graphs = true;
     bool staged = true;                  // shared-memory staging of Galerkin-level sweeps (BAH_STAGED=0: off)
-    bool fuse = true;                    // fused level visits above the cluster levels (BAH_FUSED_LEVELS=0: off)
+    bool fuse = false;                   // fused level visits above the cluster levels (BAH_FUSED_LEVELS=1: on)
     double dgks_eta2 = 0.5;              // second Gram-Schmidt pass when ||w'||^2 < eta2 ||w||^2
     int sm_l0 = 0;                       // first level of the shared-memory cluster multigrid (0: off)
     int sm_cs = 0, sm_rm = 2;            // its CTAs per cluster and stencil radius bound
@@ -114,7 +115,7 @@ struct Ctx {
     // by an inner FGMRES(mi) in FP64, preconditioned by its multigrid cycle
     bool exact = false;
     Fine5<double, double2> f5x{};       // FP64 block operators, diagonals shifted by block_alpha
-    int mi = 30;
+    int mi = 60;                        // inner restart length
     double2 *iV = nullptr, *iZ = nullptr, *iW = nullptr, *iR = nullptr, *iH = nullptr;
     double2 *ih1 = nullptr, *ih2 = nullptr, *ics = nullptr, *isn = nullptr, *igv = nullptr, *iy = nullptr;
     double2* ipart = nullptr;
@@ -789,6 +790,8 @@ static int alloc_krylov(Ctx& c, cudaStream_t st) {
     TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m * nbt));
     TRY(c.alloc_t(&c.h1v, so * nbt)); TRY(c.alloc_t(&c.h2v, so * nbt));
     TRY(c.alloc_t(&c.gsflag, nbt));
+    TRY(c.alloc_t(&c.gscount, 2 * nbt));
+    BAH_CUDA_TRY(cudaMemsetAsync(c.gscount, 0, 2 * nbt * sizeof(unsigned), st));
     TRY(c.alloc_t(&c.cs, so * nbt)); TRY(c.alloc_t(&c.sn, so * nbt)); TRY(c.alloc_t(&c.g, so * nbt));
     TRY(c.alloc_t(&c.y, so * nbt));
     TRY(c.alloc_t(&c.partial, so * RED_CTAS * nbt));
@@ -1013,7 +1016,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
         c.use_graphs = false;             // the block solves read their status on the host
     }
     if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
-    if (const char* e = getenv("BAH_FUSED_LEVELS")) c.fuse = (e[0] != '0');
+    if (const char* e = getenv("BAH_FUSED_LEVELS")) c.fuse = (e[0] == '1');
     if (const char* e = getenv("BAH_DGKS_ETA2")) c.dgks_eta2 = atof(e);
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
@@ -1148,6 +1151,35 @@ static void iter_body(Ctx& c, int j, cudaStream_t st) {
     else precond_any(c, c.V + (size_t)j * n, ks.sv, zj, ks.sz, bt, st);
     op_apply_z(c, zj, ks.sz, c.W, n, bt, st);
     const double k1 = j + 1;
+    if (!c.kdf) {
+        // FP64 basis: Gram-Schmidt with selective reorthogonalisation and the
+        // Givens update in four launches; the second pass's bytes count as zero
+        // (it runs only where the DGKS flag is set)
+        {
+            Prof pr(c, BAH_K_DOT, st, nb * (k1 + 1) * n * 16.0);
+            launch_gs_dot(1, c.V, j + 1, c.W, n, c.partial, c.h1v, c.gsflag, c.gscount, nb, ks, st);
+        }
+        {
+            Prof pr(c, BAH_K_AXPY, st, nb * (k1 + 2) * n * 16.0);
+            launch_gs_axpy(1, c.V, j + 1, c.h1v, c.W, n, c.dpart, c.gsflag, c.nrm, c.dgks_eta2, c.gscount, c.Hm,
+                           m + 1, j, c.h1v, c.h2v, c.cs, c.sn, c.g, c.status, nb, ks, st);
+        }
+        {
+            Prof pr(c, BAH_K_DOT, st, 0.0);
+            launch_gs_dot(2, c.V, j + 1, c.W, n, c.partial, c.h2v, c.gsflag, c.gscount, nb, ks, st);
+        }
+        {
+            Prof pr(c, BAH_K_AXPY, st, 0.0);
+            launch_gs_axpy(2, c.V, j + 1, c.h2v, c.W, n, c.dpart, c.gsflag, c.nrm, c.dgks_eta2, c.gscount, c.Hm,
+                           m + 1, j, c.h1v, c.h2v, c.cs, c.sn, c.g, c.status, nb, ks, st);
+        }
+        {
+            Prof pr(c, BAH_K_SMALL, st, nb * n * 32.0, 1);
+            launch_scale_copy(c.W, c.nrm, 2, c.V + (size_t)(j + 1) * n, n, n, ks.sv, nb, ks, st);
+        }
+        cudaMemcpyAsync(status_slot(c, j), c.status, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st);
+        return;
+    }
     {
         Prof pr(c, BAH_K_DOT, st, nb * (k1 + 1) * n * 16.0, 2);
         if (c.kdf) launch_dot_norm_df(Vd, j + 1, Wd, n, c.partial, c.h1v, nullptr, nb, ks, st);
@@ -1404,7 +1436,7 @@ void bah_default_opts(bah_opts* o) {
     o->rhs_block = 1;
     o->krylov_arith = BAH_KRYLOV_FP64;
     o->block_rtol = 0.0;
-    o->block_maxit = 500;
+    o->block_maxit = 2000;
     o->block_alpha = 0.0;
 }
 

