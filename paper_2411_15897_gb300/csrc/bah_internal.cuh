@@ -375,7 +375,8 @@ void launch_distrib3(const Op3& op, const double2* r, V* tp, cudaStream_t st);
 template <class V>
 void launch_urhs3(const Op3& op, const double2* r, const V* ep, V* const* su, cudaStream_t st);
 template <class V>
-void launch_jacobi3(int type, const int* n, int ns, const V* S, const V* b, const V* xin, V* xout, double w, int zero,
+// S: stencil entries, FP64 complex (V = double2) or bfloat16 complex (V = float2)
+void launch_jacobi3(int type, const int* n, int ns, const void* S, const V* b, const V* xin, V* xout, double w, int zero,
                     int res, cudaStream_t st);
 template <class V>
 void launch_restrict3(int type, const int* nf, const V* r, V* bc, cudaStream_t st);

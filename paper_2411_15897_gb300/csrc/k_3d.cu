@@ -14,6 +14,8 @@
 // against the grid before it loads it.
 #include "bah_internal.cuh"
 
+#include <type_traits>
+
 namespace bah {
 
 __host__ __device__ __forceinline__ bool valid3(int type, const int* c) { return type >= 3 || c[type] >= 1; }
@@ -304,8 +306,9 @@ template void launch_urhs3<float2>(const Op3&, const double2*, const float2*, fl
 // ---------------------------------------------------------------------------
 // one damped Jacobi sweep x_out = x_in + w D^{-1} (b - A x_in) (zero: x_in = 0),
 // or the residual x_out = b - A x_in (res)
-template <class V, int NS>
-__global__ void __launch_bounds__(256) k_jacobi3(int type, int n1, int n2, int n3, const V* __restrict__ S,
+// (stencil entries stored as SC: FP64 complex, or bfloat16 complex in mixed mode)
+template <class V, class SC, int NS>
+__global__ void __launch_bounds__(256) k_jacobi3(int type, int n1, int n2, int n3, const SC* __restrict__ S,
                                                  const V* __restrict__ b, const V* xin, V* xout,
                                                  typename VecTraits<V>::R w, int zero, int res) {
     const int np = n1 * n2 * n3;
@@ -329,27 +332,29 @@ __global__ void __launch_bounds__(256) k_jacobi3(int type, int n1, int n2, int n
                 q += o[a] * st[a];
             }
             if (!in) continue;
-            acc = csub(acc, cmul(S[(size_t)s * np + p], xin[q]));
+            acc = csub(acc, cmul(ldc(S[(size_t)s * np + p]), xin[q]));
         }
     }
     if (res) { xout[p] = acc; return; }
-    const V upd = cscale(cdiv(acc, S[(size_t)scentre<NS>() * np + p]), w);
+    const V upd = cscale(cdiv(acc, ldc(S[(size_t)scentre<NS>() * np + p])), w);
     xout[p] = zero ? upd : cadd(xin[p], upd);
 }
 
 template <class V>
-void launch_jacobi3(int type, const int* n, int ns, const V* S, const V* b, const V* xin, V* xout, double w, int zero,
+void launch_jacobi3(int type, const int* n, int ns, const void* S, const V* b, const V* xin, V* xout, double w, int zero,
                     int res, cudaStream_t st) {
     const int np = n[0] * n[1] * n[2];
     using R = typename VecTraits<V>::R;
+    using SC = typename std::conditional<std::is_same<V, double2>::value, double2, __nv_bfloat162>::type;
+    const SC* s = (const SC*)S;
     if (ns == 7)
-        k_jacobi3<V, 7><<<(np + 255) / 256, 256, 0, st>>>(type, n[0], n[1], n[2], S, b, xin, xout, (R)w, zero, res);
+        k_jacobi3<V, SC, 7><<<(np + 255) / 256, 256, 0, st>>>(type, n[0], n[1], n[2], s, b, xin, xout, (R)w, zero, res);
     else
-        k_jacobi3<V, 27><<<(np + 255) / 256, 256, 0, st>>>(type, n[0], n[1], n[2], S, b, xin, xout, (R)w, zero, res);
+        k_jacobi3<V, SC, 27><<<(np + 255) / 256, 256, 0, st>>>(type, n[0], n[1], n[2], s, b, xin, xout, (R)w, zero, res);
 }
-template void launch_jacobi3<double2>(int, const int*, int, const double2*, const double2*, const double2*, double2*,
+template void launch_jacobi3<double2>(int, const int*, int, const void*, const double2*, const double2*, double2*,
                                       double, int, int, cudaStream_t);
-template void launch_jacobi3<float2>(int, const int*, int, const float2*, const float2*, const float2*, float2*, double,
+template void launch_jacobi3<float2>(int, const int*, int, const void*, const float2*, const float2*, float2*, double,
                                      int, int, cudaStream_t);
 
 // 1-D transfer weights.  Restriction (Eq. 4.1 / 4.4, mixed intergrid): along

@@ -106,6 +106,7 @@ struct Ctx {
     bool staged = true;                  // shared-memory staging of Galerkin-level sweeps (BAH_STAGED=0: off)
     bool fuse = false;                   // fused level visits above the cluster levels (BAH_FUSED_LEVELS=1: on)
     double dgks_eta2 = 0.5;              // second Gram-Schmidt pass when ||w'||^2 < eta2 ||w||^2
+    bool gs_fused = true;                // FP64 Gram-Schmidt step in four launches (BAH_GS_FUSED=0: nine)
     int sm_l0 = 0;                       // first level of the shared-memory cluster multigrid (0: off)
     int sm_cs = 0, sm_rm = 2;            // its CTAs per cluster and stencil radius bound
     size_t sm_bytes = 0;                 // its dynamic shared memory per CTA
@@ -133,7 +134,7 @@ struct Ctx {
     Op3 op3{};
     std::vector<std::array<int, 3>> d3;            // level grids
     std::vector<std::array<double2*, 4>> s3;       // FP64 stencils (level 0: 7-point, coarser: 27-point)
-    std::vector<std::array<void*, 4>> s3s;         // the same in the cycle's vector type (levels below the coarsest)
+    std::vector<std::array<void*, 4>> s3s;         // the same in storage precision, bf16 in mixed mode (levels below the coarsest)
     std::vector<std::array<void*, 4>> v3B, v3X, v3T;
     double2* inv3[4] = {nullptr, nullptr, nullptr, nullptr};
 
@@ -530,8 +531,9 @@ struct MG3 {
     static void sweep(Ctx& c, int l, int q, const V* b, const V* xin, V* xout, int zero, int res, cudaStream_t st) {
         const int ns = l == 0 ? 7 : 27;
         const double vb = sizeof(V);
-        Prof pr(c, res ? BAH_K_RESIDUAL : BAH_K_JACOBI, st, (double)pts(c, l) * (ns * vb + (zero ? 2.0 : 3.0) * vb));
-        launch_jacobi3<V>(q, c.d3[l].data(), ns, (const V*)c.s3s[l][q], b, xin, xout, jw(c, l), zero, res, st);
+        const double sb = MODE == BAH_MIXED ? 4.0 : 16.0;          // bytes per stored stencil entry
+        Prof pr(c, res ? BAH_K_RESIDUAL : BAH_K_JACOBI, st, (double)pts(c, l) * (ns * sb + (zero ? 2.0 : 3.0) * vb));
+        launch_jacobi3<V>(q, c.d3[l].data(), ns, c.s3s[l][q], b, xin, xout, jw(c, l), zero, res, st);
     }
     // x = approximately A_q^{-1} b_q on level l (b_q in v3B[l][q]); zero: zero initial guess, else start from x
     static void cycle(Ctx& c, int l, int q, V* x, bool zero, cudaStream_t st) {
@@ -1018,6 +1020,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
     if (const char* e = getenv("BAH_FUSED_LEVELS")) c.fuse = (e[0] == '1');
     if (const char* e = getenv("BAH_DGKS_ETA2")) c.dgks_eta2 = atof(e);
+    if (const char* e = getenv("BAH_GS_FUSED")) c.gs_fused = (e[0] != '0');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
     return BAH_OK;
@@ -1065,8 +1068,9 @@ static int build3(Ctx& c, const bah_medium* med, cudaStream_t st) {
         for (int q = 0; q < 4; ++q) {
             const size_t cnt = (l == 0 ? 7 : 27) * pts(l);
             if (c.mode == BAH_MIXED) {
-                TRY(c.alloc(&c.s3s[l][q], cnt * sizeof(float2)));
-                launch_convert<double2, float2>(c.s3[l][q], (float2*)c.s3s[l][q], cnt, st);
+                // the mixed cycle's stencils in bfloat16 (entries rounded once from FP64)
+                TRY(c.alloc(&c.s3s[l][q], cnt * sizeof(__nv_bfloat162)));
+                launch_round_cplx(c.s3[l][q], c.s3s[l][q], cnt, BAH_MIXED, st);
             } else {
                 c.s3s[l][q] = c.s3[l][q];
             }
@@ -1151,7 +1155,7 @@ static void iter_body(Ctx& c, int j, cudaStream_t st) {
     else precond_any(c, c.V + (size_t)j * n, ks.sv, zj, ks.sz, bt, st);
     op_apply_z(c, zj, ks.sz, c.W, n, bt, st);
     const double k1 = j + 1;
-    if (!c.kdf) {
+    if (!c.kdf && c.gs_fused) {
         // FP64 basis: Gram-Schmidt with selective reorthogonalisation and the
         // Givens update in four launches; the second pass's bytes count as zero
         // (it runs only where the DGKS flag is set)

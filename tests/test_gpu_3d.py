@@ -9,10 +9,12 @@ Tolerances (relative 2-norm errors):
   * FP64-mode cycles and preconditioner: 1e-10 (the same arithmetic in another
     summation order, amplified at most by the coarsest inverse's condition
     number, a few hundred here);
-  * mixed-mode cycles and preconditioner: 1e-3.  In 3-D the mixed mode keeps
-    its stencils in FP32 while the oracle's stay FP64: rounding a coefficient
-    to FP32 (unit roundoff 6e-8) moves the cycle's output by at most about
-    cond(coarsest) * 6e-8 per dependent sweep, 1e3 * 6e-8 * 20 ~ 1e-3;
+  * mixed-mode cycles and preconditioner: 2e-4, against the oracle's
+    mixed-precision preconditioner, which rounds every level's stencil below
+    the coarsest to bfloat16 as the GPU stores it; the GPU then computes in
+    FP32 (unit roundoff 6e-8) through about 20 dependent sweeps and the
+    coarsest solve, whose condition number (<= ~1e3) amplifies the rounding of
+    its right-hand side, as in 2-D;
   * solves: the true relative residual ||b - H x|| / ||b|| recomputed with the
     oracle's assembled H must be <= 1e-6 (the stopping rule of Sec. 4), and
     FP64-mode iterates after a fixed number of FGMRES steps equal the oracle's
@@ -42,7 +44,7 @@ CYCLES = {
 W22 = CYCLES["W22"][0]
 C5_ALPHA = 0.4
 PREC = {"fp64": bah.BAH_FP64, "mixed": bah.BAH_MIXED}
-TOL = {"fp64": 1e-10, "mixed": 1e-3}
+TOL = {"fp64": 1e-10, "mixed": 2e-4}
 
 
 def rel(a, b):
@@ -125,7 +127,7 @@ def test_3d_block_cycle_matches_oracle(prec, cyc):
     levels = 3
     alpha = precond.default_alpha(levels)
     s = solver(p, prec, levels=levels, shift_alpha=alpha, **CYCLES[cyc][0])
-    pc = precond.multigrid(S, levels, alpha, intergrid="mixed", **CYCLES[cyc][1])
+    pc = precond.multigrid(S, levels, alpha, intergrid="mixed", precision=prec, **CYCLES[cyc][1])
     for q in range(4):
         v = block_vector(p.n, q, 200 + q)
         x = to_host(s.block_cycle(q, to_dev(v)))
@@ -146,7 +148,7 @@ def test_3d_preconditioner_matches_oracle(prec, nu):
     count."""
     p, S = small()
     s = solver(p, prec, nu_pre=nu[0], nu_post=nu[1])
-    pc = precond.multigrid(S, s.levels, s.alpha, intergrid="mixed", nu_pre=nu[0], nu_post=nu[1])
+    pc = precond.multigrid(S, s.levels, s.alpha, intergrid="mixed", nu_pre=nu[0], nu_post=nu[1], precision=prec)
     r = W.random_vector(p.n, 31)
     z = to_host(s.apply_preconditioner(to_dev(r)))
     assert rel(W.padded_to_compact(z, p.n), pc.apply(W.padded_to_compact(r, p.n))) <= TOL[prec]
