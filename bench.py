@@ -51,24 +51,26 @@ WORKLOADS = {
           "layer, centre point source, FGMRES(20) to rel-res 1e-6",
     "c2": "2D 512x512 layered medium (6 layers, Vp U[1.5,4.5], nu U[0.25,0.45], rho=0.31 Vp^0.25), "
           "10 points per shear wavelength, 20-cell absorbing layer, one top-centre point source, "
-          "FGMRES(20) to rel-res 1e-6",
+          "FGMRES to rel-res 1e-6",
     "c3": "2D 1024x1024 smooth random medium (log Vp Gaussian random field, correlation 32 cells, std 0.2, mean "
           "log 3; nu in [0.3,0.49]), 10 points per shear wavelength, 20-cell absorbing layer, top-centre source, "
-          "FGMRES(20) to rel-res 1e-6",
+          "FGMRES to rel-res 1e-6",
     "c4": "2D 1024x512 layered medium (6 layers, seed 5), 64 point sources along row 20 solved as one batch, "
-          "FGMRES(20) to rel-res 1e-6 per source",
+          "FGMRES to rel-res 1e-6 per source",
     "c5": "3D 128x128x128 smooth random medium (log Vp Gaussian random field, correlation 16 cells, std 0.2, mean "
           "log 3; nu in [0.3,0.49]), 8 points per shear wavelength, 10-cell absorbing layer, top-face point source, "
-          "FGMRES(20) to rel-res 1e-6",
+          "FGMRES to rel-res 1e-6",
 }
 # per-workload cycle settings where they differ from the 2-D benchmark's: the 3-D
 # workload runs the paper's 3-D multigrid (Sec. 4.5: mixed intergrid, W(2,2),
 # Jacobi 0.8, 0.8, 0.2) on 5 levels (coarsest 8^3) with the FP64 Krylov basis
 PRESETS = {
-    "2d": dict(levels=0, alpha=0.8, cycle="V", nu="1,3", jacobi="0.8,0.8,0.3", intergrid="bilinear", krylov="fp64"),
+    "2d": dict(levels=0, alpha=0.8, cycle="V", nu="1,3", jacobi="0.8,0.8,0.3", intergrid="bilinear", krylov="fp64",
+               restart=10),
     # many sources: the library's own cycle, V(1,2) with the shift by level count (1.0 at 7 levels)
     "c4": dict(alpha=-1.0, nu="1,2"),
-    "c5": dict(levels=5, alpha=0.4, cycle="W", nu="2,2", jacobi="0.8,0.8,0.2", intergrid="mixed", krylov="fp64"),
+    "c5": dict(levels=5, alpha=0.4, cycle="W", nu="2,2", jacobi="0.8,0.8,0.2", intergrid="mixed", krylov="fp64",
+               restart=20),
 }
 WORKLOAD = WORKLOADS["c2"]
 L2_FLUSH_BYTES = 512 << 20
@@ -76,7 +78,7 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA/clk/SM at the 2070 MHz max
 KERNEL_NAMES = {0: "k_elastic_apply", 1: "k_distributor", 2: "k_u_rhs", 3: "k_jacobi", 4: "k_residual",
                 5: "k_restrict", 6: "k_prolong_add", 7: "k_coarse_apply", 8: "k_dot_norm_partial",
                 9: "k_axpy_norm", 10: "k_norm2_partial", 11: "k_update_x", 12: "small kernels",
-                13: "k_level_down", 14: "k_cluster_mg", 15: "k_level_up"}
+                14: "k_cluster_mg"}
 KERNEL_NAMES_3D = {0: "k_apply3", 1: "k_distrib3", 2: "k_urhs3", 3: "k_jacobi3", 4: "k_jacobi3 (residual)",
                    5: "k_restrict3", 6: "k_prolong3", 7: "k_coarse_apply", 8: "k_dot_norm_partial",
                    9: "k_axpy_norm", 10: "k_norm2_partial", 11: "k_update_x", 12: "small kernels"}
@@ -99,11 +101,13 @@ def parse():
     ap.add_argument("--profile-json", default="", help="write the per-kernel-class profile here")
     ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--max-coarse", type=int, default=256)
-    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--krylov", default=None, choices=["fp64", "df"])
     ap.add_argument("--rhs-block", type=int, default=0,
                     help="right-hand sides per batch (default: all sources; -1: chosen by the autotuner)")
     ap.add_argument("--gradient", action="store_true", help="also time the adjoint gradient of a receiver misfit")
+    ap.add_argument("--tune-cycle", action="store_true",
+                    help="choose the cycle, shift and restart by timing complete solves first (autotune.tune_cycle)")
     ap.add_argument("--maxit", type=int, default=20000)
     # the benchmark's tuned cycle: V(1,3) with alpha 0.8 (searched at a resolution of 0.1 on this
     # workload, as the paper searches its shifts); --alpha -1 --nu 1,2 gives the library defaults
@@ -204,7 +208,7 @@ def run_reference(args):
     alpha = args.alpha if args.alpha >= 0 else precond.default_alpha(levels)
     nu = tuple(int(v) for v in args.nu.split(","))
     same = (bool(counts) and counts.get("levels") == levels and abs(counts.get("alpha", -1.0) - alpha) < 1e-12
-            and tuple(counts.get("nu", (1, 2))) == nu)
+            and tuple(counts.get("nu", (1, 2))) == nu and counts.get("restart", 20) == args.restart)
     its = counts["iters"] if same else None
     per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=args.warmup + args.steps,
                                nu=nu, cycle=args.cycle, weights=tuple(float(v) for v in args.jacobi.split(",")),
@@ -316,6 +320,21 @@ def run_bah(args):
                 nu_pre=int(args.nu.split(",")[0]), nu_post=int(args.nu.split(",")[1]),
                 jacobi_w=tuple(float(v) for v in args.jacobi.split(",")),
                 intergrid=bah.BAH_INTERGRID_MIXED if args.intergrid == "mixed" else bah.BAH_INTERGRID_BILINEAR)
+    tuned_cycle = None
+    if args.tune_cycle:
+        # cycle, sweeps, shift and restart by timing complete solves of a sample of the
+        # sources (autotune.py), before the timed context; the search grid is smaller
+        # for many-source workloads, whose solves are long
+        from paper_2411_15897_gb300 import autotune
+        cands = (autotune.cycle_candidates() if nsrc_all == 1 else
+                 autotune.cycle_candidates(alphas=(0.8, 1.0), cycles=(("V", 1, 2), ("V", 1, 3)), restarts=(10, 20)))
+        tuned_cycle = autotune.tune_cycle(prob, opts, candidates=cands, sample=4)
+        st_ = tuned_cycle.settings
+        opts.update(st_)
+        args.cycle = "W" if st_["cycle"] == 1 else "V"
+        args.nu = f"{st_['nu_pre']},{st_['nu_post']}"
+        args.alpha = st_["shift_alpha"]
+        args.restart = st_["restart"]
     if args.rhs_block < 0:
         # batch size and launch variant by timing short solves (autotune.py), before the timed context
         from paper_2411_15897_gb300 import autotune
@@ -546,7 +565,7 @@ def run_bah(args):
         per, setup = oracle_sample(prob, levels, alpha, args.restart, args.cpu_iters, reps=1, nu=nu, cycle=args.cycle,
                                    weights=tuple(float(v) for v in args.jacobi.split(",")), intergrid=args.intergrid)
         same = (bool(counts) and counts.get("levels") == levels and abs(counts.get("alpha", -1.0) - alpha) < 1e-12
-                and tuple(counts.get("nu", (1, 2))) == nu)
+                and tuple(counts.get("nu", (1, 2))) == nu and counts.get("restart", 20) == args.restart)
         its = counts["iters"] if same else statistics.median(iters)
         src = "oracle's own count" if same else "the GPU run's count"
         cpu = {"value": 1.0 / (its * per[0]), "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -566,6 +585,7 @@ def run_bah(args):
         "data": "synthetic",
         "config": workload_config(args, prob, levels, solver.alpha, world),
         "run": {"sources_per_rank": nsrc, "rhs_block": rhs_block, "autotune": tuned.as_dict() if tuned else None,
+                "autotune_cycle": tuned_cycle.as_dict() if tuned_cycle else None,
                 "context_bytes": context_bytes, "cluster_levels_from": solver.info["cluster_level"],
                 "iters": iters[-1], "relres_true": relres},
         "fp64": fp64,

@@ -300,9 +300,9 @@ int bah_level_stencil(const bah_ctx* ctx, int block, int level, double* out, int
 #define BAH_K_NORM     10   /* 2-norms (2 kernels) */
 #define BAH_K_UPDATE   11   /* x += Z y */
 #define BAH_K_SMALL    12   /* Givens update, triangular solve, scaling, copies, conversions */
-#define BAH_K_DOWN     13   /* fused level visit, down: zero-guess sweep + residual + restriction */
+/* class 13 is unused */
 #define BAH_K_CLUSTER  14   /* thread-block-cluster launch running the small levels of a cycle */
-#define BAH_K_UP       15   /* fused level visit, up: prolongation + correction + post-sweeps */
+/* class 15 is unused */
 #define BAH_NKCLASS    16
 
 typedef struct {

@@ -272,7 +272,7 @@ def bah_solve(ctx, b, x, nrhs=1, rtol=1e-6, stream=None):
 
 
 BAH_K_NAMES = ("operator", "distrib", "urhs", "jacobi", "residual", "restrict", "prolong", "coarse", "dot",
-               "axpy", "norm", "update", "small", "down", "cluster", "up")
+               "axpy", "norm", "update", "small", "unused13", "cluster", "unused15")
 
 
 class bah_profile(C.Structure):

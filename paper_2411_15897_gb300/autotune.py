@@ -18,6 +18,12 @@ shared-memory staging of the Galerkin-level sweeps (``BAH_STAGED``).
 Results are cached in a JSON file keyed by grid, sources, precision and
 device, so a job tunes once.  ``tune`` takes the timing function as an
 argument; the default one runs on the current CUDA device.
+
+``tune_cycle`` chooses the multigrid cycle, its sweep counts, the shift alpha
+(Eq. 2.8) and the FGMRES restart length.  These change the iteration count,
+not only the cost of an iteration, so each candidate is timed on complete
+solves to the tolerance (of a sample of the workload's sources), as the paper
+chooses its shift by a search at a resolution of 0.1 (Sec. 4.4.3).
 """
 from __future__ import annotations
 
@@ -131,4 +137,78 @@ def tune(problem, nsrc=None, opts=None, iters=20, variants=None, measure=time_ba
         cache[key] = best.as_dict()
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
+    return best
+
+
+# ---------------------------------------------------------------------------
+# cycle, shift and restart: timed on complete solves
+# ---------------------------------------------------------------------------
+@dataclass
+class CycleChoice:
+    settings: dict                    # solver options (cycle, nu_pre, nu_post, shift_alpha, restart)
+    seconds: float                    # per source, to the tolerance
+    iters: int
+    table: list = field(default_factory=list)   # (settings, seconds, iters) of every candidate
+
+    def as_dict(self):
+        return {"settings": self.settings, "seconds": self.seconds, "iters": self.iters, "table": self.table}
+
+
+def cycle_candidates(alphas=(0.6, 0.7, 0.8, 0.9, 1.0), cycles=(("V", 1, 2), ("V", 1, 3), ("W", 1, 2)),
+                     restarts=(10, 20)):
+    """The search grid: every cycle (type, nu_pre, nu_post) x shift x restart."""
+    out = []
+    for cyc, n1, n2 in cycles:
+        for a in alphas:
+            for m in restarts:
+                out.append({"cycle": 1 if cyc == "W" else 0, "nu_pre": n1, "nu_post": n2,
+                            "shift_alpha": float(a), "restart": int(m)})
+    return out
+
+
+def time_solve(problem, settings, opts, sources, rtol=1e-6, maxit=20000):
+    """(seconds per source, max iterations) of one solve of ``sources`` (indices
+    into problem.sources, one batch) to ``rtol`` with the given settings, on
+    the current CUDA device (one untimed solve first); inf if it does not
+    converge."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from . import BAH_OK, Solver, bah_solve
+
+    nb = len(sources)
+    s = Solver.from_problem(problem, **dict(opts, **settings, rhs_block=nb, maxit=maxit))
+    b = torch.from_numpy(np.stack([W.point_source(problem, problem.sources[q]) for q in sources])).cuda()
+    x = torch.zeros_like(b)
+    st, stats = bah_solve(s.ctx, b, x, nb, rtol)
+    if st != BAH_OK:
+        s.close()
+        return float("inf"), max(q["iters"] for q in stats)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    st, stats = bah_solve(s.ctx, b, x, nb, rtol)
+    e1.record(stream)
+    e1.synchronize()
+    s.close()
+    return e0.elapsed_time(e1) * 1e-3 / nb, max(q["iters"] for q in stats)
+
+
+def tune_cycle(problem, opts=None, candidates=None, sample=4, measure=time_solve) -> CycleChoice:
+    """Fastest settings per source to the tolerance over ``candidates``
+    (default: cycle_candidates()), timed on up to ``sample`` of the problem's
+    sources spread over its source list, solved as one batch."""
+    opts = {k: v for k, v in dict(opts or {}).items()
+            if k not in ("cycle", "nu_pre", "nu_post", "shift_alpha", "restart", "rhs_block", "maxit")}
+    nsrc = max(1, len(problem.sources))
+    k = min(sample, nsrc)
+    sources = sorted({int(round(i * (nsrc - 1) / max(k - 1, 1))) for i in range(k)})
+    table, best = [], None
+    for cand in (candidates or cycle_candidates()):
+        sec, its = measure(problem, cand, opts, sources)
+        table.append((cand, sec, its))
+        if best is None or sec < best.seconds:
+            best = CycleChoice(dict(cand), sec, its)
+    best.table = table
     return best

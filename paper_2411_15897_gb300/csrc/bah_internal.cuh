@@ -255,18 +255,6 @@ void launch_residual(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::C
 template <int MODE>
 void launch_restrict(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                      typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride = 0);
-// fused level visits (k_mg_fused.cu): zero-guess sweep + residual +
-// restriction (smoothed iterate into s.blk[z].xout, R r into coarse_b), and
-// prolongation with correction + nu sweeps (x_out = nu sweeps on x_in + P e;
-// x_out must not alias x_in).  Return nonzero if the launch could not be made.
-template <int MODE>
-int launch_level_down(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
-                      const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
-                      typename Prec<MODE>::V* const* coarse_b, int intergrid, cudaStream_t st, size_t coarse_stride);
-template <int MODE>
-int launch_level_up(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& s,
-                    const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC>* f5, double w,
-                    const typename Prec<MODE>::V* const* coarse_x, int nu, cudaStream_t st, size_t coarse_stride);
 template <int MODE>
 void launch_prolong_add(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>& fine,
                         const typename Prec<MODE>::V* const* coarse_x, cudaStream_t st, size_t coarse_stride = 0);
@@ -308,17 +296,6 @@ void launch_axpy_norm(const double2* V, int k, const double2* coef, double2* w, 
 // flag = 1 (second pass) when ||w'||^2 < eta2 ||w||^2 (DGKS criterion; eta2 = 1/2 classically)
 void launch_dgks_decide(const double* npart, const double2* h1norm, int k, int* flag, double* sc, int nrhs,
                         const KS& ks, cudaStream_t st, double eta2 = 0.5);
-// one Gram-Schmidt step with selective reorthogonalisation and the Givens
-// update in four launches (FP64 basis): gs_dot pass 1 (h1 and |w|^2), gs_axpy
-// pass 1 (w -= V h1, ||w'||, the DGKS flag), gs_dot pass 2 (h2, zero unless
-// flagged), gs_axpy pass 2 (w -= V h2 if flagged, ||w||, Givens update of
-// column j).  counters: 2 * nrhs unsigned, zero at entry and left zero.
-void launch_gs_dot(int pass, const double2* V, int k, const double2* w, size_t n, double2* partial, double2* h,
-                   const int* flag, unsigned* counters, int nrhs, const KS& ks, cudaStream_t st);
-void launch_gs_axpy(int pass, const double2* V, int k, const double2* coef, double2* w, size_t n, double* npart,
-                    int* flag, double* sc, double eta2, unsigned* counters, double2* Hm, int ldh, int j,
-                    const double2* h1, const double2* h2, double2* cs, double2* sn, double2* g, double* status,
-                    int nrhs, const KS& ks, cudaStream_t st);
 void launch_pass2_norm(const double* npart, const int* flag, double* sc, int nrhs, const KS& ks, cudaStream_t st);
 void launch_norm2(const double2* w, size_t n, double* partial, double* sc, int slot, int nrhs, const KS& ks,
                   cudaStream_t st);

@@ -326,6 +326,14 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
             unsigned x = L.off_x, t = L.off_t;
             int s0 = 0;
             if (!warm[k]) {
+                // with a zero initial guess, start in the buffer from which the visit's
+                // buffer swaps (the pre-sweeps after the first, and the post-sweeps)
+                // end in off_x, where the parent level and the final store read the
+                // result: no copy phase
+                if (((a.nu_pre >= 1 ? a.nu_pre - 1 : 0) + a.nu_post) & 1) {
+                    x = L.off_t;
+                    t = L.off_x;
+                }
                 if (a.nu_pre >= 1) {
                     jacobi(k, 0, x, true);
                     s0 = 1;

@@ -221,242 +221,6 @@ void launch_pass2_norm(const double* npart, const int* flag, double* sc, int nrh
 }
 
 // ---------------------------------------------------------------------------
-// One Gram-Schmidt step (FP64 basis) in four launches instead of nine.  Each
-// kernel ends with a "last CTA done" reduction: every CTA writes its partial
-// sums, fences, and counts itself in on a per-right-hand-side counter; the CTA
-// that arrives last sums all partials in a fixed order (so the result does
-// not depend on which CTA that is) and resets the counter.
-//   gs_dot   (pass p):  h_p = V^H w and, in pass 1, |w|^2;
-//   gs_axpy  (pass 1):  w -= V h_1, ||w'||, the DGKS decision (flag);
-//   gs_axpy  (pass 2):  if flagged w -= V h_2 and ||w''||; then, in either case,
-//                       the Givens update of the Hessenberg column.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned total) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == total - 1u;
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
-
-// Hessenberg column j = h1 + h2 with subdiagonal sc[2]; the previous rotations,
-// the new one, and g (as k_arnoldi_givens); called by every thread of one CTA
-__device__ void givens_update(double2* Hm, int ldh, const double2* h1, const double2* h2, const double* sc, int j,
-                              double2* cs, double2* sn, double2* g, double* status) {
-    __shared__ double2 h[66];
-    __shared__ double2 ssn[65];
-    __shared__ double scs[65];
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        h[i] = cadd(h1[i], h2[i]);
-        if (i < j) { scs[i] = cs[i].x; ssn[i] = sn[i]; }
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    double2* Hcol = Hm + (size_t)j * ldh;
-    const double wn = sc[2];
-    h[j + 1] = make_double2(wn, 0.0);
-    bool bad = !isfinite(wn);
-    for (int i = 0; i <= j; ++i) bad |= !isfinite(h[i].x) || !isfinite(h[i].y);
-    for (int i = 0; i < j; ++i) {
-        const double c = scs[i];
-        const double2 s = ssn[i];
-        const double2 a = h[i], b = h[i + 1];
-        h[i] = cadd(cscale(a, c), cmul(s, b));
-        h[i + 1] = csub(cscale(b, c), cmul(cconj(s), a));
-    }
-    const double2 a = h[j], b = h[j + 1];
-    const double na2 = a.x * a.x + a.y * a.y, nb2 = b.x * b.x + b.y * b.y;
-    double c;
-    double2 s;
-    if (nb2 == 0.0) {
-        c = 1.0; s = make_double2(0.0, 0.0);
-    } else if (na2 == 0.0) {
-        c = 0.0; s = cscale(cconj(b), 1.0 / sqrt(nb2));
-    } else {
-        const double na = sqrt(na2), rr = sqrt(na2 + nb2);
-        c = na / rr;
-        s = cscale(cmul(a, cconj(b)), 1.0 / (na * rr));
-    }
-    cs[j] = make_double2(c, 0.0);
-    sn[j] = s;
-    h[j] = cadd(cscale(a, c), cmul(s, b));
-    h[j + 1] = make_double2(0.0, 0.0);
-    for (int i = 0; i <= j + 1; ++i) Hcol[i] = h[i];
-    const double2 gj = g[j];
-    g[j] = cscale(gj, c);
-    const double2 gn = cscale(cmul(cconj(s), gj), -1.0);
-    g[j + 1] = gn;
-    status[0] = sqrt(gn.x * gn.x + gn.y * gn.y);
-    status[1] = wn;
-    status[2] = bad ? 1.0 : 0.0;
-}
-
-// rows y0 .. y0+kDotG-1 of h = V^H w (row k = |w|^2 in pass 1), partials per CTA, then the last CTA's sums
-__global__ void __launch_bounds__(256) k_gs_dot(const double2* __restrict__ V, int k, const double2* __restrict__ w,
-                                                size_t n, double2* __restrict__ partial, double2* __restrict__ out,
-                                                const int* flag, unsigned* counter, KS ks) {
-    pdl_prologue();
-    const int r = blockIdx.z;
-    if (inactive(ks, r)) return;
-    out += r * ks.so;
-    const int rows = flag ? k : k + 1;              // pass 2 needs no norm row
-    if (flag && flag[r] == 0) {
-        if (blockIdx.x == 0 && blockIdx.y == 0)
-            for (int i = threadIdx.x; i < rows; i += blockDim.x) out[i] = make_double2(0.0, 0.0);
-        return;
-    }
-    V += r * ks.sv;
-    w += r * ks.sw;
-    partial += r * ks.sp;
-    const int y0 = blockIdx.y * kDotG;
-    const int ny = min(kDotG, rows - y0);
-    double2 acc[kDotG];
-#pragma unroll
-    for (int q = 0; q < kDotG; ++q) acc[q] = make_double2(0.0, 0.0);
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-        const double2 b = __ldg(w + e);
-        double2 a[kDotG];
-#pragma unroll
-        for (int q = 0; q < kDotG; ++q)
-            if (q < ny && y0 + q < k) a[q] = __ldg(V + (size_t)(y0 + q) * n + e);
-#pragma unroll
-        for (int q = 0; q < kDotG; ++q) {
-            if (q >= ny) break;
-            if (y0 + q < k) {
-                cmac_conj(acc[q], a[q], b);
-            } else {
-                acc[q].x = fma(b.x, b.x, acc[q].x);
-                acc[q].x = fma(b.y, b.y, acc[q].x);
-            }
-        }
-    }
-    __shared__ double sh[2 * kDotG][256];
-#pragma unroll
-    for (int q = 0; q < kDotG; ++q) {
-        sh[2 * q][threadIdx.x] = acc[q].x;
-        sh[2 * q + 1][threadIdx.x] = acc[q].y;
-    }
-    __syncthreads();
-    const int qv = threadIdx.x >> 4, sl = threadIdx.x & 15;
-    double s = 0.0;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) s += sh[qv][sl * 16 + u];
-    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const int G = gridDim.x;
-    if (sl == 0 && (qv >> 1) < ny) {
-        double* dst = reinterpret_cast<double*>(partial + (size_t)(y0 + (qv >> 1)) * G + blockIdx.x);
-        dst[qv & 1] = s;
-    }
-    if (!arrive_last(counter + r, gridDim.x * gridDim.y)) return;
-    // the last CTA: out[y] = sum over the CTAs' partials of row y, one warp per row
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int y = wp; y < rows; y += blockDim.x >> 5) {
-        double2 t = make_double2(0.0, 0.0);
-        for (int e = lane; e < G; e += 32) {
-            const double2 a = __ldcg(partial + (size_t)y * G + e);
-            t.x += a.x;
-            t.y += a.y;
-        }
-        t = warp_sum2(t);
-        if (lane == 0) out[y] = t;
-    }
-    if (threadIdx.x == 0) counter[r] = 0u;
-}
-
-// w -= V coef; per-CTA |w|^2; the last CTA: pass 1 -> ||w'|| and the DGKS flag,
-// pass 2 -> ||w''||, then (pass 2, flagged or not) the Givens update of column j
-struct GivensArgs {
-    double2* Hm;
-    int ldh, j;
-    const double2 *h1, *h2;
-    double2 *cs, *sn, *g;
-    double* status;
-};
-__global__ void __launch_bounds__(512) k_gs_axpy(const double2* __restrict__ V, int k, const double2* __restrict__ coef,
-                                                 double2* __restrict__ w, size_t n, double* __restrict__ npart,
-                                                 int pass, int* flag, double* sc, double eta2, unsigned* counter,
-                                                 GivensArgs ga, KS ks) {
-    pdl_prologue();
-    const int r = blockIdx.z;
-    if (inactive(ks, r)) return;
-    sc += r * 8;
-    if (pass == 2 && flag[r] == 0) {
-        // no second pass: the Givens update alone, by one CTA
-        if (blockIdx.x == 0)
-            givens_update(ga.Hm + r * ks.sh, ga.ldh, ga.h1 + r * ks.so, ga.h2 + r * ks.so, sc, ga.j, ga.cs + r * ks.so,
-                          ga.sn + r * ks.so, ga.g + r * ks.so, ga.status + r * 4);
-        return;
-    }
-    V += r * ks.sv;
-    w += r * ks.sw;
-    coef += r * ks.so;
-    npart += r * RED_CTAS;
-    __shared__ double2 c[64];
-    if (threadIdx.x < k) c[threadIdx.x] = coef[threadIdx.x];
-    __syncthreads();
-    double nn = 0.0;
-    constexpr int kU = 8;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        double2 acc = w[e];
-        int i = 0;
-        for (; i + kU <= k; i += kU) {
-            double2 v[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) v[u] = __ldg(V + (size_t)(i + u) * n + e);
-#pragma unroll
-            for (int u = 0; u < kU; ++u) cmsub(acc, c[i + u], v[u]);
-        }
-        for (; i < k; ++i) cmsub(acc, c[i], __ldg(V + (size_t)i * n + e));
-        w[e] = acc;
-        nn = fma(acc.x, acc.x, nn);
-        nn = fma(acc.y, acc.y, nn);
-    }
-    double2 rs = block_sum2(make_double2(nn, 0.0));
-    if (threadIdx.x == 0) npart[blockIdx.x] = rs.x;
-    if (!arrive_last(counter + r, gridDim.x)) return;
-    double t = 0.0;
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (wp == 0) {
-        for (int e = lane; e < (int)gridDim.x; e += 32) t += __ldcg(npart + e);
-        t = warp_sum2(make_double2(t, 0.0)).x;
-    }
-    if (threadIdx.x == 0) {
-        if (pass == 1) {
-            const double w0 = coef[k].x;                 // |w|^2 before pass 1 (row k of the pass-1 dots)
-            const int f = (t < eta2 * w0) ? 1 : 0;
-            flag[r] = f;
-            sc[3] += (double)f;
-        }
-        sc[2] = sqrt(t);
-        counter[r] = 0u;
-    }
-    if (pass == 2) {
-        __syncthreads();
-        givens_update(ga.Hm + r * ks.sh, ga.ldh, ga.h1 + r * ks.so, ga.h2 + r * ks.so, sc, ga.j, ga.cs + r * ks.so,
-                      ga.sn + r * ks.so, ga.g + r * ks.so, ga.status + r * 4);
-    }
-}
-
-void launch_gs_dot(int pass, const double2* V, int k, const double2* w, size_t n, double2* partial, double2* h,
-                   const int* flag, unsigned* counters, int nrhs, const KS& ks, cudaStream_t st) {
-    const int rows = pass == 1 ? k + 1 : k;
-    const dim3 g(RED_CTAS, (rows + kDotG - 1) / kDotG, nrhs);
-    launch_pdl(k_gs_dot, g, dim3(256), 0, st, V, k, w, n, partial, h, pass == 1 ? (const int*)nullptr : flag,
-               counters, ks);
-}
-void launch_gs_axpy(int pass, const double2* V, int k, const double2* coef, double2* w, size_t n, double* npart,
-                    int* flag, double* sc, double eta2, unsigned* counters, double2* Hm, int ldh, int j,
-                    const double2* h1, const double2* h2, double2* cs, double2* sn, double2* g, double* status,
-                    int nrhs, const KS& ks, cudaStream_t st) {
-    GivensArgs ga{Hm, ldh, j, h1, h2, cs, sn, g, status};
-    launch_pdl(k_gs_axpy, dim3(RED_CTAS, 1, nrhs), dim3(512), 0, st, V, k, coef, w, n, npart, pass, flag, sc, eta2,
-               counters + nrhs, ga, ks);
-}
-
-// ---------------------------------------------------------------------------
 // 2-norm of w per right-hand side: sc[r*8 + slot] = ||w_r||
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_norm2_partial(const double2* __restrict__ w, size_t n, double* partial, KS ks) {

@@ -90,7 +90,6 @@ struct Ctx {
 
     // Gram-Schmidt flag and per-step graphs
     int* gsflag = nullptr;
-    unsigned* gscount = nullptr;         // last-CTA counters of the fused Gram-Schmidt kernels (2 per right-hand side)
     struct IterGraph {
         cudaGraphExec_t exec = nullptr;
         unsigned mask = ~0u;
@@ -104,9 +103,7 @@ struct Ctx {
     std::vector<cudaEvent_t> itev;
     bool use_graphs = true;
     bool staged = true;                  // shared-memory staging of Galerkin-level sweeps (BAH_STAGED=0: off)
-    bool fuse = false;                   // fused level visits above the cluster levels (BAH_FUSED_LEVELS=1: on)
     double dgks_eta2 = 0.5;              // second Gram-Schmidt pass when ||w'||^2 < eta2 ||w||^2
-    bool gs_fused = true;                // FP64 Gram-Schmidt step in four launches (BAH_GS_FUSED=0: nine)
     int sm_l0 = 0;                       // first level of the shared-memory cluster multigrid (0: off)
     int sm_cs = 0, sm_rm = 2;            // its CTAs per cluster and stencil radius bound
     size_t sm_bytes = 0;                 // its dynamic shared memory per CTA
@@ -400,29 +397,6 @@ struct MG {
         V* cx[3];
         for (int z = 0; z < nb; ++z) { cb[z] = (V*)c.vB[l + 1][b0 + z]; cx[z] = (V*)c.vX[l + 1][b0 + z]; }
         const bool wcyc = c.o.cycle == BAH_CYCLE_W;
-        if (c.fuse && !x0 && c.o.nu_pre == 1 && c.o.nu_post >= 1 && c.o.nu_post <= 4) {
-            // two launches for the visit: the zero-guess sweep, the residual and
-            // the restriction (smoothed iterate into the spare buffer), then the
-            // prolongation with correction and the post-sweeps into out
-            {
-                Prof pr(c, BAH_K_DOWN, st, nr * nb * npl * vs * 2.25 + cb_);
-                launch_level_down<MODE>(set(c, l, b0, nb, nullptr, 0, oth, oth_s, bt), pf5, w, cb, c.o.intergrid, st,
-                                        nplc);
-            }
-            if (c.sm_l0 == l + 1) {
-                smem_levels(c, b0, nb, bt, st);
-                if (wcyc && l + 1 < c.L - 1) smem_levels(c, b0, nb, bt, st, true);
-            } else {
-                cycle(c, l + 1, b0, nb, cx, nplc, bt, st);
-                if (wcyc && l + 1 < c.L - 1) cycle(c, l + 1, b0, nb, cx, nplc, bt, st, true);
-            }
-            {
-                Prof pr(c, BAH_K_UP, st, nr * nb * npl * vs * 3.25 + cb_);
-                launch_level_up<MODE>(set(c, l, b0, nb, oth, oth_s, out, ostride, bt), pf5, w, cx, c.o.nu_post, st,
-                                      nplc);
-            }
-            return;
-        }
         {
             // With a zero initial guess the caller's buffer holds nothing yet: if the
             // sweeps below swap the two buffers an odd number of times, start in the
@@ -792,8 +766,6 @@ static int alloc_krylov(Ctx& c, cudaStream_t st) {
     TRY(c.alloc_t(&c.Hm, (size_t)(m + 1) * m * nbt));
     TRY(c.alloc_t(&c.h1v, so * nbt)); TRY(c.alloc_t(&c.h2v, so * nbt));
     TRY(c.alloc_t(&c.gsflag, nbt));
-    TRY(c.alloc_t(&c.gscount, 2 * nbt));
-    BAH_CUDA_TRY(cudaMemsetAsync(c.gscount, 0, 2 * nbt * sizeof(unsigned), st));
     TRY(c.alloc_t(&c.cs, so * nbt)); TRY(c.alloc_t(&c.sn, so * nbt)); TRY(c.alloc_t(&c.g, so * nbt));
     TRY(c.alloc_t(&c.y, so * nbt));
     TRY(c.alloc_t(&c.partial, so * RED_CTAS * nbt));
@@ -1018,9 +990,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
         c.use_graphs = false;             // the block solves read their status on the host
     }
     if (const char* e = getenv("BAH_STAGED")) c.staged = (e[0] != '0');
-    if (const char* e = getenv("BAH_FUSED_LEVELS")) c.fuse = (e[0] == '1');
     if (const char* e = getenv("BAH_DGKS_ETA2")) c.dgks_eta2 = atof(e);
-    if (const char* e = getenv("BAH_GS_FUSED")) c.gs_fused = (e[0] != '0');
     BAH_CUDA_TRY(cudaStreamSynchronize(st));
     // the raw medium is no longer needed
     return BAH_OK;
@@ -1155,35 +1125,6 @@ static void iter_body(Ctx& c, int j, cudaStream_t st) {
     else precond_any(c, c.V + (size_t)j * n, ks.sv, zj, ks.sz, bt, st);
     op_apply_z(c, zj, ks.sz, c.W, n, bt, st);
     const double k1 = j + 1;
-    if (!c.kdf && c.gs_fused) {
-        // FP64 basis: Gram-Schmidt with selective reorthogonalisation and the
-        // Givens update in four launches; the second pass's bytes count as zero
-        // (it runs only where the DGKS flag is set)
-        {
-            Prof pr(c, BAH_K_DOT, st, nb * (k1 + 1) * n * 16.0);
-            launch_gs_dot(1, c.V, j + 1, c.W, n, c.partial, c.h1v, c.gsflag, c.gscount, nb, ks, st);
-        }
-        {
-            Prof pr(c, BAH_K_AXPY, st, nb * (k1 + 2) * n * 16.0);
-            launch_gs_axpy(1, c.V, j + 1, c.h1v, c.W, n, c.dpart, c.gsflag, c.nrm, c.dgks_eta2, c.gscount, c.Hm,
-                           m + 1, j, c.h1v, c.h2v, c.cs, c.sn, c.g, c.status, nb, ks, st);
-        }
-        {
-            Prof pr(c, BAH_K_DOT, st, 0.0);
-            launch_gs_dot(2, c.V, j + 1, c.W, n, c.partial, c.h2v, c.gsflag, c.gscount, nb, ks, st);
-        }
-        {
-            Prof pr(c, BAH_K_AXPY, st, 0.0);
-            launch_gs_axpy(2, c.V, j + 1, c.h2v, c.W, n, c.dpart, c.gsflag, c.nrm, c.dgks_eta2, c.gscount, c.Hm,
-                           m + 1, j, c.h1v, c.h2v, c.cs, c.sn, c.g, c.status, nb, ks, st);
-        }
-        {
-            Prof pr(c, BAH_K_SMALL, st, nb * n * 32.0, 1);
-            launch_scale_copy(c.W, c.nrm, 2, c.V + (size_t)(j + 1) * n, n, n, ks.sv, nb, ks, st);
-        }
-        cudaMemcpyAsync(status_slot(c, j), c.status, 4 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st);
-        return;
-    }
     {
         Prof pr(c, BAH_K_DOT, st, nb * (k1 + 1) * n * 16.0, 2);
         if (c.kdf) launch_dot_norm_df(Vd, j + 1, Wd, n, c.partial, c.h1v, nullptr, nb, ks, st);

@@ -1,9 +1,9 @@
 """Write tests/golden/oracle_counts.json: the CPU oracle's FGMRES iteration
 count and true relative residual for the named workloads, with the solver
-options the benchmark uses (mixed-precision coefficient set, V(1,2), FGMRES(20),
-rel-res 1e-6).  Calls only oracle/ and workloads/.
+options the benchmark uses (mixed-precision coefficient set, V(nu1,nu2),
+FGMRES(m), rel-res 1e-6).  Calls only oracle/ and workloads/.
 
-    python tests/golden/make_oracle_counts.py c1 c2 [--levels L] [--alpha A] [--nu PRE,POST]
+    python tests/golden/make_oracle_counts.py c1 c2 [--levels L] [--alpha A] [--nu PRE,POST] [--restart M]
 """
 import json
 import os
@@ -39,7 +39,10 @@ def main():
     nu = (1, 2)
     if "--nu" in sys.argv:
         nu = tuple(int(v) for v in sys.argv[sys.argv.index("--nu") + 1].split(","))
-    names = [a for a in names if a not in (str(lv), str(al), ",".join(map(str, nu)))]
+    m = 20
+    if "--restart" in sys.argv:
+        m = int(sys.argv[sys.argv.index("--restart") + 1])
+    names = [a for a in names if a not in (str(lv), str(al), ",".join(map(str, nu)), str(m))]
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in names:
         p = W.config(name)
@@ -50,8 +53,8 @@ def main():
         H = S.H
         pc = precond.multigrid(S, L, alpha, precision="mixed", nu_pre=nu[0], nu_post=nu[1])
         b = W.padded_to_compact(W.point_source(p), p.n)
-        r = fgmres.fgmres(lambda v: H @ v, b, pc.apply, restart=20, rtol=1e-6, maxit=20000)
-        data[name] = {"levels": L, "alpha": alpha, "nu": list(nu), "restart": 20, "precision": "mixed", "iters": r.iters,
+        r = fgmres.fgmres(lambda v: H @ v, b, pc.apply, restart=m, rtol=1e-6, maxit=20000)
+        data[name] = {"levels": L, "alpha": alpha, "nu": list(nu), "restart": m, "precision": "mixed", "iters": r.iters,
                       "relres_true": r.relres_true, "converged": bool(r.converged),
                       "cpu_seconds": time.perf_counter() - t0}
         print(name, data[name], flush=True)

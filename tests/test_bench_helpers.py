@@ -29,16 +29,16 @@ def test_presets_keep_the_2d_benchmark_and_give_c5_the_3d_cycle(monkeypatch):
     intergrid, Jacobi 0.8/0.8/0.2) on 5 levels; explicit flags override a
     preset."""
     import bench
-    fields = ("levels", "alpha", "cycle", "nu", "jacobi", "intergrid", "krylov")
+    fields = ("levels", "alpha", "cycle", "nu", "jacobi", "intergrid", "krylov", "restart")
     monkeypatch.setattr("sys.argv", ["bench.py"])
     a = bench.parse()
-    assert tuple(getattr(a, f) for f in fields) == (0, 0.8, "V", "1,3", "0.8,0.8,0.3", "bilinear", "fp64")
+    assert tuple(getattr(a, f) for f in fields) == (0, 0.8, "V", "1,3", "0.8,0.8,0.3", "bilinear", "fp64", 10)
     monkeypatch.setattr("sys.argv", ["bench.py", "--config", "c4"])
     a = bench.parse()
-    assert tuple(getattr(a, f) for f in fields) == (0, -1.0, "V", "1,2", "0.8,0.8,0.3", "bilinear", "fp64")
+    assert tuple(getattr(a, f) for f in fields) == (0, -1.0, "V", "1,2", "0.8,0.8,0.3", "bilinear", "fp64", 10)
     monkeypatch.setattr("sys.argv", ["bench.py", "--config", "c5"])
     a = bench.parse()
-    assert tuple(getattr(a, f) for f in fields) == (5, 0.4, "W", "2,2", "0.8,0.8,0.2", "mixed", "fp64")
+    assert tuple(getattr(a, f) for f in fields) == (5, 0.4, "W", "2,2", "0.8,0.8,0.2", "mixed", "fp64", 20)
     monkeypatch.setattr("sys.argv", ["bench.py", "--config", "c5", "--alpha", "0.3", "--nu", "1,2"])
     a = bench.parse()
     assert (a.alpha, a.nu, a.cycle) == (0.3, "1,2", "W")

@@ -41,7 +41,8 @@ def bench_opts(config, **over):
              cycle=bah.BAH_CYCLE_W if pr["cycle"] == "W" else bah.BAH_CYCLE_V, nu_pre=nu[0], nu_post=nu[1],
              jacobi_w=tuple(float(v) for v in pr["jacobi"].split(",")),
              intergrid=bah.BAH_INTERGRID_MIXED if pr["intergrid"] == "mixed" else bah.BAH_INTERGRID_BILINEAR,
-             krylov_arith=bah.BAH_KRYLOV_DF if pr["krylov"] == "df" else bah.BAH_KRYLOV_FP64, maxit=20000)
+             krylov_arith=bah.BAH_KRYLOV_DF if pr["krylov"] == "df" else bah.BAH_KRYLOV_FP64, restart=pr["restart"],
+             maxit=20000)
     o.update(over)
     return o
 

@@ -471,62 +471,6 @@ def test_smem_cluster_multigrid_matches_separate_kernels(cycle, levels, monkeypa
         assert np.linalg.norm(bc - S.H @ W.padded_to_compact(xh[k], p.n)) / np.linalg.norm(bc) <= 1e-7
 
 
-@pytest.mark.parametrize("prec", [bah.BAH_FP64, bah.BAH_MIXED])
-@pytest.mark.parametrize("cycle", [bah.BAH_CYCLE_V, bah.BAH_CYCLE_W])
-@pytest.mark.parametrize("nu_post", [1, 2, 3, 4])
-@pytest.mark.parametrize("name", ["random_48x40", "layered_64x32"])
-def test_fused_level_visits_match_separate_kernels(prec, cycle, nu_post, name, systems, monkeypatch):
-    """A zero-guess level visit above the cluster levels runs as two fused
-    launches (sweep + residual + restriction; prolongation + nu sweeps with
-    halos recomputed in shared memory) with BAH_FUSED_LEVELS=1, and as
-    separate kernels by default.  Same per-point arithmetic: the preconditioner
-    agrees to rounding (tiles cut by the grid edge: 48x40 and 24x20 grids on
-    32x16 tiles), the fused classes are really taken, and both match the
-    oracle element by element."""
-    p, S = get(name, systems)
-    r = W.random_vector(p.n, 51)
-    out = {}
-    for mode in ("0", "1"):
-        monkeypatch.setenv("BAH_FUSED_LEVELS", mode)
-        s = bah.Solver.from_problem(p, precision=prec, levels=3, cycle=cycle, nu_post=nu_post)
-        bah.bah_profile_control(s.ctx, 0, True)
-        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
-        pr = bah.bah_profile_read(s.ctx)
-        assert (pr["classes"]["down"]["calls"] > 0) == (mode == "1")
-        assert (pr["classes"]["up"]["calls"] > 0) == (mode == "1")
-        s.close()
-    tol = 1e-12 if prec == bah.BAH_FP64 else 1e-6
-    assert rel(out["1"], out["0"]) <= tol, rel(out["1"], out["0"])
-    pc = precond.multigrid(S, 3, precond.default_alpha(3), precision="fp64" if prec == bah.BAH_FP64 else "mixed",
-                           cycle="W" if cycle == bah.BAH_CYCLE_W else "V", nu_post=nu_post)
-    ref = pc.apply(W.padded_to_compact(r, p.n))
-    zc = W.padded_to_compact(out["1"], p.n)
-    assert rel(zc, ref) <= (1e-10 if prec == bah.BAH_FP64 else 2e-4)
-    check_elementwise(zc, ref, p.n, 1e-9 if prec == bah.BAH_FP64 else 2e-3)
-
-
-def test_fused_level_visits_full_size_c2_fp64(monkeypatch):
-    """The benchmark's grid (512x512: 32x32 tiles on level 0, 32x16 below) in
-    FP64 mode, where every level above the coarsest runs fused: the
-    preconditioner equals the separate kernels' to 1e-12 and the oracle's to
-    1e-10."""
-    p = W.config("c2")
-    r = W.random_vector(p.n, 53)
-    out = {}
-    for mode in ("0", "1"):
-        monkeypatch.setenv("BAH_FUSED_LEVELS", mode)
-        s = bah.Solver.from_problem(p, precision=bah.BAH_FP64, nu_post=3)
-        out[mode] = to_host(s.apply_preconditioner(to_dev(r)))
-        levels = s.levels
-        s.close()
-    assert rel(out["1"], out["0"]) <= 1e-12, rel(out["1"], out["0"])
-    S = elastic.from_problem(p)
-    pc = precond.multigrid(S, levels, precond.default_alpha(levels), precision="fp64", nu_post=3)
-    zc, ref = W.padded_to_compact(out["1"], p.n), pc.apply(W.padded_to_compact(r, p.n))
-    assert rel(zc, ref) <= 1e-10
-    check_elementwise(zc, ref, p.n, 1e-9)
-
-
 @pytest.mark.parametrize("name", ["random_48x40", "layered_64x32"])
 def test_staged_level_kernels_match_plain(name, systems, monkeypatch):
     """Mixed mode stages each CTA's stencil coefficients and iterate rows in
