@@ -575,7 +575,7 @@ def run_bah(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "setup_s": setup_s, "higher_is_better": True, "scaling": "strong" if nsrc_all > 1 else "weak", "vs_baseline": None,
-        "dtype": (("mixed: f32 stencils, f32 multigrid, " if prob.dim == 3 else "mixed: bf16 coefficients, f32 multigrid, ")
+        "dtype": (("mixed: bf16 stencils, f32 multigrid, " if prob.dim == 3 else "mixed: bf16 coefficients, f32 multigrid, ")
                   + "f64 coarsest solve (f64 inverse applied in f64), "
                   + ("double-f32 (48-bit) Krylov basis and Gram-Schmidt" if args.krylov == "df"
                      else "f64 Krylov basis and Gram-Schmidt")

@@ -58,12 +58,11 @@ extern "C" {
                                       calls listed at bah_create) */
 
 /* precision of the preconditioner.  The coarsest-level inverse is computed in
- * FP64 in both modes and applied in the multigrid's precision; the outer
+ * FP64 and applied in FP64 arithmetic in both modes; the outer
  * FGMRES keeps its Hessenberg update, Givens rotations, true residual and
  * solution in FP64 in both modes (see krylov_arith for the basis) */
 #define BAH_FP64   0   /* multigrid in complex FP64 with FP64 coefficients */
-#define BAH_MIXED  1   /* multigrid in complex FP32, coefficients stored in bfloat16 (2-D) or
-                          FP32 stencils (3-D) */
+#define BAH_MIXED  1   /* multigrid in complex FP32, coefficients and stencils stored in bfloat16 */
 
 /* arithmetic of the Krylov basis (Gram-Schmidt dots and updates, and, in
  * BAH_MIXED mode, the operator w = H z and the update x += Z y on the FP32

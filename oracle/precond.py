@@ -89,9 +89,13 @@ def exact(sys: ElasticSystem, alpha=0.0, shift_sign=1.0) -> BlockAcoustic:
 
 
 def multigrid(sys: ElasticSystem, levels, alpha=None, *, weights=mg.DEFAULT_JACOBI, nu_pre=1, nu_post=2,
-              cycle="V", intergrid="bilinear", precision="fp64", shift_sign=1.0) -> BlockAcoustic:
+              cycle="V", intergrid="bilinear", precision="fp64", shift_sign=1.0, bf16_ap=None) -> BlockAcoustic:
     """Block-acoustic multigrid: one cycle of shifted-Laplacian multigrid per
-    block (Sec. 4.4.1), with ``levels`` levels (fine level included)."""
+    block (Sec. 4.4.1), with ``levels`` levels (fine level included).
+    ``precision='mixed'`` rounds the level operators below the coarsest to
+    bfloat16; ``bf16_ap`` says whether the distributor's A_p (Eq. 3.2) is
+    rounded too (default: as the level operators; the 3-D GPU path keeps its
+    distributor coefficients in FP64)."""
     if alpha is None:
         alpha = default_alpha(levels)
     d = sys.dim
@@ -103,7 +107,9 @@ def multigrid(sys: ElasticSystem, levels, alpha=None, *, weights=mg.DEFAULT_JACO
                                nu_post=nu_post, cycle=cycle, intergrid=intergrid, bf16=bf16)
         hiers.append(h)
         solvers.append(lambda b, h=h: mg.cycle(h, b))
-    Ap = round_matrix_bf16(sys.Ap) if bf16 else sys.Ap
+    if bf16_ap is None:
+        bf16_ap = bf16
+    Ap = round_matrix_bf16(sys.Ap) if bf16_ap else sys.Ap
     pc = BlockAcoustic(sys, Ap, sys.B, sys.Bt, solvers, sys.sizes, hiers)
     return pc
 

@@ -11,7 +11,8 @@ Tolerances (relative 2-norm errors):
     number, a few hundred here);
   * mixed-mode cycles and preconditioner: 2e-4, against the oracle's
     mixed-precision preconditioner, which rounds every level's stencil below
-    the coarsest to bfloat16 as the GPU stores it; the GPU then computes in
+    the coarsest to bfloat16 as the GPU stores it (the 3-D distributor keeps
+    FP64 coefficients on both sides); the GPU then computes in
     FP32 (unit roundoff 6e-8) through about 20 dependent sweeps and the
     coarsest solve, whose condition number (<= ~1e3) amplifies the rounding of
     its right-hand side, as in 2-D;
@@ -148,7 +149,8 @@ def test_3d_preconditioner_matches_oracle(prec, nu):
     count."""
     p, S = small()
     s = solver(p, prec, nu_pre=nu[0], nu_post=nu[1])
-    pc = precond.multigrid(S, s.levels, s.alpha, intergrid="mixed", nu_pre=nu[0], nu_post=nu[1], precision=prec)
+    pc = precond.multigrid(S, s.levels, s.alpha, intergrid="mixed", nu_pre=nu[0], nu_post=nu[1], precision=prec,
+                           bf16_ap=False)
     r = W.random_vector(p.n, 31)
     z = to_host(s.apply_preconditioner(to_dev(r)))
     assert rel(W.padded_to_compact(z, p.n), pc.apply(W.padded_to_compact(r, p.n))) <= TOL[prec]
