@@ -120,6 +120,14 @@ typedef struct {
     double block_rtol;
     int    block_maxit;      /* inner iterations per block solve (block_rtol > 0) */
     double block_alpha;
+    /* outer Krylov method for a batch of right-hand sides: 0 = independent FGMRES
+     * recurrences advanced in lockstep; 1 = block FGMRES, one Krylov space for
+     * the batch (block Arnoldi with two passes of block classical Gram-Schmidt
+     * and CholQR2, the block Hessenberg least squares by Householder
+     * reflections); needs 2-D, 2 <= rhs_block <= 16, BAH_KRYLOV_FP64 and
+     * nonzero right-hand sides.  The iteration count of a block solve is the
+     * same for all its right-hand sides. */
+    int    block_krylov;
 } bah_opts;
 
 typedef struct {
@@ -135,7 +143,8 @@ typedef struct {
  * level count (0.1 / 0.2 / 0.4 for 2 / 3 / 4 levels as in Sec. 4.4.3,
  * Table 4; 1.0 for deeper hierarchies, found by the same kind of search),
  * bilinear intergrid, FGMRES(20), maxit 5000, rhs_block 1, BAH_KRYLOV_FP64,
- * one multigrid cycle per block (block_rtol 0; block_maxit 2000, block_alpha 0). */
+ * one multigrid cycle per block (block_rtol 0; block_maxit 2000, block_alpha 0),
+ * lockstep batches (block_krylov 0). */
 void bah_default_opts(bah_opts* opts);
 
 /* Build a solver for one grid, medium and frequency.  Copies the host medium

@@ -59,7 +59,7 @@ class bah_opts(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("jacobi_w", C.c_double * 8), ("n_jacobi_w", C.c_int),
                 ("shift_alpha", C.c_double), ("intergrid", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
                 ("rhs_block", C.c_int), ("krylov_arith", C.c_int), ("block_rtol", C.c_double),
-                ("block_maxit", C.c_int), ("block_alpha", C.c_double)]
+                ("block_maxit", C.c_int), ("block_alpha", C.c_double), ("block_krylov", C.c_int)]
 
 
 class bah_info(C.Structure):

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string>
 #include <utility>
@@ -70,6 +71,15 @@ inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, 
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
+
+// NVTX range over a host scope (setup phases, solves, restart cycles, FGMRES
+// steps), visible in a timeline profiler; costs nothing when none is attached
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // precision traits: V = complex vector element, R = real arithmetic type,
@@ -319,6 +329,19 @@ void launch_axpy_norm_df(const float4* V, int k, const double2* coef, float4* w,
                          const int* flag, int nrhs, const KS& ks, cudaStream_t st);
 void launch_scale_copy_df(const void* w, bool from64, const double* sc, int slot, float4* v, size_t n, size_t sw,
                           size_t sv, int nrhs, const KS& ks, cudaStream_t st);
+
+// block FGMRES kernels (k_block.cu); s <= 16 columns; rows of A (and Z) for
+// block i, column a at A + a * sa + i * n
+void launch_block_dot(const double2* A, size_t sa, int k, int s, const double2* W, size_t n, double2* partial,
+                      double2* C, cudaStream_t st);
+void launch_block_update(const double2* A, size_t sa, int k, int s, const double2* C, double2* W, size_t n,
+                         int subtract, cudaStream_t st);
+void launch_block_scale(const double2* W, int s, const double2* T, double2* V, size_t sv, size_t n, cudaStream_t st);
+template <class Vz>
+void launch_block_xupdate(const Vz* Z, size_t sz, int k, int s, const double2* Y, double2* X, size_t n,
+                          cudaStream_t st);
+// allow the block update kernels the given dynamic shared memory
+void block_kernels_smem(size_t bytes);
 
 // adjoint gradient (k_grad.cu)
 void launch_conj(double2* v, size_t n, cudaStream_t st);

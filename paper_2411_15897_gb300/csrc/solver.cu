@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -125,6 +126,10 @@ struct Ctx {
     int block_failures = 0;
     int exact_status = BAH_OK;          // first failure of a block solve inside a preconditioner call
 
+    // block FGMRES workspace (block_krylov = 1)
+    double2 *bC = nullptr, *bT = nullptr, *bpart = nullptr;
+    double2* bhost = nullptr;           // pinned
+
     // three-dimensional grids (dim == 3): n1 x n2 x n3 cells
     int n3 = 1;
     double h3 = 0;
@@ -150,6 +155,7 @@ struct Ctx {
         if (hstatus) cudaFreeHost(hstatus);
         if (hint) cudaFreeHost(hint);
         if (histat) cudaFreeHost(histat);
+        if (bhost) cudaFreeHost(bhost);
     }
     int alloc(void** p, size_t bytes) {
         *p = nullptr;
@@ -664,6 +670,7 @@ static int block_solve(Ctx& c, int b, const double2* s, double2* e, cudaStream_t
 // s_u = r_u - B^T e_p, A_k e_k = s_k (Eq. 3.1-3.5)
 template <class RIN>
 static int precond_exact(Ctx& c, const RIN* r, double2* z, cudaStream_t st) {
+    NvtxRange nv("exact-block preconditioner");
     const size_t np = c.np;
     const double ihx = 1.0 / c.h1, ihz = 1.0 / c.h2;
     auto solve = [&](int b, const double2* s, double2* e) {
@@ -791,6 +798,7 @@ static int alloc_krylov(Ctx& c, cudaStream_t st) {
 // context construction
 // ---------------------------------------------------------------------------
 static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
+    NvtxRange nv("bah setup (2-D)");
     const int np = c.np;
     const size_t cs = c.mode == BAH_MIXED ? 2 : 8, ccs = c.mode == BAH_MIXED ? 4 : 16;
     // medium upload
@@ -897,6 +905,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
     BAH_CUDA_TRY(cudaGetLastError());
     // coarsest-level inverses
     {
+        NvtxRange nvi("coarsest inverses");
         const int nc = c.ln1[c.L - 1] * c.ln2[c.L - 1];
         void* work;
         int* flag;
@@ -957,6 +966,13 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
         }
     }
     TRY(alloc_krylov(c, st));
+    if (c.o.block_krylov) {
+        const size_t sq = (size_t)(c.m + 1) * c.nbatch * c.nbatch;
+        TRY(c.alloc_t(&c.bC, sq)); TRY(c.alloc_t(&c.bT, (size_t)c.nbatch * c.nbatch));
+        TRY(c.alloc_t(&c.bpart, sq * RED_CTAS));
+        BAH_CUDA_TRY(cudaMallocHost((void**)&c.bhost, sq * sizeof(double2)));
+        block_kernels_smem((size_t)(c.m + 1) * c.nbatch * c.nbatch * sizeof(double2));
+    }
     if (c.exact) {
         // the blocks solved exactly: the fine operators of Eq. 2.6 / 3.4 with their
         // diagonals shifted by block_alpha (a second medium preparation, of which
@@ -1001,6 +1017,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
 // the mixed intergrid, coarsest inverses, multigrid vectors, Krylov workspace
 // ---------------------------------------------------------------------------
 static int build3(Ctx& c, const bah_medium* med, cudaStream_t st) {
+    NvtxRange nv("bah setup (3-D)");
     const size_t np = c.np;
     double *lam, *mu, *rho, *gam, *cinv, *mue[3];
     double2 *mrt, *dg[3];
@@ -1188,6 +1205,7 @@ static int ensure_graph(Ctx& c, int j) {
 }
 
 static int launch_iter(Ctx& c, int j, cudaStream_t st) {
+    NvtxRange nv("fgmres step");
     if (c.use_graphs) {
         int s = ensure_graph(c, j);
         if (s != BAH_OK) {
@@ -1249,6 +1267,7 @@ static int fgmres_batch(Ctx& c, const double2* b, double2* x, int nr, double rto
     int total = 0;
     auto any = [&](const std::vector<int>& v) { for (int q : v) if (q) return true; return false; };
     while (any(act) && total < c.o.maxit) {
+        NvtxRange nvc("fgmres restart cycle");
         TRY(upload_ints(c, act, c.active, 0, st));
         // v_0 = r / beta, g = beta e_1
         {
@@ -1335,6 +1354,275 @@ static int fgmres_batch(Ctx& c, const double2* b, double2* x, int nr, double rto
     return first;
 }
 
+// ---------------------------------------------------------------------------
+// Block FGMRES (block_krylov = 1): one Krylov space for the batch's s
+// right-hand sides.  Per step j: Z_j = M(V_j) and W = H Z_j for the s columns
+// (the batched preconditioner and operator), two passes of block classical
+// Gram-Schmidt C = [V_0..V_j]^H W, W -= [V_0..V_j] C on the device, the new
+// block's QR by CholQR2 (the s x s Gram matrices on the device, their
+// Cholesky factors on the host), and the block Hessenberg least squares
+// min ||E_1 S_0 - Hbar Y||_F on the host by Householder reflections added
+// block column by block column.  FP64 basis and arithmetic; the flexible
+// basis Z in the multigrid's precision.  The oracle's block_fgmres follows the
+// same steps.
+// ---------------------------------------------------------------------------
+using cdx = std::complex<double>;
+
+// Cholesky G = L L^H of an s x s Hermitian matrix (row-major); false if not
+// positive definite
+static bool host_cholesky(int s, const std::vector<cdx>& G, std::vector<cdx>& L) {
+    L.assign((size_t)s * s, 0.0);
+    for (int j = 0; j < s; ++j) {
+        double d = G[(size_t)j * s + j].real();
+        for (int k = 0; k < j; ++k) d -= std::norm(L[(size_t)j * s + k]);
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        const double ljj = std::sqrt(d);
+        L[(size_t)j * s + j] = ljj;
+        for (int i = j + 1; i < s; ++i) {
+            cdx v = G[(size_t)i * s + j];
+            for (int k = 0; k < j; ++k) v -= L[(size_t)i * s + k] * std::conj(L[(size_t)j * s + k]);
+            L[(size_t)i * s + j] = v / ljj;
+        }
+    }
+    return true;
+}
+
+struct BlockWork {
+    int s = 0, m = 0;
+    double2* C = nullptr;        // device (m+1) s x s coefficients / Gram matrices / Y
+    double2* T = nullptr;        // device s x s triangular factor
+    double2* part = nullptr;     // device dot partials
+    double2* hbuf = nullptr;     // pinned host staging ((m+1) s x s)
+};
+
+// One CholQR pass: G = W^H W (W: s columns at stride n), G = L L^H, and the
+// columns W R^{-1} (R = L^H) written to dst (stride sd; may be W itself).
+// R returned (row-major, upper triangular).
+static int cholqr_pass(Ctx& c, BlockWork& bw, const double2* W, size_t n, double2* dst, size_t sd,
+                       std::vector<cdx>& R, cudaStream_t st) {
+    const int s = bw.s;
+    launch_block_dot(W, n, 1, s, W, n, bw.part, bw.C, st);
+    BAH_CUDA_TRY(cudaMemcpyAsync(bw.hbuf, bw.C, (size_t)s * s * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<cdx> G((size_t)s * s), L;
+    for (int q = 0; q < s * s; ++q) G[q] = cdx(bw.hbuf[q].x, bw.hbuf[q].y);     // G[a][b] = conj(w_a) . w_b
+    if (!host_cholesky(s, G, L)) {
+        set_error("block FGMRES: the new block is numerically rank deficient (Cholesky QR failed)");
+        return BAH_ERR_NONFINITE;
+    }
+    // R = L^H (upper); T = R^{-1} by back substitution, row-major T[q][b]
+    R.assign((size_t)s * s, 0.0);
+    for (int i = 0; i < s; ++i)
+        for (int j = i; j < s; ++j) R[(size_t)i * s + j] = std::conj(L[(size_t)j * s + i]);
+    std::vector<cdx> T((size_t)s * s, 0.0);
+    for (int b = 0; b < s; ++b) {
+        T[(size_t)b * s + b] = 1.0 / R[(size_t)b * s + b];
+        for (int q = b - 1; q >= 0; --q) {
+            cdx acc = 0.0;
+            for (int k = q + 1; k <= b; ++k) acc += R[(size_t)q * s + k] * T[(size_t)k * s + b];
+            T[(size_t)q * s + b] = -acc / R[(size_t)q * s + q];
+        }
+    }
+    for (int q = 0; q < s * s; ++q) bw.hbuf[q] = make_double2(T[q].real(), T[q].imag());
+    BAH_CUDA_TRY(cudaMemcpyAsync(bw.T, bw.hbuf, (size_t)s * s * sizeof(double2), cudaMemcpyHostToDevice, st));
+    launch_block_scale(W, s, bw.T, dst, sd, n, st);
+    BAH_CUDA_TRY(cudaStreamSynchronize(st));         // the staging buffer is reused next
+    return BAH_OK;
+}
+// CholQR2: dst = Q with W = Q R (W is overwritten by the first pass)
+static int cholqr2(Ctx& c, BlockWork& bw, double2* W, size_t n, double2* dst, size_t sd, std::vector<cdx>& R,
+                   cudaStream_t st) {
+    const int s = bw.s;
+    std::vector<cdx> R1, R2;
+    TRY(cholqr_pass(c, bw, W, n, W, n, R1, st));
+    TRY(cholqr_pass(c, bw, W, n, dst, sd, R2, st));
+    R.assign((size_t)s * s, 0.0);
+    for (int i = 0; i < s; ++i)
+        for (int j = i; j < s; ++j) {
+            cdx acc = 0.0;
+            for (int k = i; k <= j; ++k) acc += R2[(size_t)i * s + k] * R1[(size_t)k * s + j];
+            R[(size_t)i * s + j] = acc;
+        }
+    return BAH_OK;
+}
+
+// Incremental Householder QR of the block Hessenberg matrix (column-major,
+// ld rows) and of its right-hand side G = Q^H E_1 S_0
+struct BlockLS {
+    int s, m, ld;
+    std::vector<cdx> H;      // ld x (m s)
+    std::vector<cdx> G;      // ld x s
+    std::vector<std::vector<cdx>> refl;   // reflector per column (from its row down)
+    void init(int s_, int m_, const std::vector<cdx>& S0) {
+        s = s_; m = m_; ld = (m + 1) * s;
+        H.assign((size_t)ld * m * s, 0.0);
+        G.assign((size_t)ld * s, 0.0);
+        refl.assign((size_t)m * s, {});
+        for (int i = 0; i < s; ++i)
+            for (int b = 0; b < s; ++b) G[(size_t)b * ld + i] = S0[(size_t)i * s + b];
+    }
+    cdx& h(int i, int j) { return H[(size_t)j * ld + i]; }
+    // block column j is in H (rows 0 .. (j+2)s - 1); triangularise it, return
+    // the residual norm of each right-hand side column
+    void add_block(int j, std::vector<double>& res) {
+        const int c0 = j * s, rows = (j + 2) * s;
+        for (int c = 0; c < c0; ++c) apply(c, c0, c0 + s, rows);
+        for (int c = c0; c < c0 + s; ++c) {
+            std::vector<cdx> v(rows - c);
+            double nx = 0.0;
+            for (int i = c; i < rows; ++i) { v[i - c] = h(i, c); nx += std::norm(v[i - c]); }
+            nx = std::sqrt(nx);
+            const cdx x0 = v[0];
+            const cdx ph = std::abs(x0) > 0.0 ? x0 / std::abs(x0) : cdx(1.0, 0.0);
+            const cdx alpha = -ph * nx;
+            v[0] -= alpha;
+            double nv = 0.0;
+            for (const cdx& q : v) nv += std::norm(q);
+            nv = std::sqrt(nv);
+            if (nv > 0.0)
+                for (cdx& q : v) q /= nv;
+            refl[c] = v;
+            apply(c, c, c0 + s, rows);
+            applyG(c, rows);
+        }
+        res.assign(s, 0.0);
+        for (int b = 0; b < s; ++b) {
+            double t = 0.0;
+            for (int i = (j + 1) * s; i < rows; ++i) t += std::norm(G[(size_t)b * ld + i]);
+            res[b] = std::sqrt(t);
+        }
+    }
+    void apply(int c, int col_from, int col_to, int rows) {
+        const std::vector<cdx>& v = refl[c];
+        if (v.empty()) return;
+        const int top = std::min(rows, c + (int)v.size());
+        for (int k = col_from; k < col_to; ++k) {
+            cdx d = 0.0;
+            for (int i = c; i < top; ++i) d += std::conj(v[i - c]) * h(i, k);
+            for (int i = c; i < top; ++i) h(i, k) -= 2.0 * v[i - c] * d;
+        }
+    }
+    void applyG(int c, int rows) {
+        const std::vector<cdx>& v = refl[c];
+        const int top = std::min(rows, c + (int)v.size());
+        for (int b = 0; b < s; ++b) {
+            cdx d = 0.0;
+            for (int i = c; i < top; ++i) d += std::conj(v[i - c]) * G[(size_t)b * ld + i];
+            for (int i = c; i < top; ++i) G[(size_t)b * ld + i] -= 2.0 * v[i - c] * d;
+        }
+    }
+    // Y (k s x s, row-major [row][b]) = R^{-1} G[0 .. k s)
+    void solve(int k, std::vector<cdx>& Y) {
+        const int N = k * s;
+        Y.assign((size_t)N * s, 0.0);
+        for (int b = 0; b < s; ++b)
+            for (int i = N - 1; i >= 0; --i) {
+                cdx acc = G[(size_t)b * ld + i];
+                for (int q = i + 1; q < N; ++q) acc -= h(i, q) * Y[(size_t)q * s + b];
+                Y[(size_t)i * s + b] = acc / h(i, i);
+            }
+    }
+};
+
+static int fgmres_block(Ctx& c, const double2* b, double2* x, int s, double rtol, bah_stats* out, cudaStream_t st) {
+    const size_t n = c.vec_len(), sv = c.ks.sv;
+    const int m = c.m;
+    KS ks = c.ks;
+    ks.active = nullptr;
+    Batch bt;
+    bt.nr = s;
+    bt.active = nullptr;
+    BlockWork bw;
+    bw.s = s; bw.m = m;
+    bw.C = c.bC; bw.T = c.bT; bw.part = c.bpart; bw.hbuf = c.bhost;
+    std::vector<double> bn(s), beta(s), est(s, 1.0);
+    launch_norm2(b, n, c.dpart, c.nrm, 1, s, ks, st);
+    {
+        std::vector<double> tmp(c.nbatch);
+        TRY(read_scalars(c, 1, tmp.data(), st));
+        for (int r = 0; r < s; ++r) bn[r] = tmp[r];
+    }
+    for (int r = 0; r < s; ++r)
+        if (!(bn[r] > 0.0) || !std::isfinite(bn[r])) {
+            set_error("block FGMRES needs finite, nonzero right-hand sides");
+            return BAH_ERR_ARG;
+        }
+    BAH_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)s * n * sizeof(double2), st));
+    BAH_CUDA_TRY(cudaMemcpyAsync(c.R, b, (size_t)s * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    beta = bn;
+    int total = 0, restarts = 0;
+    std::vector<cdx> S0, R, Y;
+    std::vector<double> res;
+    auto done = [&]() {
+        for (int r = 0; r < s; ++r) if (beta[r] > rtol * bn[r]) return false;
+        return true;
+    };
+    while (!done() && total < c.o.maxit) {
+        NvtxRange nvc("block fgmres restart cycle");
+        // R_0 = V_0 S_0
+        TRY(cholqr2(c, bw, c.R, n, c.V, sv, S0, st));
+        BlockLS ls;
+        ls.init(s, m, S0);
+        const int mm = std::min(m, c.o.maxit - total);
+        int jd = 0;
+        for (int j = 0; j < mm; ++j) {
+            void* zj = (char*)c.Z + (size_t)j * n * c.vsz;
+            precond_any(c, c.V + (size_t)j * n, sv, zj, ks.sz, bt, st);
+            op_apply_z(c, zj, ks.sz, c.W, n, bt, st);
+            for (int pass = 0; pass < 2; ++pass) {            // block CGS2
+                launch_block_dot(c.V, sv, j + 1, s, c.W, n, bw.part, bw.C, st);
+                const size_t cnt = (size_t)(j + 1) * s * s;
+                BAH_CUDA_TRY(cudaMemcpyAsync(bw.hbuf, bw.C, cnt * sizeof(double2), cudaMemcpyDeviceToHost, st));
+                launch_block_update(c.V, sv, j + 1, s, bw.C, c.W, n, 1, st);
+                BAH_CUDA_TRY(cudaStreamSynchronize(st));
+                for (int row = 0; row < (j + 1) * s; ++row)
+                    for (int q = 0; q < s; ++q)
+                        ls.h(row, j * s + q) += cdx(bw.hbuf[(size_t)row * s + q].x, bw.hbuf[(size_t)row * s + q].y);
+            }
+            TRY(cholqr2(c, bw, c.W, n, c.V + (size_t)(j + 1) * n, sv, R, st));
+            for (int i = 0; i < s; ++i)
+                for (int q = 0; q < s; ++q) ls.h((j + 1) * s + i, j * s + q) = R[(size_t)i * s + q];
+            ls.add_block(j, res);
+            ++total;
+            jd = j + 1;
+            bool all = true;
+            for (int r = 0; r < s; ++r) {
+                est[r] = res[r] / bn[r];
+                if (!std::isfinite(est[r])) { set_error("non-finite block residual"); return BAH_ERR_NONFINITE; }
+                if (res[r] > rtol * bn[r]) all = false;
+            }
+            if (all) break;
+        }
+        // X += [Z_0 .. Z_{jd-1}] Y
+        ls.solve(jd, Y);
+        for (size_t q = 0; q < Y.size(); ++q) bw.hbuf[q] = make_double2(Y[q].real(), Y[q].imag());
+        BAH_CUDA_TRY(cudaMemcpyAsync(bw.C, bw.hbuf, Y.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+        if (c.mode == BAH_MIXED) launch_block_xupdate<float2>((const float2*)c.Z, ks.sz, jd, s, bw.C, x, n, st);
+        else launch_block_xupdate<double2>((const double2*)c.Z, ks.sz, jd, s, bw.C, x, n, st);
+        apply_h(c, x, n, c.R, n, b, n, 0, s, st);
+        launch_norm2(c.R, n, c.dpart, c.nrm, 0, s, ks, st);
+        std::vector<double> tmp(c.nbatch);
+        TRY(read_scalars(c, 0, tmp.data(), st));
+        for (int r = 0; r < s; ++r) {
+            beta[r] = tmp[r];
+            if (!std::isfinite(beta[r])) { set_error("non-finite true residual"); return BAH_ERR_NONFINITE; }
+        }
+        ++restarts;
+    }
+    int first = BAH_OK;
+    for (int r = 0; r < s; ++r) {
+        bah_stats q{};
+        q.iters = total;
+        q.restarts = restarts;
+        q.relres_true = beta[r] / bn[r];
+        q.relres_est = est[r];
+        q.status = q.relres_true <= rtol ? BAH_OK : BAH_ERR_NOT_CONVERGED;
+        if (out) out[r] = q;
+        if (q.status != BAH_OK && first == BAH_OK) first = q.status;
+    }
+    return first;
+}
+
 static bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -1383,6 +1671,7 @@ void bah_default_opts(bah_opts* o) {
     o->block_rtol = 0.0;
     o->block_maxit = 2000;
     o->block_alpha = 0.0;
+    o->block_krylov = 0;
 }
 
 const char* bah_status_string(int s) {
@@ -1435,6 +1724,13 @@ int bah_create(const bah_grid* grid, const bah_medium* med, const bah_opts* opts
     if (!(o.block_rtol >= 0.0) || o.block_maxit < 1 || !(o.block_alpha >= 0.0)) {
         set_error("block_rtol and block_alpha must be >= 0 and block_maxit >= 1");
         return BAH_ERR_ARG;
+    }
+    if (o.block_krylov != 0 && o.block_krylov != 1) { set_error("bad block_krylov"); return BAH_ERR_ARG; }
+    if (o.block_krylov && (dim != 2 || o.rhs_block < 2 || o.rhs_block > 16 || o.krylov_arith != BAH_KRYLOV_FP64 ||
+                           o.block_rtol > 0.0)) {
+        set_error("block FGMRES (block_krylov = 1) is implemented for 2-D grids, rhs_block 2..16, the FP64 basis "
+                  "and multigrid block solves");
+        return BAH_ERR_UNSUPPORTED;
     }
     if (o.block_rtol > 0.0 && (dim != 2 || o.rhs_block != 1)) {
         set_error("exact block solves (block_rtol > 0) are implemented for 2-D grids with rhs_block = 1");
@@ -1747,6 +2043,7 @@ int bah_profile_read(bah_ctx* h, bah_profile* out) {
 static int solve_impl(bah_ctx* h, const void* b, void* x, int nrhs, double rtol, bah_stats* stats, void* stream,
                       int adjoint) {
     if (!h || !b || !x || nrhs < 0 || !(rtol > 0.0)) { set_error("bad argument"); return BAH_ERR_ARG; }
+    NvtxRange nv(adjoint ? "bah_solve_adjoint" : "bah_solve");
     Ctx& c = h->c;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = c.vec_len();
@@ -1767,7 +2064,8 @@ static int solve_impl(bah_ctx* h, const void* b, void* x, int nrhs, double rtol,
             if (adjoint) launch_conj(c.Bs, (size_t)nr * n, st);
         }
         double2* xd = dev_x ? xk : c.X;
-        int s = fgmres_batch(c, c.Bs, xd, nr, rtol, stats ? stats + k0 : nullptr, st);
+        int s = c.o.block_krylov ? fgmres_block(c, c.Bs, xd, nr, rtol, stats ? stats + k0 : nullptr, st)
+                                 : fgmres_batch(c, c.Bs, xd, nr, rtol, stats ? stats + k0 : nullptr, st);
         if (s == BAH_ERR_CUDA || s == BAH_ERR_OOM || s == BAH_ERR_ARG) return s;
         if (adjoint) {
             Prof pr(c, BAH_K_SMALL, st, (double)nr * n * 32.0);
