@@ -57,52 +57,6 @@ __global__ void __launch_bounds__(256) k_jacobi(LvlSet<typename MGT<MODE>::V, ty
     xout[t] = cmk<V>(x.x + w * corr.x, x.y + w * corr.y);
 }
 
-// The fine-level sweep with PPT points per thread (a CTA covers 256 * PPT
-// consecutive points, thread t the points t, t + 256, ...): fewer CTAs, and
-// the loads of a thread's points can go out together.  Same arithmetic as
-// k_jacobi<MODE, true, 1>.
-template <int MODE, int PPT>
-__global__ void __launch_bounds__(256) k_jacobi_l0(LvlSet<typename MGT<MODE>::V, typename MGT<MODE>::CC> s,
-                                                   Fine5<typename MGT<MODE>::C, typename MGT<MODE>::CC> f5,
-                                                   typename MGT<MODE>::R w, int zero_init) {
-    pdl_prologue();
-    using V = typename MGT<MODE>::V;
-    const auto& B = s.blk[blockIdx.y];
-    const int n1 = s.n1, n2 = s.n2, np = n1 * n2;
-    const int rr = blockIdx.z;
-    if (s.active && !s.active[rr]) return;
-    V* __restrict__ xout = B.xout + rr * B.sxo;
-    const V* __restrict__ bb = B.b + rr * B.sb;
-    const V* __restrict__ xin = B.xin + rr * B.sxi;
-    const int t0 = blockIdx.x * (256 * PPT) + threadIdx.x;
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        const int t = t0 + p * 256;
-        if (t >= np) break;
-        const int i = t % n1, j = t / n1;
-        if (!valid_pt(B.type, i, j)) { xout[t] = czero<V>(); continue; }
-        const V b = bb[t];
-        const V dg = diag_only<MODE>(&f5, B, np, t);
-        if (zero_init) {
-            xout[t] = cscale(cdiv(b, dg), w);
-            continue;
-        }
-        const V ax = apply_fine5_fn<MODE>(f5, B.type, i, j, t, [&](int g) { return xin[g]; });
-        const V corr = cdiv(csub(b, ax), dg);
-        const V x = xin[t];
-        xout[t] = cmk<V>(x.x + w * corr.x, x.y + w * corr.y);
-    }
-}
-static int l0_ppt() {
-    static int v = -1;
-    if (v < 0) {
-        v = 1;
-        if (const char* e = getenv("BAH_L0_PPT")) v = atoi(e);
-        if (v != 2 && v != 4) v = 1;
-    }
-    return v;
-}
-
 // ---------------------------------------------------------------------------
 // residual:  r = b - A x
 // ---------------------------------------------------------------------------
@@ -222,12 +176,7 @@ void launch_jacobi(const LvlSet<typename Prec<MODE>::V, typename Prec<MODE>::CC>
     const Fine5<typename Prec<MODE>::C, typename Prec<MODE>::CC> nof{};
     const int rm = f5 ? 1 : max_radius(s);
     const size_t sm = (f5 || zero_init) ? 0 : staged_smem<MODE>(s, rm);
-    const int ppt = l0_ppt();
-    if (f5 && ppt > 1) {
-        dim3 g2((np + 256 * ppt - 1) / (256 * ppt), s.nb, s.nrhs);
-        if (ppt == 2) launch_pdl(k_jacobi_l0<MODE, 2>, g2, dim3(256), 0, st, s, *f5, (R)w, zero_init);
-        else launch_pdl(k_jacobi_l0<MODE, 4>, g2, dim3(256), 0, st, s, *f5, (R)w, zero_init);
-    } else if (f5) launch_pdl(k_jacobi<MODE, true, 1>, dim3(g), dim3(256), 0, st, s, *f5, (R)w, zero_init);
+    if (f5) launch_pdl(k_jacobi<MODE, true, 1>, dim3(g), dim3(256), 0, st, s, *f5, (R)w, zero_init);
     else if (sm && rm <= 1) launch_pdl(k_stencil_staged<MODE, 1, false>, dim3(g), dim3(256), sm, st, s, (R)w);
     else if (sm) launch_pdl(k_stencil_staged<MODE, 2, false>, dim3(g), dim3(256), sm, st, s, (R)w);
     else if (rm <= 1) launch_pdl(k_jacobi<MODE, false, 1>, dim3(g), dim3(256), 0, st, s, nof, (R)w, zero_init);

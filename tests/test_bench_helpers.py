@@ -35,7 +35,7 @@ def test_presets_keep_the_2d_benchmark_and_give_c5_the_3d_cycle(monkeypatch):
     assert tuple(getattr(a, f) for f in fields) == (0, 0.8, "V", "1,3", "0.8,0.8,0.3", "bilinear", "fp64", 10)
     monkeypatch.setattr("sys.argv", ["bench.py", "--config", "c4"])
     a = bench.parse()
-    assert tuple(getattr(a, f) for f in fields) == (0, -1.0, "V", "1,2", "0.8,0.8,0.3", "bilinear", "fp64", 10)
+    assert tuple(getattr(a, f) for f in fields) == (0, -1.0, "V", "1,2", "0.8,0.8,0.3", "bilinear", "fp64", 20)
     monkeypatch.setattr("sys.argv", ["bench.py", "--config", "c5"])
     a = bench.parse()
     assert tuple(getattr(a, f) for f in fields) == (5, 0.4, "W", "2,2", "0.8,0.8,0.2", "mixed", "fp64", 20)
