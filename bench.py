@@ -88,6 +88,11 @@ KERNEL_NAMES_3D = {0: "k_apply3", 1: "k_distrib3", 2: "k_urhs3", 3: "k_jacobi3",
 # FP64 flops per algorithmic byte of the FP64 classes (2 flops per real FMA):
 #   dot/axpy: 8 flops per complex MAC on 16 streamed bytes; operator: ~84 flops per cell on ~200 bytes
 FP64_FLOP_PER_BYTE = {"dot": 0.5, "axpy": 0.5, "update": 8.0 / 8.0, "operator": 84.0 / 200.0}
+# DRAM bytes (read + write) per launch of a kernel class, averaged over the class's launches in one
+# FGMRES step as they occur in the solve, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the same build and workload; the summaries under profiles/ give the
+# command and the per-kernel figures.  (workload, class) -> bytes per launch.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def parse():
@@ -544,7 +549,8 @@ def run_bah(args):
     achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
     kname = (KERNEL_NAMES_3D if prob.dim == 3 else KERNEL_NAMES).get(dom_id, dom)
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
-            "unit": "GB/s", "frac": (achieved_gbs / hbm_peak) if achieved_gbs else None, "traffic": None,
+            "unit": "GB/s", "frac": (achieved_gbs / hbm_peak) if achieved_gbs else None,
+            "traffic": TRAFFIC_PER_LAUNCH.get((args.config, dom)),
             "peak_source": peak_src, "avg_launch_us": dom_ms * 1e3, "algorithmic_bytes_per_launch": dom_bytes,
             "launches_timed": dc["calls"],
             "timing": f"CUDA events on the launching stream around every launch of the class, {args.steps} solves "
