@@ -7,11 +7,12 @@ nu in [0.25, 0.45], rho = 0.31 Vp^0.25, 10 points per shear wavelength,
 in HBM, setup excluded.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bah|reference]
-                  [--config c2|c3|c4|c5]
+                  [--config c2|c3|c4|c5|c5s]
 
 --config selects another workload: c3 (1024^2 random field), c4 (1024x512
 layered, 64 sources in one batch) or c5 (128^3 random field, run with the
-paper's 3-D cycle: W(2,2), mixed intergrid, Jacobi 0.8/0.8/0.2).
+paper's 3-D cycle: W(2,2), mixed intergrid, Jacobi 0.8/0.8/0.2); c5s is a
+64^3 copy of c5, a small case for profiling the 3-D kernels.
 
 The main arm (bah) times the mixed-precision solve (bfloat16 coefficients,
 FP32 multigrid, FP64 FGMRES / operator / coarsest solve) and, beside it, the
@@ -60,6 +61,8 @@ WORKLOADS = {
     "c5": "3D 128x128x128 smooth random medium (log Vp Gaussian random field, correlation 16 cells, std 0.2, mean "
           "log 3; nu in [0.3,0.49]), 8 points per shear wavelength, 10-cell absorbing layer, top-face point source, "
           "FGMRES to rel-res 1e-6",
+    "c5s": "3D 64x64x64 copy of the c5 medium (correlation 8 cells, 5-cell absorbing layer), 8 points per shear "
+           "wavelength, top-face point source, FGMRES to rel-res 1e-6 (a small case of the 3-D kernels, for profiles)",
 }
 # per-workload cycle settings where they differ from the 2-D benchmark's: the 3-D
 # workload runs the paper's 3-D multigrid (Sec. 4.5: mixed intergrid, W(2,2),
@@ -74,6 +77,8 @@ PRESETS = {
     "c4": dict(alpha=-1.0, nu="1,2", restart=20),
     "c5": dict(levels=5, alpha=0.4, cycle="W", nu="2,2", jacobi="0.8,0.8,0.2", intergrid="mixed", krylov="fp64",
                restart=20),
+    "c5s": dict(levels=4, alpha=0.4, cycle="W", nu="2,2", jacobi="0.8,0.8,0.2", intergrid="mixed", krylov="fp64",
+                restart=20),
 }
 WORKLOAD = WORKLOADS["c2"]
 L2_FLUSH_BYTES = 512 << 20

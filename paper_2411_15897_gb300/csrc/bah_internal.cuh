@@ -374,14 +374,16 @@ template <class V>
 void launch_distrib3(const Op3& op, const double2* r, V* tp, cudaStream_t st);
 template <class V>
 void launch_urhs3(const Op3& op, const double2* r, const V* ep, V* const* su, cudaStream_t st);
+// the level kernels run blocks type0 .. type0 + nq - 1 (nq <= 3) of one level in
+// one launch, block y on the y-th pointer of each array
 template <class V>
 // S: stencil entries, FP64 complex (V = double2) or bfloat16 complex (V = float2)
-void launch_jacobi3(int type, const int* n, int ns, const void* S, const V* b, const V* xin, V* xout, double w, int zero,
-                    int res, cudaStream_t st);
+void launch_jacobi3(int type0, int nq, const int* n, int ns, const void* const* S, const V* const* b,
+                    const V* const* xin, V* const* xout, double w, int zero, int res, cudaStream_t st);
 template <class V>
-void launch_restrict3(int type, const int* nf, const V* r, V* bc, cudaStream_t st);
+void launch_restrict3(int type0, int nq, const int* nf, const V* const* r, V* const* bc, cudaStream_t st);
 template <class V>
-void launch_prolong3(int type, const int* nf, const V* ec, V* x, cudaStream_t st);
+void launch_prolong3(int type0, int nq, const int* nf, const V* const* ec, V* const* x, cudaStream_t st);
 void launch_galerkin3(int type, const int* nf, int nsf, const double2* Sf, double2* Sc, int* err, cudaStream_t st);
 int coarse_invert3(int type, const int* n, const double2* S, double2* inv, double2* work, int* flag, cudaStream_t st);
 // dense FP64 inverse X = A^{-1} of an n x n matrix by Gauss-Jordan elimination

@@ -11,12 +11,22 @@
 // every kernel writes as zero and none reads as an unknown.
 //
 // Each kernel runs one thread per point and bounds-checks every neighbour
-// against the grid before it loads it.
+// against the grid before it loads it.  The kernels of the solve's step begin
+// with pdl_prologue() and are launched with programmatic dependent launch; the
+// level kernels run the three displacement blocks of a level in one launch.
 #include "bah_internal.cuh"
 
 #include <type_traits>
 
 namespace bah {
+
+// pointers of up to three blocks of one level, one per blockIdx.y of a launch;
+// pick() selects without indexing the parameter array at a run-time index
+// (which would copy it to the stack)
+template <class T> struct Set3 { T* p[3]; };
+template <class T> __device__ __forceinline__ T* pick(const Set3<T>& s, int y) {
+    return y == 0 ? s.p[0] : (y == 1 ? s.p[1] : s.p[2]);
+}
 
 __host__ __device__ __forceinline__ bool valid3(int type, const int* c) { return type >= 3 || c[type] >= 1; }
 
@@ -155,6 +165,7 @@ template <class Vin>
 __global__ void __launch_bounds__(256) k_apply3(Op3 op, const Vin* __restrict__ x, double2* __restrict__ y,
                                                 const double2* __restrict__ b, int conj, size_t sx, size_t sy,
                                                 size_t sb) {
+    pdl_prologue();
     const int n1 = op.n[0], n2 = op.n[1];
     const int np = n1 * n2 * op.n[2];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,7 +217,7 @@ void launch_apply3(const Op3& op, const Vin* x, double2* y, const double2* b, in
                    size_t sb, cudaStream_t st) {
     const int np = op.n[0] * op.n[1] * op.n[2];
     if (nrhs < 1) return;
-    k_apply3<Vin><<<dim3((np + 255) / 256, nrhs), 256, 0, st>>>(op, x, y, b, conj, sx, sy, sb);
+    launch_pdl(k_apply3<Vin>, dim3((np + 255) / 256, nrhs), dim3(256), 0, st, op, x, y, b, conj, sx, sy, sb);
 }
 template void launch_apply3<double2>(const Op3&, const double2*, double2*, const double2*, int, int, size_t, size_t,
                                      size_t, cudaStream_t);
@@ -236,6 +247,7 @@ void launch_sanitize3(double2* v, int n1, int n2, int n3, int nvec, cudaStream_t
 // ---------------------------------------------------------------------------
 template <class V>
 __global__ void __launch_bounds__(256) k_distrib3(Op3 op, const double2* __restrict__ r, V* __restrict__ tp) {
+    pdl_prologue();
     const int n1 = op.n[0], n2 = op.n[1];
     const int np = n1 * n2 * op.n[2];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,6 +278,7 @@ __global__ void __launch_bounds__(256) k_distrib3(Op3 op, const double2* __restr
 template <class V>
 __global__ void __launch_bounds__(256) k_urhs3(Op3 op, const double2* __restrict__ r, const V* __restrict__ ep,
                                                V* __restrict__ s0, V* __restrict__ s1, V* __restrict__ s2) {
+    pdl_prologue();
     const int n1 = op.n[0], n2 = op.n[1];
     const int np = n1 * n2 * op.n[2];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,12 +301,12 @@ __global__ void __launch_bounds__(256) k_urhs3(Op3 op, const double2* __restrict
 template <class V>
 void launch_distrib3(const Op3& op, const double2* r, V* tp, cudaStream_t st) {
     const int np = op.n[0] * op.n[1] * op.n[2];
-    k_distrib3<V><<<(np + 255) / 256, 256, 0, st>>>(op, r, tp);
+    launch_pdl(k_distrib3<V>, dim3((np + 255) / 256), dim3(256), 0, st, op, r, tp);
 }
 template <class V>
 void launch_urhs3(const Op3& op, const double2* r, const V* ep, V* const* su, cudaStream_t st) {
     const int np = op.n[0] * op.n[1] * op.n[2];
-    k_urhs3<V><<<(np + 255) / 256, 256, 0, st>>>(op, r, ep, su[0], su[1], su[2]);
+    launch_pdl(k_urhs3<V>, dim3((np + 255) / 256), dim3(256), 0, st, op, r, ep, su[0], su[1], su[2]);
 }
 template void launch_distrib3<double2>(const Op3&, const double2*, double2*, cudaStream_t);
 template void launch_distrib3<float2>(const Op3&, const double2*, float2*, cudaStream_t);
@@ -305,12 +318,21 @@ template void launch_urhs3<float2>(const Op3&, const double2*, const float2*, fl
 // point p at S[s * points + p].
 // ---------------------------------------------------------------------------
 // one damped Jacobi sweep x_out = x_in + w D^{-1} (b - A x_in) (zero: x_in = 0),
-// or the residual x_out = b - A x_in (res)
-// (stencil entries stored as SC: FP64 complex, or bfloat16 complex in mixed mode)
+// or the residual x_out = b - A x_in (res), for up to three blocks of one
+// level in one launch: blockIdx.y = y runs block type type0 + y on the y-th
+// pointers.  Stencil entries are stored as SC: FP64 complex, or bfloat16
+// complex in mixed mode, where every entry and neighbour of a point is loaded
+// before the first multiply-add.
 template <class V, class SC, int NS>
-__global__ void __launch_bounds__(256) k_jacobi3(int type, int n1, int n2, int n3, const SC* __restrict__ S,
-                                                 const V* __restrict__ b, const V* xin, V* xout,
+__global__ void __launch_bounds__(256) k_jacobi3(int type0, int n1, int n2, int n3, Set3<const SC> Sset,
+                                                 Set3<const V> bset, Set3<const V> xiset, Set3<V> xoset,
                                                  typename VecTraits<V>::R w, int zero, int res) {
+    pdl_prologue();
+    const int y = blockIdx.y, type = type0 + y;
+    const SC* __restrict__ S = pick(Sset, y);
+    const V* __restrict__ b = pick(bset, y);
+    const V* xin = pick(xiset, y);
+    V* xout = pick(xoset, y);
     const int np = n1 * n2 * n3;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
@@ -321,6 +343,11 @@ __global__ void __launch_bounds__(256) k_jacobi3(int type, int n1, int n2, int n
     const int st[3] = {1, n1, n1 * n2};
     V acc = b[p];
     if (!zero) {
+        constexpr bool kBatch = sizeof(SC) <= 4;          // bf16 entries: all loads first
+        SC sv[kBatch ? NS : 1];
+        V xv[kBatch ? NS : 1];
+        bool inn[kBatch ? NS : 1];
+#pragma unroll
         for (int s = 0; s < NS; ++s) {
             int o[3];
             soff<NS>(s, o);
@@ -331,8 +358,18 @@ __global__ void __launch_bounds__(256) k_jacobi3(int type, int n1, int n2, int n
                 if (cc < 0 || cc >= n[a]) in = false;
                 q += o[a] * st[a];
             }
-            if (!in) continue;
-            acc = csub(acc, cmul(ldc(S[(size_t)s * np + p]), xin[q]));
+            if constexpr (kBatch) {
+                inn[s] = in;
+                sv[s] = S[(size_t)s * np + p];
+                xv[s] = xin[in ? q : p];
+            } else {
+                if (in) acc = csub(acc, cmul(ldc(S[(size_t)s * np + p]), xin[q]));
+            }
+        }
+        if constexpr (kBatch) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+                if (inn[s]) acc = csub(acc, cmul(ldc(sv[s]), xv[s]));
         }
     }
     if (res) { xout[p] = acc; return; }
@@ -340,22 +377,34 @@ __global__ void __launch_bounds__(256) k_jacobi3(int type, int n1, int n2, int n
     xout[p] = zero ? upd : cadd(xin[p], upd);
 }
 
+template <class T>
+static Set3<T> set3(T* const* v, int nq) {
+    Set3<T> s;
+    for (int y = 0; y < 3; ++y) s.p[y] = y < nq ? v[y] : nullptr;
+    return s;
+}
+
 template <class V>
-void launch_jacobi3(int type, const int* n, int ns, const void* S, const V* b, const V* xin, V* xout, double w, int zero,
-                    int res, cudaStream_t st) {
+void launch_jacobi3(int type0, int nq, const int* n, int ns, const void* const* S, const V* const* b,
+                    const V* const* xin, V* const* xout, double w, int zero, int res, cudaStream_t st) {
     const int np = n[0] * n[1] * n[2];
     using R = typename VecTraits<V>::R;
     using SC = typename std::conditional<std::is_same<V, double2>::value, double2, __nv_bfloat162>::type;
-    const SC* s = (const SC*)S;
+    const SC* s[3];
+    for (int y = 0; y < nq; ++y) s[y] = (const SC*)S[y];
+    const Set3<const SC> ss = set3<const SC>(s, nq);
+    const dim3 g((np + 255) / 256, nq);
     if (ns == 7)
-        k_jacobi3<V, SC, 7><<<(np + 255) / 256, 256, 0, st>>>(type, n[0], n[1], n[2], s, b, xin, xout, (R)w, zero, res);
+        launch_pdl(k_jacobi3<V, SC, 7>, g, dim3(256), 0, st, type0, n[0], n[1], n[2], ss, set3<const V>(b, nq),
+                   set3<const V>(xin, nq), set3<V>(xout, nq), (R)w, zero, res);
     else
-        k_jacobi3<V, SC, 27><<<(np + 255) / 256, 256, 0, st>>>(type, n[0], n[1], n[2], s, b, xin, xout, (R)w, zero, res);
+        launch_pdl(k_jacobi3<V, SC, 27>, g, dim3(256), 0, st, type0, n[0], n[1], n[2], ss, set3<const V>(b, nq),
+                   set3<const V>(xin, nq), set3<V>(xout, nq), (R)w, zero, res);
 }
-template void launch_jacobi3<double2>(int, const int*, int, const void*, const double2*, const double2*, double2*,
-                                      double, int, int, cudaStream_t);
-template void launch_jacobi3<float2>(int, const int*, int, const void*, const float2*, const float2*, float2*, double,
-                                     int, int, cudaStream_t);
+template void launch_jacobi3<double2>(int, int, const int*, int, const void* const*, const double2* const*,
+                                      const double2* const*, double2* const*, double, int, int, cudaStream_t);
+template void launch_jacobi3<float2>(int, int, const int*, int, const void* const*, const float2* const*,
+                                     const float2* const*, float2* const*, double, int, int, cudaStream_t);
 
 // 1-D transfer weights.  Restriction (Eq. 4.1 / 4.4, mixed intergrid): along
 // the block's nodal axis 1/4 [1 2 1] around fine face 2K; along a cell-centred
@@ -392,10 +441,53 @@ __host__ __device__ __forceinline__ int plist3(bool nodal, int m, int nc, int* K
     return 2;
 }
 
-// b_c = R r on the coarse grid (fine grid n, coarse n/2)
+// the transfer weights of one axis as a fixed number of (index, weight)
+// pairs, unused pairs with weight 0 at an in-range index, so that the
+// kernels below keep them in registers: restriction, three fine indices;
+// prolongation, two coarse indices (the same weights as rlist3 / plist3)
+template <class R>
+__device__ __forceinline__ void raxis3(bool nodal, int J, int* f, R* w) {
+    if (nodal) {
+        f[0] = 2 * J - 1; w[0] = R(0.25);
+        f[1] = 2 * J;     w[1] = R(0.5);
+        f[2] = 2 * J + 1; w[2] = R(0.25);
+    } else {
+        f[0] = 2 * J;     w[0] = R(0.5);
+        f[1] = 2 * J + 1; w[1] = R(0.5);
+        f[2] = 2 * J;     w[2] = R(0);
+    }
+}
+template <class R>
+__device__ __forceinline__ void paxis3(bool nodal, int m, int nc, int* K, R* w) {
+    if (nodal) {
+        if ((m & 1) == 0) {
+            K[0] = m >> 1; w[0] = (K[0] >= 1 && K[0] <= nc - 1) ? R(1) : R(0);
+            K[1] = K[0];   w[1] = R(0);
+        } else {
+            K[0] = (m - 1) >> 1; w[0] = K[0] >= 1 ? R(0.5) : R(0);
+            K[1] = (m + 1) >> 1; w[1] = K[1] <= nc - 1 ? R(0.5) : R(0);
+        }
+        K[0] = min(K[0], nc - 1);
+        K[1] = min(K[1], nc - 1);
+        return;
+    }
+    const int J = m >> 1;
+    int Jn = (m & 1) ? J + 1 : J - 1;
+    if (Jn < 0 || Jn > nc - 1) Jn = J;
+    K[0] = J;  w[0] = R(0.75);
+    K[1] = Jn; w[1] = R(0.25);
+}
+
+// b_c = R r on the coarse grid (fine grid n, coarse n/2), accumulated in the
+// cycle's arithmetic (FP32 in mixed mode; the weights 1/2 and 1/4 and their
+// products are exact there)
 template <class V>
-__global__ void __launch_bounds__(256) k_restrict3(int type, int f1, int f2, int f3, const V* __restrict__ r,
-                                                   V* __restrict__ bc) {
+__global__ void __launch_bounds__(256) k_restrict3(int type0, int f1, int f2, int f3, Set3<const V> rset,
+                                                   Set3<V> bcset) {
+    pdl_prologue();
+    const int type = type0 + (int)blockIdx.y;
+    const V* __restrict__ r = pick(rset, (int)blockIdx.y);
+    V* __restrict__ bc = pick(bcset, (int)blockIdx.y);
     const int c1 = f1 / 2, c2 = f2 / 2, c3 = f3 / 2;
     const int npc = c1 * c2 * c3;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,24 +496,25 @@ __global__ void __launch_bounds__(256) k_restrict3(int type, int f1, int f2, int
     coords3(p, c1, c2, J);
     if (!valid3(type, J)) { bc[p] = czero<V>(); return; }
     using R = typename VecTraits<V>::R;
-    int f[3][3], cnt[3];
-    double wd[3][3] = {};
-    R w[3][3];
-    for (int a = 0; a < 3; ++a) {
-        cnt[a] = rlist3(a == type, J[a], f[a], wd[a]);
-        for (int e = 0; e < 3; ++e) w[a][e] = (R)wd[a][e];     // 1/2, 1/4, 3/8, 1/8: exact in FP32
-    }
-    // accumulated in the cycle's arithmetic (FP32 in mixed mode)
+    int fx[3], fy[3], fz[3];
+    R wx[3], wy[3], wz[3];
+    raxis3<R>(type == 0, J[0], fx, wx);
+    raxis3<R>(type == 1, J[1], fy, wy);
+    raxis3<R>(type == 2, J[2], fz, wz);
     V acc = czero<V>();
-    for (int z = 0; z < cnt[2]; ++z)
-        for (int y = 0; y < cnt[1]; ++y) {
-            const R wzy = w[2][z] * w[1][y];
-            for (int x = 0; x < cnt[0]; ++x) {
-                const size_t q = ((size_t)f[2][z] * f2 + f[1][y]) * f1 + f[0][x];
-                const V v = r[q];
-                const R ww = wzy * w[0][x];
-                acc.x += ww * v.x;
-                acc.y += ww * v.y;
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            const R wzy = wz[z] * wy[y];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const R ww = wzy * wx[x];
+                if (ww != R(0)) {
+                    const V v = r[((size_t)fz[z] * f2 + fy[y]) * f1 + fx[x]];
+                    acc.x += ww * v.x;
+                    acc.y += ww * v.y;
+                }
             }
         }
     bc[p] = acc;
@@ -429,10 +522,13 @@ __global__ void __launch_bounds__(256) k_restrict3(int type, int f1, int f2, int
 
 // x += P e_c on the fine grid
 template <class V>
-__global__ void __launch_bounds__(256) k_prolong3(int type, int f1, int f2, int f3, const V* __restrict__ ec,
-                                                  V* __restrict__ x) {
-    const int c1 = f1 / 2, c2 = f2 / 2;
-    const int nc[3] = {f1 / 2, f2 / 2, f3 / 2};
+__global__ void __launch_bounds__(256) k_prolong3(int type0, int f1, int f2, int f3, Set3<const V> ecset,
+                                                  Set3<V> xset) {
+    pdl_prologue();
+    const int type = type0 + (int)blockIdx.y;
+    const V* __restrict__ ec = pick(ecset, (int)blockIdx.y);
+    V* __restrict__ x = pick(xset, (int)blockIdx.y);
+    const int c1 = f1 / 2, c2 = f2 / 2, c3 = f3 / 2;
     const int np = f1 * f2 * f3;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
@@ -440,42 +536,46 @@ __global__ void __launch_bounds__(256) k_prolong3(int type, int f1, int f2, int 
     coords3(p, f1, f2, F);
     if (!valid3(type, F)) return;
     using R = typename VecTraits<V>::R;
-    int K[3][2], cnt[3];
-    double wd[3][2] = {};
-    R w[3][2];
-    for (int a = 0; a < 3; ++a) {
-        cnt[a] = plist3(a == type, F[a], nc[a], K[a], wd[a]);
-        for (int e = 0; e < 2; ++e) w[a][e] = (R)wd[a][e];     // 1, 1/2, 3/4, 1/4: exact in FP32
-    }
+    int kx[2], ky[2], kz[2];
+    R wx[2], wy[2], wz[2];
+    paxis3<R>(type == 0, F[0], c1, kx, wx);
+    paxis3<R>(type == 1, F[1], c2, ky, wy);
+    paxis3<R>(type == 2, F[2], c3, kz, wz);
     V acc = czero<V>();
-    for (int z = 0; z < cnt[2]; ++z)
-        for (int y = 0; y < cnt[1]; ++y) {
-            const R wzy = w[2][z] * w[1][y];
-            for (int xx = 0; xx < cnt[0]; ++xx) {
-                const size_t q = ((size_t)K[2][z] * c2 + K[1][y]) * c1 + K[0][xx];
-                const V v = ec[q];
-                const R ww = wzy * w[0][xx];
-                acc.x += ww * v.x;
-                acc.y += ww * v.y;
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const R wzy = wz[z] * wy[y];
+#pragma unroll
+            for (int xx = 0; xx < 2; ++xx) {
+                const R ww = wzy * wx[xx];
+                if (ww != R(0)) {
+                    const V v = ec[((size_t)kz[z] * c2 + ky[y]) * c1 + kx[xx]];
+                    acc.x += ww * v.x;
+                    acc.y += ww * v.y;
+                }
             }
         }
     x[p] = cadd(x[p], acc);
 }
 
 template <class V>
-void launch_restrict3(int type, const int* nf, const V* r, V* bc, cudaStream_t st) {
+void launch_restrict3(int type0, int nq, const int* nf, const V* const* r, V* const* bc, cudaStream_t st) {
     const int npc = (nf[0] / 2) * (nf[1] / 2) * (nf[2] / 2);
-    k_restrict3<V><<<(npc + 255) / 256, 256, 0, st>>>(type, nf[0], nf[1], nf[2], r, bc);
+    launch_pdl(k_restrict3<V>, dim3((npc + 255) / 256, nq), dim3(256), 0, st, type0, nf[0], nf[1], nf[2],
+               set3<const V>(r, nq), set3<V>(bc, nq));
 }
 template <class V>
-void launch_prolong3(int type, const int* nf, const V* ec, V* x, cudaStream_t st) {
+void launch_prolong3(int type0, int nq, const int* nf, const V* const* ec, V* const* x, cudaStream_t st) {
     const int np = nf[0] * nf[1] * nf[2];
-    k_prolong3<V><<<(np + 255) / 256, 256, 0, st>>>(type, nf[0], nf[1], nf[2], ec, x);
+    launch_pdl(k_prolong3<V>, dim3((np + 255) / 256, nq), dim3(256), 0, st, type0, nf[0], nf[1], nf[2],
+               set3<const V>(ec, nq), set3<V>(x, nq));
 }
-template void launch_restrict3<double2>(int, const int*, const double2*, double2*, cudaStream_t);
-template void launch_restrict3<float2>(int, const int*, const float2*, float2*, cudaStream_t);
-template void launch_prolong3<double2>(int, const int*, const double2*, double2*, cudaStream_t);
-template void launch_prolong3<float2>(int, const int*, const float2*, float2*, cudaStream_t);
+template void launch_restrict3<double2>(int, int, const int*, const double2* const*, double2* const*, cudaStream_t);
+template void launch_restrict3<float2>(int, int, const int*, const float2* const*, float2* const*, cudaStream_t);
+template void launch_prolong3<double2>(int, int, const int*, const double2* const*, double2* const*, cudaStream_t);
+template void launch_prolong3<float2>(int, int, const int*, const float2* const*, float2* const*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Galerkin coarse operator A_c = R A P (Eq. 4.3) in FP64, one thread per

@@ -497,70 +497,103 @@ struct MG {
 };
 
 // ---------------------------------------------------------------------------
-// three-dimensional multigrid: one block's cycle (Algorithm 1 applied
-// recursively; a W-cycle visits every level below the first twice, the second
-// visit starting from the first's result) and the block-acoustic
-// preconditioner e = P^{-1} D r (Eq. 3.3 - 3.5) with its four blocks
+// three-dimensional multigrid: the cycle of one block, or of the three
+// displacement blocks in the same launches (Algorithm 1 applied recursively; a
+// W-cycle visits every level below the first twice, the second visit starting
+// from the first's result) and the block-acoustic preconditioner
+// e = P^{-1} D r (Eq. 3.3 - 3.5) with its four blocks
 // ---------------------------------------------------------------------------
 template <int MODE>
 struct MG3 {
     using V = typename Prec<MODE>::V;
     static size_t pts(const Ctx& c, int l) { return (size_t)c.d3[l][0] * c.d3[l][1] * c.d3[l][2]; }
     static double jw(const Ctx& c, int l) { return c.o.jacobi_w[std::min(l, c.o.n_jacobi_w - 1)]; }
-    // x_out = Jacobi sweep from x_in (zero: from x_in = 0), or x_out = b - A x_in (res)
-    static void sweep(Ctx& c, int l, int q, const V* b, const V* xin, V* xout, int zero, int res, cudaStream_t st) {
+    // for blocks q0 .. q0 + nq - 1 of level l in one launch: x_out = Jacobi sweep
+    // from x_in (zero: from x_in = 0), or x_out = b - A x_in (res)
+    static void sweep(Ctx& c, int l, int q0, int nq, V* const* xin, V* const* xout, int zero, int res,
+                      cudaStream_t st) {
         const int ns = l == 0 ? 7 : 27;
         const double vb = sizeof(V);
         const double sb = MODE == BAH_MIXED ? 4.0 : 16.0;          // bytes per stored stencil entry
-        Prof pr(c, res ? BAH_K_RESIDUAL : BAH_K_JACOBI, st, (double)pts(c, l) * (ns * sb + (zero ? 2.0 : 3.0) * vb));
-        launch_jacobi3<V>(q, c.d3[l].data(), ns, c.s3s[l][q], b, xin, xout, jw(c, l), zero, res, st);
+        Prof pr(c, res ? BAH_K_RESIDUAL : BAH_K_JACOBI, st, (double)nq * pts(c, l) * (ns * sb + (zero ? 2.0 : 3.0) * vb));
+        const void* S[3];
+        const V* b[3];
+        const V* xi[3];
+        for (int y = 0; y < nq; ++y) {
+            S[y] = c.s3s[l][q0 + y];
+            b[y] = (const V*)c.v3B[l][q0 + y];
+            xi[y] = xin[y];
+        }
+        launch_jacobi3<V>(q0, nq, c.d3[l].data(), ns, S, b, xi, xout, jw(c, l), zero, res, st);
     }
-    // x = approximately A_q^{-1} b_q on level l (b_q in v3B[l][q]); zero: zero initial guess, else start from x
-    static void cycle(Ctx& c, int l, int q, V* x, bool zero, cudaStream_t st) {
-        const V* b = (const V*)c.v3B[l][q];
+    // x_y = approximately A_{q0+y}^{-1} b_{q0+y} on level l for y < nq (b in v3B[l]),
+    // all blocks in the same launches; zero: zero initial guess, else start from x
+    static void cycle(Ctx& c, int l, int q0, int nq, V* const* x, bool zero, cudaStream_t st) {
         const size_t np = pts(c, l);
         if (l == c.L - 1) {
             const double vb = sizeof(V);
-            Prof pr(c, BAH_K_COARSE, st, (double)np * np * 16.0 + 2.0 * np * vb);
-            const double2* inv[1] = {c.inv3[q]};
-            const V* bb[1] = {b};
-            V* xx[1] = {x};
-            launch_coarse_apply<MODE>(1, (int)np, inv, bb, xx, st);
+            Prof pr(c, BAH_K_COARSE, st, nq * ((double)np * np * 16.0 + 2.0 * np * vb));
+            const double2* inv[3];
+            const V* bb[3];
+            for (int y = 0; y < nq; ++y) {
+                inv[y] = c.inv3[q0 + y];
+                bb[y] = (const V*)c.v3B[l][q0 + y];
+            }
+            launch_coarse_apply<MODE>(nq, (int)np, inv, bb, x, st);
             return;
         }
-        V* cur = x;
-        V* spare = (V*)c.v3T[l][q];
+        // the two buffers of each block's ping-pong; the current iterate is in A[y] when inA
+        V* A[3] = {nullptr, nullptr, nullptr};
+        V* B[3] = {nullptr, nullptr, nullptr};
+        for (int y = 0; y < nq; ++y) {
+            A[y] = x[y];
+            B[y] = (V*)c.v3T[l][q0 + y];
+        }
+        bool inA = true;
+        auto cur = [&]() { return inA ? A : B; };
+        auto spare = [&]() { return inA ? B : A; };
         int s0 = 0;
         if (zero) {
             s0 = c.o.nu_pre >= 1 ? 1 : 0;
             // start the ping-pong so that the last sweep writes x
-            if (((c.o.nu_pre - s0) + c.o.nu_post) % 2) std::swap(cur, spare);
-            if (s0) sweep(c, l, q, b, cur, cur, 1, 0, st);
-            else cudaMemsetAsync(cur, 0, np * sizeof(V), st);
+            if (((c.o.nu_pre - s0) + c.o.nu_post) % 2) inA = false;
+            if (s0) sweep(c, l, q0, nq, cur(), cur(), 1, 0, st);
+            else
+                for (int y = 0; y < nq; ++y) cudaMemsetAsync(cur()[y], 0, np * sizeof(V), st);
         }
         for (int s = s0; s < c.o.nu_pre; ++s) {
-            sweep(c, l, q, b, cur, spare, 0, 0, st);
-            std::swap(cur, spare);
+            sweep(c, l, q0, nq, cur(), spare(), 0, 0, st);
+            inA = !inA;
         }
-        sweep(c, l, q, b, cur, spare, 0, 1, st);
-        {
-            Prof pr(c, BAH_K_RESTRICT, st, (double)np * sizeof(V) * 1.125);
-            launch_restrict3<V>(q, c.d3[l].data(), spare, (V*)c.v3B[l + 1][q], st);
+        sweep(c, l, q0, nq, cur(), spare(), 0, 1, st);
+        V* bc[3] = {nullptr, nullptr, nullptr};
+        V* xc[3] = {nullptr, nullptr, nullptr};
+        for (int y = 0; y < nq; ++y) {
+            bc[y] = (V*)c.v3B[l + 1][q0 + y];
+            xc[y] = (V*)c.v3X[l + 1][q0 + y];
         }
-        V* xc = (V*)c.v3X[l + 1][q];
-        cycle(c, l + 1, q, xc, true, st);
-        if (c.o.cycle == BAH_CYCLE_W && l + 1 < c.L - 1) cycle(c, l + 1, q, xc, false, st);
         {
-            Prof pr(c, BAH_K_PROLONG, st, (double)np * sizeof(V) * 2.125);
-            launch_prolong3<V>(q, c.d3[l].data(), xc, cur, st);
+            Prof pr(c, BAH_K_RESTRICT, st, nq * (double)np * sizeof(V) * 1.125);
+            const V* r[3] = {spare()[0], spare()[1], spare()[2]};
+            launch_restrict3<V>(q0, nq, c.d3[l].data(), r, bc, st);
+        }
+        cycle(c, l + 1, q0, nq, xc, true, st);
+        if (c.o.cycle == BAH_CYCLE_W && l + 1 < c.L - 1) cycle(c, l + 1, q0, nq, xc, false, st);
+        {
+            Prof pr(c, BAH_K_PROLONG, st, nq * (double)np * sizeof(V) * 2.125);
+            const V* e[3] = {xc[0], xc[1], xc[2]};
+            launch_prolong3<V>(q0, nq, c.d3[l].data(), e, cur(), st);
         }
         for (int s = 0; s < c.o.nu_post; ++s) {
-            sweep(c, l, q, b, cur, spare, 0, 0, st);
-            std::swap(cur, spare);
+            sweep(c, l, q0, nq, cur(), spare(), 0, 0, st);
+            inA = !inA;
         }
-        if (cur != x) cudaMemcpyAsync(x, cur, np * sizeof(V), cudaMemcpyDeviceToDevice, st);
+        if (!inA)
+            for (int y = 0; y < nq; ++y) cudaMemcpyAsync(x[y], B[y], np * sizeof(V), cudaMemcpyDeviceToDevice, st);
     }
-    // z = P^{-1} D r for one right-hand side (r FP64, z in the cycle's type)
+    // z = P^{-1} D r for one right-hand side (r FP64, z in the cycle's type):
+    // the pressure block's cycle, then the three displacement blocks' cycles
+    // together
     static void precond(Ctx& c, const double2* r, V* z, cudaStream_t st) {
         const size_t np = c.np;
         const double vb = sizeof(V);
@@ -568,13 +601,15 @@ struct MG3 {
             Prof pr(c, BAH_K_DISTRIB, st, (double)np * (64.0 + 56.0 + vb));
             launch_distrib3<V>(c.op3, r, (V*)c.v3B[0][3], st);
         }
-        cycle(c, 0, 3, z + 3 * np, true, st);
+        V* zp[1] = {z + 3 * np};
+        cycle(c, 0, 3, 1, zp, true, st);
         {
             V* su[3] = {(V*)c.v3B[0][0], (V*)c.v3B[0][1], (V*)c.v3B[0][2]};
             Prof pr(c, BAH_K_URHS, st, (double)np * (48.0 + 4.0 * vb));
             launch_urhs3<V>(c.op3, r, z + 3 * np, su, st);
         }
-        for (int q = 0; q < 3; ++q) cycle(c, 0, q, z + q * np, true, st);
+        V* zu[3] = {z, z + np, z + 2 * np};
+        cycle(c, 0, 0, 3, zu, true, st);
     }
 };
 
@@ -954,6 +989,7 @@ static int build(Ctx& c, const bah_medium* med, cudaStream_t st) {
                     rm = std::max(rm, std::max(c.s64[l0 + k][b].rx, c.s64[l0 + k][b].rz));
                 }
             }
+            if (rm > 2) continue;                      // the kernel's stencil radius is at most 2
             for (int cs = 16; cs >= 8 && c.sm_l0 == 0; cs /= 2) {
                 SmArgs a;
                 std::memset(&a, 0, sizeof(a));
@@ -1973,11 +2009,13 @@ int bah_block_cycle(bah_ctx* h, int block, const void* b, void* x, void* stream)
     if (c.dim == 3) {
         if (c.mode == BAH_MIXED) {
             launch_convert<double2, float2>((const double2*)b, (float2*)c.v3B[0][block], np, st);
-            MG3<BAH_MIXED>::cycle(c, 0, block, (float2*)c.ztmp, true, st);
+            float2* xx[1] = {(float2*)c.ztmp};
+            MG3<BAH_MIXED>::cycle(c, 0, block, 1, xx, true, st);
             launch_convert<float2, double2>((const float2*)c.ztmp, (double2*)x, np, st);
         } else {
             BAH_CUDA_TRY(cudaMemcpyAsync(c.v3B[0][block], b, np * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            MG3<BAH_FP64>::cycle(c, 0, block, (double2*)x, true, st);
+            double2* xx[1] = {(double2*)x};
+            MG3<BAH_FP64>::cycle(c, 0, block, 1, xx, true, st);
         }
         BAH_CUDA_TRY(cudaGetLastError());
         return BAH_OK;

@@ -241,7 +241,7 @@ def random_medium(n, seed, lam_range=(1.0, 4.0), mu_range=(0.5, 2.0), rho_range=
 # standard workloads
 # ----------------------------------------------------------------------------
 def config(name: str) -> Problem:
-    """The five named workloads: c1 .. c5."""
+    """The five named workloads c1 .. c5, and c5s, a 64^3 copy of c5."""
     if name == "c1":
         return homogeneous(64, 64, 1.0, 2.0, 0.25, 10.0, 8, "centre")
     if name == "c2":
@@ -252,6 +252,10 @@ def config(name: str) -> Problem:
         return layered(1024, 512, 6, 5, nsrc=64, src_spacing=16)
     if name == "c5":
         return grf_medium((128, 128, 128), 16.0, 3, 4, 8.0, 10)
+    if name == "c5s":
+        # the c5 medium on a 64^3 grid (correlation length and absorbing layer
+        # halved): a small case of the 3-D kernels for profiling
+        return grf_medium((64, 64, 64), 8.0, 3, 4, 8.0, 5)
     raise KeyError(name)
 
 
