@@ -33,7 +33,7 @@
 
 namespace bah {
 
-constexpr int kSmThreads = 384;   // threads per CTA (one CTA per SM)
+constexpr int kSmThreads = 512;   // threads per CTA (one CTA per SM)
 
 namespace {
 
@@ -308,78 +308,128 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_cluster_mg(SmArgs a) {
     };
 
     // ---- the cycle: an explicit walk over the recursion of Algorithm 1 ----
+    // Each pass of the loop picks the next phase from the per-level state and
+    // runs it through one switch, so every phase's code exists once in the
+    // kernel (fewer instructions to fetch after other kernels ran on the SM).
+    enum { kJacobi, kZero, kResidual, kRestrict, kCoarse, kProlong, kCopy };
     unsigned xs[kMaxLevels], ts[kMaxLevels];
-    int stage[kMaxLevels];
+    int pc[kMaxLevels], nsw[kMaxLevels];
     bool warm[kMaxLevels];
     int k = 0;
-    stage[0] = 0;
+    pc[0] = 0;
     warm[0] = a.warm != 0;
     while (true) {
+        int op = -1, kk = k;
+        unsigned u = 0, v = 0;
+        bool zero = false;
         if (k == kc) {
-            coarse();
-            cluster_barrier();
+            op = kCoarse;
             --k;
-            continue;
-        }
-        const SmLevel& L = a.lv[k];
-        if (stage[k] == 0) {
-            unsigned x = L.off_x, t = L.off_t;
-            int s0 = 0;
-            if (!warm[k]) {
-                // with a zero initial guess, start in the buffer from which the visit's
-                // buffer swaps (the pre-sweeps after the first, and the post-sweeps)
-                // end in off_x, where the parent level and the final store read the
-                // result: no copy phase
-                if (((a.nu_pre >= 1 ? a.nu_pre - 1 : 0) + a.nu_post) & 1) {
-                    x = L.off_t;
-                    t = L.off_x;
+        } else {
+            const SmLevel& L = a.lv[k];
+            switch (pc[k]) {
+            case 0: {                                       // entering the visit
+                unsigned x = L.off_x, t = L.off_t;
+                nsw[k] = 0;
+                if (!warm[k]) {
+                    // with a zero initial guess, start in the buffer from which the visit's
+                    // buffer swaps (the pre-sweeps after the first, and the post-sweeps)
+                    // end in off_x, where the parent level and the final store read the
+                    // result: no copy phase
+                    if (((a.nu_pre >= 1 ? a.nu_pre - 1 : 0) + a.nu_post) & 1) {
+                        x = L.off_t;
+                        t = L.off_x;
+                    }
+                    if (a.nu_pre >= 1) {
+                        op = kJacobi;
+                        zero = true;
+                        v = x;
+                        nsw[k] = 1;
+                    } else {
+                        op = kZero;
+                        u = x;
+                    }
                 }
-                if (a.nu_pre >= 1) {
-                    jacobi(k, 0, x, true);
-                    s0 = 1;
+                xs[k] = x;
+                ts[k] = t;
+                pc[k] = 1;
+                break;
+            }
+            case 1:                                         // pre-sweeps, then the residual
+                if (nsw[k] < a.nu_pre) {
+                    op = kJacobi;
+                    u = xs[k];
+                    v = ts[k];
+                    ts[k] = u;
+                    xs[k] = v;
+                    ++nsw[k];
                 } else {
-                    zero_vec(k, x);
+                    op = kResidual;
+                    u = xs[k];
+                    v = ts[k];
+                    pc[k] = 2;
                 }
-                cluster_barrier();
+                break;
+            case 2:
+                op = kRestrict;
+                u = ts[k];
+                pc[k] = 3;
+                break;
+            case 3:                                         // the coarse visit(s)
+                pc[k] = (a.wcycle && k + 1 < kc) ? 4 : 5;
+                ++k;
+                pc[k] = 0;
+                warm[k] = false;
+                break;
+            case 4:                                         // the W-cycle's second coarse visit
+                pc[k] = 5;
+                ++k;
+                pc[k] = 0;
+                warm[k] = true;
+                break;
+            case 5:
+                op = kProlong;
+                u = xs[k];
+                nsw[k] = 0;
+                pc[k] = 6;
+                break;
+            case 6:                                         // post-sweeps, then the copy to off_x
+                if (nsw[k] < a.nu_post) {
+                    op = kJacobi;
+                    u = xs[k];
+                    v = ts[k];
+                    ts[k] = u;
+                    xs[k] = v;
+                    ++nsw[k];
+                    break;
+                }
+                pc[k] = 7;
+                if (xs[k] != L.off_x) {
+                    op = kCopy;
+                    u = xs[k];
+                    v = L.off_x;
+                    xs[k] = L.off_x;
+                }
+                break;
+            default:                                        // visit done
+                break;
             }
-            for (int s = s0; s < a.nu_pre; ++s) {
-                jacobi(k, x, t, false);
-                cluster_barrier();
-                const unsigned sw = x; x = t; t = sw;
+            if (op < 0 && pc[kk] == 7) {
+                if (kk == 0) break;
+                k = kk - 1;
             }
-            residual(k, x, t);
-            cluster_barrier();
-            restrict_(k, t);
-            cluster_barrier();
-            xs[k] = x;
-            ts[k] = t;
-            stage[k] = 1;
-            ++k;
-            stage[k] = 0;
-            warm[k] = false;
-            continue;
         }
-        if (stage[k] == 1 && a.wcycle && k + 1 < kc) {
-            stage[k] = 2;
-            ++k;
-            stage[k] = 0;
-            warm[k] = true;
-            continue;
+        if (op < 0) continue;
+        switch (op) {
+        case kJacobi: jacobi(kk, u, v, zero); break;
+        case kZero: zero_vec(kk, u); break;
+        case kResidual: residual(kk, u, v); break;
+        case kRestrict: restrict_(kk, u); break;
+        case kCoarse: coarse(); break;
+        case kProlong: prolong(kk, u); break;
+        default: copy_vec(kk, u, v); break;
         }
-        unsigned x = xs[k], t = ts[k];
-        prolong(k, x);
         cluster_barrier();
-        for (int s = 0; s < a.nu_post; ++s) {
-            jacobi(k, x, t, false);
-            cluster_barrier();
-            const unsigned sw = x; x = t; t = sw;
-        }
-        if (x != L.off_x) {
-            copy_vec(k, x, L.off_x);
-            cluster_barrier();
-        }
-        if (k == 0) break;
-        --k;
     }
 
     // ---- store the level-l0 result; keep shared memory alive for remote readers ----
