@@ -97,7 +97,11 @@ FP64_FLOP_PER_BYTE = {"dot": 0.5, "axpy": 0.5, "update": 8.0 / 8.0, "operator": 
 # FGMRES step as they occur in the solve, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the same build and workload; the summaries under profiles/ give the
 # command and the per-kernel figures.  (workload, class) -> bytes per launch.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # 512x512 layered: k_jacobi (level 0) and k_stencil_staged sweeps (level 1), 161 launches over
+    # 10 FGMRES steps of the launch list in profiles/launches_c2_512x512_mixed.md
+    ("c2", "jacobi"): 7.289e6,
+}
 
 
 def parse():

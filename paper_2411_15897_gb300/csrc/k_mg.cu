@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) k_restrict(LvlSet<typename MGT<MODE>::V, 
                 acc.y += wgt * v[a * 4 + q].y;
             }
     }
-    cb.p[blockIdx.y][rr * cb.s + t] = acc;
+    pick(cb, (int)blockIdx.y)[rr * cb.s + t] = acc;
 }
 
 template <int MODE>
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(LvlSet<typename MGT<MODE>::
     const int i = t % n1, j = t / n1;
     if (!valid_pt(B.type, i, j)) return;
     const bool nodx = B.type == 0, nodz = B.type == 1;
-    const V* e = ce.p[blockIdx.y] + rr * ce.s;
+    const V* e = pick(ce, (int)blockIdx.y) + rr * ce.s;
     V* xo = B.xout + rr * B.sxo;
     R px[3], pz[3];
 #pragma unroll
@@ -334,14 +334,14 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const dou
     const int lane = threadIdx.x & 31;
     extern __shared__ __align__(16) unsigned char coarse_raw[];
     V* bsh = reinterpret_cast<V*>(coarse_raw);
-    const V* bb = b.p[z] + rr * b.s;
+    const V* bb = pick(b, z) + rr * b.s;
     const bool staged = npts <= kCoarseSmem;
     if (staged) {
         for (int c = threadIdx.x; c < npts; c += blockDim.x) bsh[c] = bb[c];
         __syncthreads();
     }
     if (warp >= npts) return;
-    const double2* row = inv.p[z] + (size_t)warp * npts;
+    const double2* row = pick(inv, z) + (size_t)warp * npts;
     double re = 0.0, im = 0.0;
     auto mac = [&](const double2& a, const V& v) {
         const double vx = (double)v.x, vy = (double)v.y;
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int npts, PtrSet<const dou
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) x.p[z][rr * x.s + warp] = cmk<V>((typename VecTraits<V>::R)re, (typename VecTraits<V>::R)im);
+    if (lane == 0) pick(x, z)[rr * x.s + warp] = cmk<V>((typename VecTraits<V>::R)re, (typename VecTraits<V>::R)im);
 }
 
 template <int MODE>

@@ -8,8 +8,13 @@
 
 namespace bah {
 
-// one pointer per block of a set, with the element stride between right-hand sides
+// one pointer per block of a set, with the element stride between right-hand sides;
+// pick() selects without indexing the kernel-parameter array at a run-time index
+// (which would copy it to the stack)
 template <class V> struct PtrSet { V* p[3]; size_t s = 0; };
+template <class V> __device__ __forceinline__ V* pick(const PtrSet<V>& s, int y) {
+    return y == 0 ? s.p[0] : (y == 1 ? s.p[1] : s.p[2]);
+}
 
 template <int MODE>
 struct MGT {
